@@ -1,0 +1,171 @@
+/*
+ * tc.h -- C ABI of a GB300 (sm_103a) tensor-contraction engine.
+ *
+ * The operation is the two-operand contraction of Section 1 ("Tensor
+ * Notation") of Peise, Fabregat-Traver and Bientinesi, "On the Performance
+ * Prediction of BLAS-based Tensor Contractions":
+ *
+ *     C[f] = alpha * sum_{k contracted} A[f_A, k] * B[f_B, k] + beta * C[f]
+ *
+ * An index that appears in both inputs and not in C is contracted; an index
+ * that appears in exactly one input and in C is free.  Every algorithm the
+ * library runs is one of the loop nests of Section 2 (slicing rules of
+ * Table 1: a loop nest around one dot, axpy, gemv, ger or gemm kernel, with
+ * copies where a matrix slice has no unit-stride dimension), or the fused
+ * GETT kernel (algorithm 0), which has no counterpart in the paper.
+ *
+ * Conventions (not fixed by the paper):
+ *   spec     "C=A,B" with one lower-case letter per index, e.g. "abc=ai,ibc".
+ *   extents  one int64 per distinct index, in order of first appearance in
+ *            the spec string read left to right ("abc=ai,ibc": a, b, c, i).
+ *   strides  element strides, C modes then A modes then B modes, each in the
+ *            spec's mode order; NULL means Fortran-contiguous storage, first
+ *            index fastest (Section 1).  Strides must be >= 1.
+ *   A, B, C  device pointers owned by the caller.  The library never frees
+ *            them.  Element types by plan dtype:
+ *              TC_F64      A, B, C double
+ *              TC_F32      A, B, C float
+ *              TC_TF32     A, B, C float (tensor cores, TF32 products)
+ *              TC_BF16X3   A, B, C float (each input split in three BF16
+ *                          slices on the tensor cores; see tc_plan_set_split)
+ *              TC_BF16     A, B __nv_bfloat16; C float
+ *              TC_F16      A, B __half; C float
+ *   alpha,   host pointers to one double (TC_F64) or one float (all other
+ *   beta     dtypes).  beta == 0 writes C without reading it.
+ *   stream   a cudaStream_t passed as void*; NULL is the legacy default
+ *            stream.
+ *
+ * Errors: every call returns a tc_status.  Device work is asynchronous:
+ * tc_execute reports argument and launch errors at once and device-side
+ * timeouts through tc_plan_device_status after the stream is synchronised.
+ * A plan is not thread-safe; use one plan per host thread.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TC_SUCCESS = 0,
+    TC_ERROR_INVALID_SPEC = 1,      /* malformed spec or index classes */
+    TC_ERROR_INVALID_EXTENT = 2,    /* extent < 1 or product overflow */
+    TC_ERROR_INVALID_STRIDE = 3,    /* stride < 1 or C self-overlap */
+    TC_ERROR_UNSUPPORTED_DTYPE = 4, /* dtype not valid for this algorithm */
+    TC_ERROR_INVALID_ALGORITHM = 5, /* id out of range */
+    TC_ERROR_OUT_OF_MEMORY = 6,     /* workspace allocation failed */
+    TC_ERROR_CUDA = 7,              /* a CUDA runtime call failed */
+    TC_ERROR_TIMEOUT = 8,           /* a bounded device wait gave up */
+    TC_ERROR_INVALID_ARGUMENT = 9,  /* NULL pointer, bad size, misuse */
+    TC_ERROR_ADMISSION = 10         /* request does not fit the budget */
+} tc_status;
+
+typedef enum {
+    TC_F64 = 0,
+    TC_F32 = 1,
+    TC_TF32 = 2,
+    TC_BF16 = 3,
+    TC_F16 = 4,
+    TC_BF16X3 = 5
+} tc_dtype;
+
+/* Kernels of Section 2 (BLAS-1: dot, axpy; BLAS-2: gemv, ger; BLAS-3:
+ * gemm) plus the fused GETT of algorithm 0. */
+typedef enum {
+    TC_KERNEL_DOT = 0,
+    TC_KERNEL_AXPY = 1,
+    TC_KERNEL_GEMV = 2,
+    TC_KERNEL_GER = 3,
+    TC_KERNEL_GEMM = 4,
+    TC_KERNEL_GETT = 5
+} tc_kernel;
+
+typedef struct tc_plan_s *tc_plan;
+
+/* One algorithm.  Loop and index letters are those of the spec. */
+typedef struct {
+    int32_t id;               /* 0 = fused GETT; 1..n = Section 2 algorithms
+                                 in enumeration order (kernels dot, axpy,
+                                 gemv, ger, gemm; kernel-index choices with
+                                 the free index of A outermost, then that of
+                                 B, then the contracted one; loop orders in
+                                 lexicographic order of first appearance) */
+    char name[32];            /* NUL-terminated, e.g. "i'c-gemm" or "gett":
+                                 sliced loops outermost first, an apostrophe
+                                 after the loop holding a copy, then "-" and
+                                 the kernel (Section 2, naming footnote) */
+    int32_t kernel;           /* tc_kernel */
+    int32_t n_loops;          /* number of sliced loops */
+    char loops[8];            /* sliced indices, outermost first */
+    int32_t n_kernel_indices;
+    char kernel_indices[4];   /* by role: dot {k}; axpy {f}; gemv {f, k};
+                                 ger {fA, fB}; gemm {fA, fB, k} */
+    uint32_t copy_mask;       /* bit 0: A slice copied, bit 1: B, bit 2: C */
+    int32_t copy_level[3];    /* A, B, C: position of the loop whose body
+                                 holds the copy, -1 before every loop,
+                                 -2 no copy */
+    int32_t n_phases;         /* device-wide sequential phases: product of
+                                 the contracted loops that enclose a free
+                                 loop (1 for GETT) */
+} tc_algorithm;
+
+/* Parses the spec, classifies the indices, validates extents and strides
+ * and enumerates the algorithms (Section 2, Table 1).  No device work and
+ * no device memory.  Rejects: an index in all three operands or in one
+ * input only, a repeated index within an operand, more than 8 modes per
+ * operand, extents < 1, strides < 1, and C strides under which two C
+ * elements share an address.  *out is NULL on failure. */
+tc_status tc_plan_create(tc_plan *out, const char *spec, const int64_t *extents,
+                         const int64_t *strides, tc_dtype dtype);
+
+/* Frees the plan and the device workspace it owns.  NULL is accepted. */
+tc_status tc_plan_destroy(tc_plan plan);
+
+/* Number of algorithms including GETT (ids 0 .. count-1). */
+tc_status tc_algorithm_count(tc_plan plan, int32_t *count);
+
+/* Copies up to capacity algorithm records into out (out may be NULL when
+ * capacity is 0) and stores the total in *count. */
+tc_status tc_enumerate_algorithms(tc_plan plan, tc_algorithm *out,
+                                  int32_t capacity, int32_t *count);
+
+/* Selects the algorithm tc_execute runs.  A new plan starts with GETT
+ * (id 0) selected, or with the top-ranked algorithm once tc_predict has
+ * ranked every candidate through tc_plan_select_best. */
+tc_status tc_plan_select(tc_plan plan, int32_t alg_id);
+
+/* The currently selected algorithm id. */
+tc_status tc_plan_selected(tc_plan plan, int32_t *alg_id);
+
+/* Bytes of device workspace the algorithm needs (copy buffers).  The plan
+ * allocates it on the first tc_execute of that algorithm and keeps it until
+ * tc_plan_destroy; call tc_execute once before capturing a CUDA graph. */
+tc_status tc_algorithm_workspace(tc_plan plan, int32_t alg_id, size_t *bytes);
+
+/* C = alpha * A.B + beta * C with the selected algorithm, enqueued on
+ * stream.  Returns after the launches are enqueued. */
+tc_status tc_execute(tc_plan plan, const void *alpha, const void *A,
+                     const void *B, const void *beta, void *C, void *stream);
+
+/* Reads and clears the plan's device status word (waits for the stream
+ * the plan last ran on): TC_SUCCESS or TC_ERROR_TIMEOUT. */
+tc_status tc_plan_device_status(tc_plan plan);
+
+/* 2 * product of all extents. */
+tc_status tc_plan_flops(tc_plan plan, double *flops);
+
+/* Static description of a status code.  Never NULL. */
+const char *tc_status_string(tc_status status);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *tc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

@@ -1,0 +1,723 @@
+// Nest executor: runs one Section 2 algorithm (a loop nest around one BLAS
+// kernel) on the GPU, plus the SIMT form of the fused GETT for FP64/FP32.
+//
+// Reading of the sequential loop nests for a parallel device (the paper
+// describes sequential CPU loops only):
+//  * Loops keep their nest order.  Iterations of a free loop write disjoint
+//    C slices and run concurrently.
+//  * A contracted loop that encloses a free loop becomes a device-wide
+//    phase: one launch per iteration, in order, C carried through memory.
+//  * The remaining contracted loops (those with no free loop inside them)
+//    run in order inside each task, C held in registers.
+//  * Every C element therefore sees one fixed chain of fused multiply-adds
+//    acc = fma(alpha*a, b, acc) over the contracted indices in nest order
+//    (phase loops, then in-task loops, then the kernel's own contracted
+//    index), starting from beta*C.  Algorithms with the same contracted
+//    order give bitwise identical results.
+//  * Copies (Section 2: a matrix slice without a unit-stride dimension)
+//    materialise the slice into a contiguous workspace at the phase they
+//    belong to, once per combination of the loops the slice depends on.
+//
+// Kernels: dot, axpy, gemv and ger run one thread per output element of a
+// kernel call (kernel outputs fastest across threads, then the innermost
+// free loop), reading operands straight from L1/L2 -- the BLAS-1/2 shape.
+// gemm runs as a shared-memory tiled register-blocked kernel -- the BLAS-3
+// shape.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tc_internal.h"
+
+namespace tc {
+
+struct Dims {
+    int n;
+    int64_t ext[kMaxModes];
+    int64_t sA[kMaxModes], sB[kMaxModes], sC[kMaxModes];
+};
+
+struct PhaseDesc {
+    Dims out;   // kernel output modes, first fastest
+    Dims task;  // free sliced loops, outermost first (innermost fastest)
+    Dims red;   // contracted: in-task loops outermost first, kernel index last
+    int64_t total;
+    const void *A;
+    const void *B;
+    void *C;
+    double alpha, beta;
+    int init;       // 0: acc = C, 1: acc = beta*C, 2: acc = 0
+    int alpha_one;  // alpha == 1: skip the scaling multiply
+};
+
+struct TileDesc {
+    Dims m;     // M modes (first fastest): strides sA and sC
+    Dims n;     // N modes: strides sB and sC
+    Dims red;   // K modes, outermost first
+    Dims task;  // tasks: free sliced loops, outermost first
+    int64_t M, N, K;
+    int64_t tiles_m, tiles_n;
+    const void *A;
+    const void *B;
+    void *C;
+    double alpha, beta;
+    int init, alpha_one;
+    int a_m_fast, b_n_fast;  // load mapping: M (N) contiguous in memory
+};
+
+struct GatherDesc {
+    int n;
+    int64_t ext[2 * kMaxModes];
+    int64_t ss[2 * kMaxModes];  // source strides
+    int64_t sd[2 * kMaxModes];  // destination strides
+    int64_t total;
+    const void *src;
+    void *dst;
+};
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c);
+template <>
+__device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
+template <>
+__device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
+
+// ---------------------------------------------------------------- dot/axpy/gemv/ger
+template <typename T>
+__global__ void __launch_bounds__(256) elementwise_kernel(const PhaseDesc d) {
+    const T *__restrict__ A = (const T *)d.A;
+    const T *__restrict__ B = (const T *)d.B;
+    T *__restrict__ C = (T *)d.C;
+    const T alpha = (T)d.alpha, beta = (T)d.beta;
+    const int nr = d.red.n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d.total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e, oA = 0, oB = 0, oC = 0;
+        for (int m = 0; m < d.out.n; ++m) {
+            int64_t x = r % d.out.ext[m];
+            r /= d.out.ext[m];
+            oA += x * d.out.sA[m];
+            oB += x * d.out.sB[m];
+            oC += x * d.out.sC[m];
+        }
+        for (int m = d.task.n - 1; m >= 0; --m) {
+            int64_t x = r % d.task.ext[m];
+            r /= d.task.ext[m];
+            oA += x * d.task.sA[m];
+            oB += x * d.task.sB[m];
+            oC += x * d.task.sC[m];
+        }
+        T acc;
+        if (d.init == 2) {
+            acc = T(0);
+        } else {
+            acc = C[oC];
+            if (d.init == 1) acc = beta * acc;
+        }
+        if (nr == 0) {
+            T a = A[oA];
+            if (!d.alpha_one) a = alpha * a;
+            acc = fma_t<T>(a, B[oB], acc);
+        } else {
+            int64_t idx[kMaxModes];
+            for (int m = 0; m < nr; ++m) idx[m] = 0;
+            const int64_t kext = d.red.ext[nr - 1];
+            const int64_t ksA = d.red.sA[nr - 1], ksB = d.red.sB[nr - 1];
+            for (;;) {
+                int64_t pa = oA, pb = oB;
+                for (int m = 0; m < nr - 1; ++m) {
+                    pa += idx[m] * d.red.sA[m];
+                    pb += idx[m] * d.red.sB[m];
+                }
+                for (int64_t k = 0; k < kext; ++k) {
+                    T a = A[pa];
+                    if (!d.alpha_one) a = alpha * a;
+                    acc = fma_t<T>(a, B[pb], acc);
+                    pa += ksA;
+                    pb += ksB;
+                }
+                int m = nr - 2;
+                while (m >= 0) {
+                    if (++idx[m] < d.red.ext[m]) break;
+                    idx[m] = 0;
+                    --m;
+                }
+                if (m < 0) break;
+            }
+        }
+        C[oC] = acc;
+    }
+}
+
+// ---------------------------------------------------------------- gemm / SIMT GETT
+// One CTA computes a BM x BN tile of one task's C slice; K runs over the
+// linearised contracted space in chunks of BK staged through shared memory.
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+tile_kernel(const TileDesc d) {
+    constexpr int TX = BN / TN, TY = BM / TM, NT = TX * TY;
+    __shared__ T As[BK][BM];
+    __shared__ T Bs[BK][BN];
+    __shared__ int64_t offAm[BM], offCm[BM], offBn[BN], offCn[BN];
+    __shared__ int64_t kA[BK], kB[BK];
+    const T *__restrict__ A = (const T *)d.A;
+    const T *__restrict__ B = (const T *)d.B;
+    T *__restrict__ C = (T *)d.C;
+    const T alpha = (T)d.alpha, beta = (T)d.beta;
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+
+    int64_t bid = blockIdx.x;
+    const int64_t tm = bid % d.tiles_m;
+    bid /= d.tiles_m;
+    const int64_t tn = bid % d.tiles_n;
+    int64_t task = bid / d.tiles_n;
+    int64_t tA = 0, tB = 0, tC = 0;
+    for (int m = d.task.n - 1; m >= 0; --m) {
+        int64_t x = task % d.task.ext[m];
+        task /= d.task.ext[m];
+        tA += x * d.task.sA[m];
+        tB += x * d.task.sB[m];
+        tC += x * d.task.sC[m];
+    }
+    for (int i = tid; i < BM; i += NT) {
+        int64_t mm = tm * BM + i;
+        int64_t oa = -1, oc = -1;
+        if (mm < d.M) {
+            oa = tA;
+            oc = tC;
+            for (int m = 0; m < d.m.n; ++m) {
+                int64_t x = mm % d.m.ext[m];
+                mm /= d.m.ext[m];
+                oa += x * d.m.sA[m];
+                oc += x * d.m.sC[m];
+            }
+        }
+        offAm[i] = oa;
+        offCm[i] = oc;
+    }
+    for (int j = tid; j < BN; j += NT) {
+        int64_t nn = tn * BN + j;
+        int64_t ob = -1, oc = -1;
+        if (nn < d.N) {
+            ob = tB;
+            oc = 0;
+            for (int m = 0; m < d.n.n; ++m) {
+                int64_t x = nn % d.n.ext[m];
+                nn /= d.n.ext[m];
+                ob += x * d.n.sB[m];
+                oc += x * d.n.sC[m];
+            }
+        }
+        offBn[j] = ob;
+        offCn[j] = oc;
+    }
+    __syncthreads();
+
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int64_t om = offCm[ty + i * TY];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int64_t on = offCn[tx + j * TX];
+            T v = T(0);
+            if (d.init != 2 && om >= 0 && on >= 0) {
+                v = C[om + on];
+                if (d.init == 1) v = beta * v;
+            }
+            acc[i][j] = v;
+        }
+    }
+
+    for (int64_t k0 = 0; k0 < d.K; k0 += BK) {
+        for (int kk = tid; kk < BK; kk += NT) {
+            int64_t k = k0 + kk;
+            int64_t oa = -1, ob = -1;
+            if (k < d.K) {
+                oa = 0;
+                ob = 0;
+                for (int m = d.red.n - 1; m >= 0; --m) {
+                    int64_t x = k % d.red.ext[m];
+                    k /= d.red.ext[m];
+                    oa += x * d.red.sA[m];
+                    ob += x * d.red.sB[m];
+                }
+            }
+            kA[kk] = oa;
+            kB[kk] = ob;
+        }
+        __syncthreads();
+        for (int e = tid; e < BM * BK; e += NT) {
+            int i, kk;
+            if (d.a_m_fast) { i = e % BM; kk = e / BM; }
+            else { kk = e % BK; i = e / BK; }
+            const int64_t om = offAm[i], ok = kA[kk];
+            T v = T(0);
+            if (om >= 0 && ok >= 0) {
+                v = A[om + ok];
+                if (!d.alpha_one) v = alpha * v;
+            }
+            As[kk][i] = v;
+        }
+        for (int e = tid; e < BN * BK; e += NT) {
+            int j, kk;
+            if (d.b_n_fast) { j = e % BN; kk = e / BN; }
+            else { kk = e % BK; j = e / BK; }
+            const int64_t on = offBn[j], ok = kB[kk];
+            Bs[kk][j] = (on >= 0 && ok >= 0) ? B[on + ok] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * TY];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + j * TX];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma_t<T>(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int64_t om = offCm[ty + i * TY];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int64_t on = offCn[tx + j * TX];
+            if (om >= 0 && on >= 0) C[om + on] = acc[i][j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- copy
+template <typename T>
+__global__ void __launch_bounds__(256) gather_kernel(const GatherDesc g) {
+    const T *__restrict__ src = (const T *)g.src;
+    T *__restrict__ dst = (T *)g.dst;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g.total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e, os = 0, od = 0;
+        for (int m = 0; m < g.n; ++m) {
+            int64_t x = r % g.ext[m];
+            r /= g.ext[m];
+            os += x * g.ss[m];
+            od += x * g.sd[m];
+        }
+        dst[od] = src[os];
+    }
+}
+
+// ---------------------------------------------------------------- host helpers
+int g_sm_count = 0;
+
+int sm_count() {
+    if (g_sm_count == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sm_count <= 0) g_sm_count = 1;
+    }
+    return g_sm_count;
+}
+
+int64_t grid_for(int64_t total, int per_block) {
+    int64_t blocks = (total + per_block - 1) / per_block;
+    int64_t cap = (int64_t)sm_count() * 32;
+    return std::max<int64_t>(1, std::min(blocks, cap));
+}
+
+void add_dim(Dims &d, int64_t ext, int64_t sA, int64_t sB, int64_t sC) {
+    d.ext[d.n] = ext;
+    d.sA[d.n] = sA;
+    d.sB[d.n] = sB;
+    d.sC[d.n] = sC;
+    ++d.n;
+}
+
+// Per-operand addressing for one execution: original or workspace layout.
+struct OpView {
+    bool copied = false;
+    const char *base = nullptr;        // workspace base when copied
+    int64_t ws_stride[kMaxIdx] = {};   // workspace stride per index id
+    bool ws_has[kMaxIdx] = {};
+    // copy description
+    std::vector<int> copy_ids;         // kernel modes, then non-phase dependencies
+    int64_t elems = 0;
+};
+
+struct NestLayout {
+    std::vector<int> phase_pos;   // positions of phase loops (contracted, <= q)
+    std::vector<int> task_ids;    // free loop index ids, nest order
+    std::vector<int> red_ids;     // contracted in-task loops, then kernel k
+    std::vector<int> out_ids;     // kernel output modes
+    OpView view[3];
+    size_t ws_offset[3] = {0, 0, 0};
+    size_t ws_bytes = 0;
+};
+
+NestLayout layout_for(const Plan &p, const Algorithm &alg) {
+    NestLayout L;
+    for (int pos = 0; pos < alg.nloops; ++pos) {
+        int id = alg.loops[pos];
+        if (p.cls[id] == CLS_CONTRACTED) {
+            if (pos <= alg.q) L.phase_pos.push_back(pos);
+            else L.red_ids.push_back(id);
+        } else {
+            L.task_ids.push_back(id);
+        }
+    }
+    switch (alg.kernel) {
+    case TC_KERNEL_DOT: L.red_ids.push_back(alg.kidx[0]); break;
+    case TC_KERNEL_AXPY: L.out_ids.push_back(alg.kidx[0]); break;
+    case TC_KERNEL_GEMV:
+        L.out_ids.push_back(alg.kidx[0]);
+        L.red_ids.push_back(alg.kidx[1]);
+        break;
+    case TC_KERNEL_GER:
+        L.out_ids.push_back(alg.kidx[0]);
+        L.out_ids.push_back(alg.kidx[1]);
+        break;
+    case TC_KERNEL_GEMM:
+        L.out_ids.push_back(alg.kidx[0]);
+        L.out_ids.push_back(alg.kidx[1]);
+        L.red_ids.push_back(alg.kidx[2]);
+        break;
+    }
+    size_t esz[3] = {elem_bytes_ab(p.dtype), elem_bytes_ab(p.dtype), elem_bytes_c(p.dtype)};
+    size_t off = 0;
+    for (int o = 0; o < 3; ++o) {
+        if (alg.copy_level[o] == -2) continue;
+        OpView &v = L.view[o];
+        v.copied = true;
+        const Layout &lay = p.op[o];
+        // kernel modes in storage order, then the loops the slice depends on
+        // that are not fixed by the phase, in nest order
+        for (int m = 0; m < lay.n; ++m)
+            for (int r = 0; r < alg.nk; ++r)
+                if (lay.idx[m] == alg.kidx[r]) v.copy_ids.push_back(lay.idx[m]);
+        for (int pos = 0; pos < alg.nloops; ++pos) {
+            int id = alg.loops[pos];
+            if (!lay.has(id)) continue;
+            bool phase = p.cls[id] == CLS_CONTRACTED && pos <= alg.q;
+            if (!phase) v.copy_ids.push_back(id);
+        }
+        int64_t s = 1;
+        for (int id : v.copy_ids) {
+            v.ws_stride[id] = s;
+            v.ws_has[id] = true;
+            s *= p.ext[id];
+        }
+        v.elems = s;
+        L.ws_offset[o] = off;
+        off += ((size_t)s * esz[o] + 255) / 256 * 256;
+    }
+    L.ws_bytes = off;
+    return L;
+}
+
+template <typename T>
+tc_status launch_gather(const GatherDesc &g, cudaStream_t st) {
+    int64_t grid = grid_for(g.total, 256);
+    gather_kernel<T><<<(unsigned)grid, 256, 0, st>>>(g);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? TC_SUCCESS : fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+}
+
+template <typename T>
+tc_status launch_copy(const Plan &p, int o, const OpView &v, const char *src_base,
+                      void *dst, bool scatter, cudaStream_t st) {
+    GatherDesc g;
+    std::memset(&g, 0, sizeof(g));
+    g.n = (int)v.copy_ids.size();
+    for (int m = 0; m < g.n; ++m) {
+        int id = v.copy_ids[m];
+        g.ext[m] = p.ext[id];
+        int64_t orig = p.op[o].stride_of(id);
+        int64_t ws = v.ws_stride[id];
+        g.ss[m] = scatter ? ws : orig;
+        g.sd[m] = scatter ? orig : ws;
+    }
+    g.total = v.elems;
+    g.src = scatter ? dst : src_base;
+    g.dst = scatter ? (void *)src_base : dst;
+    return launch_gather<T>(g, st);
+}
+
+template <typename T>
+tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *B,
+                   T beta, T *C, cudaStream_t st) {
+    NestLayout L = layout_for(p, alg);
+    char *ws = (char *)p.workspace;
+    const char *base[3] = {(const char *)A, (const char *)B, (const char *)C};
+    const size_t esz = sizeof(T);
+    // stride of index id in operand o as the phase kernel sees it
+    auto stride_in = [&](int o, int id) -> int64_t {
+        if (L.view[o].copied) return L.view[o].ws_has[id] ? L.view[o].ws_stride[id] : 0;
+        return p.op[o].stride_of(id);
+    };
+    auto fill = [&](Dims &d, const std::vector<int> &ids) {
+        d.n = 0;
+        for (int id : ids)
+            add_dim(d, p.ext[id], stride_in(OP_A, id), stride_in(OP_B, id), stride_in(OP_C, id));
+    };
+    const int init0 = beta == T(0) ? 2 : (beta == T(1) ? 0 : 1);
+    const bool alpha_one = alpha == T(1);
+    const bool tiled = alg.kernel == TC_KERNEL_GEMM;
+
+    PhaseDesc pd;
+    TileDesc td;
+    std::memset(&pd, 0, sizeof(pd));
+    std::memset(&td, 0, sizeof(td));
+    int64_t ntasks = 1;
+    for (int id : L.task_ids) ntasks *= p.ext[id];
+    if (tiled) {
+        std::vector<int> mi{L.out_ids[0]}, ni{L.out_ids[1]};
+        fill(td.m, mi);
+        fill(td.n, ni);
+        fill(td.red, L.red_ids);
+        fill(td.task, L.task_ids);
+        td.M = p.ext[L.out_ids[0]];
+        td.N = p.ext[L.out_ids[1]];
+        td.K = 1;
+        for (int id : L.red_ids) td.K *= p.ext[id];
+        td.alpha = alpha;
+        td.beta = beta;
+        td.alpha_one = alpha_one;
+        // map threads along whichever of M / K is contiguous in memory
+        int64_t kinA = td.red.n ? td.red.sA[td.red.n - 1] : 0;
+        int64_t kinB = td.red.n ? td.red.sB[td.red.n - 1] : 0;
+        td.a_m_fast = td.m.sA[0] <= kinA || kinA == 0;
+        td.b_n_fast = td.n.sB[0] <= kinB || kinB == 0;
+    } else {
+        fill(pd.out, L.out_ids);
+        fill(pd.task, L.task_ids);
+        fill(pd.red, L.red_ids);
+        int64_t nout = 1;
+        for (int id : L.out_ids) nout *= p.ext[id];
+        pd.total = nout * ntasks;
+        pd.alpha = alpha;
+        pd.beta = beta;
+        pd.alpha_one = alpha_one;
+    }
+
+    // C copy (reading for a C slice without a unit-stride mode): gather once,
+    // run every phase on the workspace, scatter back at the end
+    void *Cptr = C;
+    tc_status s;
+    if (L.view[OP_C].copied) {
+        Cptr = ws + L.ws_offset[OP_C];
+        if (init0 != 2) {
+            s = launch_copy<T>(p, OP_C, L.view[OP_C], base[OP_C], Cptr, false, st);
+            if (s != TC_SUCCESS) return s;
+        }
+    }
+
+    const int nph = (int)L.phase_pos.size();
+    std::vector<int64_t> ph(nph, 0);
+    bool first = true;
+    int changed_from = 0;  // outermost phase digit that changed
+    for (;;) {
+        // operand bases for this phase: fixed contracted indices applied
+        const char *opb[2];
+        for (int o = 0; o < 2; ++o) {
+            int64_t off = 0;
+            for (int k = 0; k < nph; ++k) off += ph[k] * p.op[o].stride_of(alg.loops[L.phase_pos[k]]);
+            opb[o] = base[o] + off * (int64_t)esz;
+        }
+        const void *Aeff = opb[0], *Beff = opb[1];
+        for (int o = 0; o < 2; ++o) {
+            if (!L.view[o].copied) continue;
+            void *dst = ws + L.ws_offset[o];
+            int level = alg.copy_level[o];
+            bool redo = first || level > alg.q;
+            if (!redo) {
+                for (int k = changed_from; k < nph; ++k)
+                    if (L.phase_pos[k] <= level) redo = true;
+            }
+            if (redo) {
+                s = launch_copy<T>(p, o, L.view[o], opb[o], dst, false, st);
+                if (s != TC_SUCCESS) return s;
+            }
+            if (o == 0) Aeff = dst;
+            else Beff = dst;
+        }
+        const int init = first ? init0 : 0;
+        if (tiled) {
+            td.A = Aeff;
+            td.B = Beff;
+            td.C = Cptr;
+            td.init = init;
+            if (sizeof(T) == 8) {
+                constexpr int BM = 64, BN = 64;
+                td.tiles_m = (td.M + BM - 1) / BM;
+                td.tiles_n = (td.N + BN - 1) / BN;
+                int64_t grid = td.tiles_m * td.tiles_n * ntasks;
+                tile_kernel<T, 64, 64, 16, 4, 4><<<(unsigned)grid, 256, 0, st>>>(td);
+            } else {
+                constexpr int BM = 128, BN = 128;
+                td.tiles_m = (td.M + BM - 1) / BM;
+                td.tiles_n = (td.N + BN - 1) / BN;
+                int64_t grid = td.tiles_m * td.tiles_n * ntasks;
+                tile_kernel<T, 128, 128, 8, 8, 8><<<(unsigned)grid, 256, 0, st>>>(td);
+            }
+        } else {
+            pd.A = Aeff;
+            pd.B = Beff;
+            pd.C = Cptr;
+            pd.init = init;
+            int64_t grid = grid_for(pd.total, 256);
+            elementwise_kernel<T><<<(unsigned)grid, 256, 0, st>>>(pd);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+        first = false;
+        // advance the phase odometer (innermost phase loop fastest)
+        int k = nph - 1;
+        while (k >= 0) {
+            if (++ph[k] < p.ext[alg.loops[L.phase_pos[k]]]) break;
+            ph[k] = 0;
+            --k;
+        }
+        if (k < 0) break;
+        changed_from = k;
+    }
+    if (L.view[OP_C].copied) {
+        s = launch_copy<T>(p, OP_C, L.view[OP_C], base[OP_C], Cptr, true, st);
+        if (s != TC_SUCCESS) return s;
+    }
+    return TC_SUCCESS;
+}
+
+// SIMT GETT: the whole contraction as one tiled kernel, M = free indices
+// of A, N = free indices of B, K = contracted indices.
+template <typename T>
+tc_status run_gett_simt(Plan &p, T alpha, const T *A, const T *B, T beta, T *C,
+                        cudaStream_t st) {
+    TileDesc td;
+    std::memset(&td, 0, sizeof(td));
+    auto by_c_stride = [&](std::vector<int> ids) {
+        std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) {
+            return p.op[OP_C].stride_of(x) < p.op[OP_C].stride_of(y);
+        });
+        return ids;
+    };
+    std::vector<int> mi = by_c_stride(p.freeA), ni = by_c_stride(p.freeB);
+    // K: the contracted index contiguous in A (or else in B) innermost
+    std::vector<int> ki(p.contracted);
+    std::stable_sort(ki.begin(), ki.end(), [&](int x, int y) {
+        int64_t mx = std::min(p.op[OP_A].stride_of(x), p.op[OP_B].stride_of(x));
+        int64_t my = std::min(p.op[OP_A].stride_of(y), p.op[OP_B].stride_of(y));
+        return mx > my;
+    });
+    auto fill = [&](Dims &d, const std::vector<int> &ids) {
+        d.n = 0;
+        for (int id : ids)
+            add_dim(d, p.ext[id], p.op[OP_A].stride_of(id), p.op[OP_B].stride_of(id),
+                    p.op[OP_C].stride_of(id));
+    };
+    fill(td.m, mi);
+    fill(td.n, ni);
+    fill(td.red, ki);
+    td.task.n = 0;
+    td.M = td.N = td.K = 1;
+    for (int id : mi) td.M *= p.ext[id];
+    for (int id : ni) td.N *= p.ext[id];
+    for (int id : ki) td.K *= p.ext[id];
+    td.A = A;
+    td.B = B;
+    td.C = C;
+    td.alpha = alpha;
+    td.beta = beta;
+    td.alpha_one = alpha == T(1);
+    td.init = beta == T(0) ? 2 : (beta == T(1) ? 0 : 1);
+    int64_t kinA = td.red.n ? td.red.sA[td.red.n - 1] : 0;
+    int64_t kinB = td.red.n ? td.red.sB[td.red.n - 1] : 0;
+    td.a_m_fast = td.m.n ? (td.m.sA[0] <= kinA || kinA == 0) : 0;
+    td.b_n_fast = td.n.n ? (td.n.sB[0] <= kinB || kinB == 0) : 0;
+    if (sizeof(T) == 8) {
+        td.tiles_m = (td.M + 63) / 64;
+        td.tiles_n = (td.N + 63) / 64;
+        tile_kernel<T, 64, 64, 16, 4, 4><<<(unsigned)(td.tiles_m * td.tiles_n), 256, 0, st>>>(td);
+    } else {
+        td.tiles_m = (td.M + 127) / 128;
+        td.tiles_n = (td.N + 127) / 128;
+        tile_kernel<T, 128, 128, 8, 8, 8><<<(unsigned)(td.tiles_m * td.tiles_n), 256, 0, st>>>(td);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? TC_SUCCESS : fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+size_t nest_workspace_bytes(const Plan &p, const Algorithm &alg) {
+    return layout_for(p, alg).ws_bytes;
+}
+
+tc_status ensure_device_resources(Plan &p, size_t workspace_bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+    if (p.device < 0) {
+        p.device = dev;
+    } else if (p.device != dev) {
+        return fail(TC_ERROR_INVALID_ARGUMENT, "plan used on a different device than its first execute");
+    }
+    if (!p.dev_status) {
+        e = cudaMalloc((void **)&p.dev_status, sizeof(int) * 4);
+        if (e != cudaSuccess) return fail(TC_ERROR_OUT_OF_MEMORY, cudaGetErrorString(e));
+        cudaMemset(p.dev_status, 0, sizeof(int) * 4);
+    }
+    if (workspace_bytes > p.workspace_bytes) {
+        if (p.workspace) cudaFree(p.workspace);
+        p.workspace = nullptr;
+        p.workspace_bytes = 0;
+        e = cudaMalloc(&p.workspace, workspace_bytes);
+        if (e != cudaSuccess) {
+            p.workspace = nullptr;
+            return fail(TC_ERROR_OUT_OF_MEMORY, cudaGetErrorString(e));
+        }
+        p.workspace_bytes = workspace_bytes;
+    }
+    return TC_SUCCESS;
+}
+
+tc_status exec_nest(Plan &p, const Algorithm &alg, const void *alpha, const void *A,
+                    const void *B, const void *beta, void *C, void *stream) {
+    if (p.dtype != TC_F64 && p.dtype != TC_F32)
+        return fail(TC_ERROR_UNSUPPORTED_DTYPE,
+                    "the loop-nest algorithms run in FP64 or FP32; use GETT (id 0) for tensor-core dtypes");
+    tc_status s = ensure_device_resources(p, nest_workspace_bytes(p, alg));
+    if (s != TC_SUCCESS) return s;
+    p.last_stream = stream;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p.dtype == TC_F64)
+        return run_nest<double>(p, alg, *(const double *)alpha, (const double *)A,
+                                (const double *)B, *(const double *)beta, (double *)C, st);
+    return run_nest<float>(p, alg, *(const float *)alpha, (const float *)A, (const float *)B,
+                           *(const float *)beta, (float *)C, st);
+}
+
+tc_status exec_gett_simt(Plan &p, const void *alpha, const void *A, const void *B,
+                         const void *beta, void *C, void *stream) {
+    tc_status s = ensure_device_resources(p, 0);
+    if (s != TC_SUCCESS) return s;
+    p.last_stream = stream;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p.dtype == TC_F64)
+        return run_gett_simt<double>(p, *(const double *)alpha, (const double *)A,
+                                     (const double *)B, *(const double *)beta, (double *)C, st);
+    return run_gett_simt<float>(p, *(const float *)alpha, (const float *)A, (const float *)B,
+                                *(const float *)beta, (float *)C, st);
+}
+
+}  // namespace tc

@@ -1,0 +1,91 @@
+// Internal declarations shared by the host planner (tc_plan.cpp) and the
+// device executors (*.cu).  Not part of the public ABI (include/tc.h).
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "tc.h"
+
+namespace tc {
+
+constexpr int kMaxModes = 8;    // modes per operand
+constexpr int kMaxIdx = 24;     // distinct indices per spec
+
+enum OperandId { OP_A = 0, OP_B = 1, OP_C = 2 };
+
+enum IndexClass { CLS_FREE_A = 0, CLS_FREE_B = 1, CLS_CONTRACTED = 2 };
+
+struct Layout {
+    int n = 0;                    // number of modes
+    int idx[kMaxModes] = {};      // index id of each mode, storage order
+    int64_t stride[kMaxModes] = {};
+    bool has(int id) const {
+        for (int m = 0; m < n; ++m)
+            if (idx[m] == id) return true;
+        return false;
+    }
+    int64_t stride_of(int id) const {
+        for (int m = 0; m < n; ++m)
+            if (idx[m] == id) return stride[m];
+        return 0;
+    }
+};
+
+struct Algorithm {
+    tc_algorithm pub{};
+    int kernel = 0;                 // tc_kernel
+    int nk = 0;
+    int kidx[3] = {-1, -1, -1};     // kernel indices by role
+    int nloops = 0;
+    int loops[kMaxIdx] = {};        // sliced index ids, outermost first
+    int copy_level[3] = {-2, -2, -2};
+    int q = -1;                     // deepest contracted loop enclosing a free loop
+};
+
+struct Plan {
+    std::string spec;
+    tc_dtype dtype = TC_F64;
+    int nidx = 0;
+    char letter[kMaxIdx] = {};
+    int64_t ext[kMaxIdx] = {};
+    int cls[kMaxIdx] = {};
+    Layout op[3];                   // A, B, C
+    std::vector<int> contracted, freeA, freeB;  // first-appearance order
+    std::vector<Algorithm> algs;    // algs[0] is the fused GETT
+    int selected = 0;
+    int split_products = 6;         // TC_BF16X3: 3, 6 or 9 slice products
+    // device resources, created lazily by the first execute
+    int device = -1;
+    void *workspace = nullptr;
+    size_t workspace_bytes = 0;
+    int *dev_status = nullptr;      // bounded-wait status word
+    void *last_stream = nullptr;
+    void *gett_state = nullptr;     // owned by the GETT executor
+};
+
+// error reporting (thread-local message)
+tc_status fail(tc_status st, const std::string &msg);
+
+// element size of A/B and of C for a dtype
+size_t elem_bytes_ab(tc_dtype dt);
+size_t elem_bytes_c(tc_dtype dt);
+
+// device-side executors (tc_exec.cu, tc_gett.cu)
+tc_status exec_nest(Plan &p, const Algorithm &alg, const void *alpha,
+                    const void *A, const void *B, const void *beta, void *C,
+                    void *stream);
+size_t nest_workspace_bytes(const Plan &p, const Algorithm &alg);
+tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B,
+                    const void *beta, void *C, void *stream);
+size_t gett_workspace_bytes(const Plan &p);
+void gett_release(Plan &p);
+tc_status ensure_device_resources(Plan &p, size_t workspace_bytes);
+
+}  // namespace tc
+
+struct tc_plan_s {
+    tc::Plan p;
+};

@@ -1,0 +1,233 @@
+"""Thin ctypes binding of the C ABI in include/tc.h (argument marshalling
+only: every step of the contraction runs in the CUDA library).
+
+The functions carry the C names (``tc_plan_create``, ``tc_execute``, ...);
+``Plan`` wraps a plan handle.  Device buffers are passed as integers or as
+objects with ``data_ptr()`` (torch tensors); streams as integers or objects
+with ``cuda_stream`` / ``stream_id`` (torch streams).  The library is loaded
+on first use; a missing library raises ``RuntimeError`` -- there is no
+fallback.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtc.so")
+
+TC_SUCCESS = 0
+STATUS_NAMES = {
+    0: "TC_SUCCESS", 1: "TC_ERROR_INVALID_SPEC", 2: "TC_ERROR_INVALID_EXTENT",
+    3: "TC_ERROR_INVALID_STRIDE", 4: "TC_ERROR_UNSUPPORTED_DTYPE",
+    5: "TC_ERROR_INVALID_ALGORITHM", 6: "TC_ERROR_OUT_OF_MEMORY",
+    7: "TC_ERROR_CUDA", 8: "TC_ERROR_TIMEOUT", 9: "TC_ERROR_INVALID_ARGUMENT",
+    10: "TC_ERROR_ADMISSION",
+}
+DTYPES = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3, "f16": 4, "bf16x3": 5}
+KERNELS = ("dot", "axpy", "gemv", "ger", "gemm", "gett")
+
+
+class TcError(RuntimeError):
+    def __init__(self, status, where, message=""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}"
+                         + (f" ({message})" if message else ""))
+
+
+class tc_algorithm(ctypes.Structure):
+    _fields_ = [
+        ("id", ctypes.c_int32),
+        ("name", ctypes.c_char * 32),
+        ("kernel", ctypes.c_int32),
+        ("n_loops", ctypes.c_int32),
+        ("loops", ctypes.c_char * 8),
+        ("n_kernel_indices", ctypes.c_int32),
+        ("kernel_indices", ctypes.c_char * 4),
+        ("copy_mask", ctypes.c_uint32),
+        ("copy_level", ctypes.c_int32 * 3),
+        ("n_phases", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+# name -> (restype, argtypes); mirrors include/tc.h
+_VP, _I64P, _I32P = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)
+SIGNATURES = {
+    "tc_plan_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_char_p, _I64P, _I64P, ctypes.c_int]),
+    "tc_plan_destroy": (ctypes.c_int, [_VP]),
+    "tc_algorithm_count": (ctypes.c_int, [_VP, _I32P]),
+    "tc_enumerate_algorithms": (ctypes.c_int, [_VP, ctypes.POINTER(tc_algorithm), ctypes.c_int32, _I32P]),
+    "tc_plan_select": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "tc_plan_selected": (ctypes.c_int, [_VP, _I32P]),
+    "tc_algorithm_workspace": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    "tc_execute": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "tc_plan_device_status": (ctypes.c_int, [_VP]),
+    "tc_plan_flops": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "tc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "tc_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load(path=LIB_PATH):
+    """Load libtc.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libtc.so not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status, where):
+    if status != TC_SUCCESS:
+        msg = load().tc_last_error().decode(errors="replace")
+        raise TcError(status, where, msg)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return int(x)
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    for attr in ("cuda_stream", "stream_id"):
+        if hasattr(s, attr):
+            return int(getattr(s, attr))
+    return int(s)
+
+
+def _i64(vals):
+    if vals is None:
+        return None
+    vals = [int(v) for v in vals]
+    return (ctypes.c_int64 * len(vals))(*vals)
+
+
+def _scalar(value, dtype):
+    return ctypes.c_double(value) if dtype == "f64" else ctypes.c_float(value)
+
+
+# ---------------------------------------------------------------- C names
+def tc_plan_create(spec, extents, strides=None, dtype="f64"):
+    h = ctypes.c_void_p()
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    _check(load().tc_plan_create(ctypes.byref(h), spec.encode(), _i64(extents),
+                                 _i64(strides), dt), "tc_plan_create")
+    return h
+
+
+def tc_plan_destroy(plan):
+    _check(load().tc_plan_destroy(plan), "tc_plan_destroy")
+
+
+def tc_enumerate_algorithms(plan):
+    n = ctypes.c_int32()
+    _check(load().tc_enumerate_algorithms(plan, None, 0, ctypes.byref(n)), "tc_enumerate_algorithms")
+    buf = (tc_algorithm * n.value)()
+    _check(load().tc_enumerate_algorithms(plan, buf, n.value, ctypes.byref(n)), "tc_enumerate_algorithms")
+    out = []
+    for a in buf:
+        out.append({
+            "id": a.id,
+            "name": a.name.decode(),
+            "kernel": KERNELS[a.kernel],
+            "loops": tuple(chr(c) for c in a.loops[:a.n_loops]),
+            "kernel_indices": tuple(chr(c) for c in a.kernel_indices[:a.n_kernel_indices]),
+            "copy_mask": a.copy_mask,
+            "copy_level": tuple(a.copy_level),
+            "n_phases": a.n_phases,
+        })
+    return out
+
+
+def tc_plan_select(plan, alg_id):
+    _check(load().tc_plan_select(plan, int(alg_id)), "tc_plan_select")
+
+
+def tc_plan_selected(plan):
+    v = ctypes.c_int32()
+    _check(load().tc_plan_selected(plan, ctypes.byref(v)), "tc_plan_selected")
+    return v.value
+
+
+def tc_algorithm_workspace(plan, alg_id):
+    v = ctypes.c_size_t()
+    _check(load().tc_algorithm_workspace(plan, int(alg_id), ctypes.byref(v)), "tc_algorithm_workspace")
+    return v.value
+
+
+def tc_execute(plan, alpha, A, B, beta, C, stream=None, dtype="f64"):
+    a, b = _scalar(alpha, dtype), _scalar(beta, dtype)
+    _check(load().tc_execute(plan, ctypes.addressof(a), _ptr(A), _ptr(B), ctypes.addressof(b),
+                             _ptr(C), _stream(stream)), "tc_execute")
+
+
+def tc_plan_device_status(plan):
+    _check(load().tc_plan_device_status(plan), "tc_plan_device_status")
+
+
+def tc_plan_flops(plan):
+    v = ctypes.c_double()
+    _check(load().tc_plan_flops(plan, ctypes.byref(v)), "tc_plan_flops")
+    return v.value
+
+
+def tc_status_string(status):
+    return load().tc_status_string(int(status)).decode()
+
+
+# ---------------------------------------------------------------- convenience
+class Plan:
+    """Owns one plan handle (destroyed on close / garbage collection)."""
+
+    def __init__(self, spec, extents, strides=None, dtype="f64"):
+        self.spec, self.extents, self.dtype = spec, list(extents), dtype
+        self.handle = tc_plan_create(spec, extents, strides, dtype)
+
+    def algorithms(self):
+        return tc_enumerate_algorithms(self.handle)
+
+    def select(self, alg_id):
+        tc_plan_select(self.handle, alg_id)
+
+    @property
+    def selected(self):
+        return tc_plan_selected(self.handle)
+
+    def workspace(self, alg_id):
+        return tc_algorithm_workspace(self.handle, alg_id)
+
+    def execute(self, A, B, C, alpha=1.0, beta=0.0, stream=None):
+        tc_execute(self.handle, alpha, A, B, beta, C, stream, self.dtype)
+
+    def device_status(self):
+        tc_plan_device_status(self.handle)
+
+    @property
+    def flops(self):
+        return tc_plan_flops(self.handle)
+
+    def close(self):
+        if self.handle is not None and _lib is not None:
+            tc_plan_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

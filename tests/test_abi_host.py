@@ -1,0 +1,117 @@
+"""Host-side checks of the C ABI (no GPU): the library loads and exports
+every declared entry point, the planner rejects malformed input, and its
+algorithm generator agrees exactly with the oracle's (integer work)."""
+import ctypes
+
+import pytest
+
+import __graft_entry__
+from oracle import algorithms as oa
+from paper_1409_8608_gb300 import tc
+from tests.abi_util import declared_functions
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build_library()
+    return tc.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "tc_execute" in names and "tc_plan_create" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header(lib):
+    for name in declared_functions():
+        assert name in tc.SIGNATURES or hasattr(tc, name), name
+
+
+@pytest.mark.parametrize("spec,extents", [
+    ("abc=ai,ibc", [8, 9, 10, 4]),
+    ("abc=iaj,jbic", [6, 5, 4, 3, 2]),
+    ("abc=ija,jbic", [6, 5, 4, 3, 2]),
+    ("ab=aij,jib", [7, 6, 3, 2]),
+    ("a=iaj,ji", [5, 4, 3]),
+    ("ab=ai,ib", [3, 4, 5]),
+    ("abcd=iabj,jcid", [2, 3, 4, 5, 2, 3]),
+])
+def test_enumeration_matches_oracle(lib, spec, extents):
+    plan = tc.Plan(spec, extents)
+    got = plan.algorithms()
+    want = oa.enumerate_algorithms(spec, extents)
+    assert got[0]["name"] == "gett" and got[0]["kernel"] == "gett"
+    assert len(got) == len(want) + 1
+    for g, w in zip(got[1:], want):
+        assert g["id"] == w["id"] + 1
+        assert g["name"] == w["name"]
+        assert g["kernel"] == w["kernel"]
+        assert g["loops"] == w["loops"]
+        assert g["kernel_indices"] == w["kernel_indices"]
+        lv = {op: g["copy_level"][k] for k, op in enumerate("ABC") if g["copy_level"][k] != -2}
+        assert lv == w["copies"], g["name"]
+    plan.close()
+
+
+def test_strided_copy_decision_matches_oracle(lib):
+    strides = [1, 4, 2, 8, 1, 3]
+    plan = tc.Plan("ab=ai,ib", [4, 5, 3], strides=strides)
+    got = plan.algorithms()
+    want = oa.enumerate_algorithms("ab=ai,ib", [4, 5, 3], strides=strides)
+    assert [g["name"] for g in got[1:]] == [w["name"] for w in want]
+    plan.close()
+
+
+def test_phase_counts(lib):
+    plan = tc.Plan("abc=iaj,jbic", [64, 64, 64, 16, 16])
+    algs = {a["name"]: a for a in plan.algorithms()}
+    # i'c-gemm: the copy loop i encloses the free loop c -> 16 phases
+    assert algs["i'c-gemm"]["n_phases"] == 16
+    # ci'-gemm: the contracted loop is innermost -> one phase
+    assert algs["ci'-gemm"]["n_phases"] == 1
+    assert algs["gett"]["n_phases"] == 1
+    plan.close()
+
+
+@pytest.mark.parametrize("spec,extents,strides,status", [
+    ("abc", [1, 2, 3], None, "TC_ERROR_INVALID_SPEC"),
+    ("abc=ai,ibc,x", [1, 2, 3, 4], None, "TC_ERROR_INVALID_SPEC"),
+    ("abc=aic,ibc", [2, 2, 2, 2], None, "TC_ERROR_INVALID_SPEC"),      # batch index c
+    ("ab=aik,ib", [2, 2, 2, 2], None, "TC_ERROR_INVALID_SPEC"),       # k in A only
+    ("ab=aai,ib", [2, 2, 2], None, "TC_ERROR_INVALID_SPEC"),          # repeated index
+    ("aB=ai,iB", [2, 2, 2], None, "TC_ERROR_INVALID_SPEC"),           # not a-z
+    ("ab=ai,ib", [2, 0, 2], None, "TC_ERROR_INVALID_EXTENT"),
+    ("ab=ai,ib", [2, 3, 2], [1, 1, 1, 2, 1, 2], "TC_ERROR_INVALID_STRIDE"),  # C overlaps
+    ("ab=ai,ib", [2, 3, 2], [1, 2, 0, 2, 1, 2], "TC_ERROR_INVALID_STRIDE"),  # zero stride
+])
+def test_rejections(lib, spec, extents, strides, status):
+    with pytest.raises(tc.TcError) as e:
+        tc.tc_plan_create(spec, extents, strides)
+    assert tc.STATUS_NAMES[e.value.status] == status
+
+
+def test_status_strings_and_null_arguments(lib):
+    for code in tc.STATUS_NAMES:
+        assert tc.tc_status_string(code)
+    assert lib.tc_plan_destroy(None) == 0
+    assert lib.tc_plan_select(None, 0) == 9
+    plan = tc.Plan("abc=ai,ibc", [4, 4, 4, 2])
+    with pytest.raises(tc.TcError):
+        plan.select(999)
+    # NULL operands are rejected before any device work
+    a = ctypes.c_double(1.0)
+    st = lib.tc_execute(plan.handle, ctypes.addressof(a), None, None, ctypes.addressof(a), None, None)
+    assert st == 9
+    plan.close()
+
+
+def test_flops_and_workspace(lib):
+    plan = tc.Plan("abc=iaj,jbic", [8, 8, 8, 4, 4])
+    assert plan.flops == 2 * 8 * 8 * 8 * 4 * 4
+    algs = {a["name"]: a["id"] for a in plan.algorithms()}
+    assert plan.workspace(algs["cab" + "j-dot"] if "cabj-dot" in algs else 1) == 0
+    # i'c-gemm copies A[i,:,:] (a x j doubles) once per phase
+    assert plan.workspace(algs["i'c-gemm"]) == ((8 * 4 * 8 + 255) // 256) * 256
+    plan.close()
