@@ -1,0 +1,337 @@
+"""Benchmark: contraction throughput on one GB300 (or N replicas).
+
+Workload: C[a,b,c] = sum_{i,j} A[i,a,j] * B[j,b,i,c] with a = b = c = 512 and
+i = j = 16 (the permuted plain workload, dense column-major, entries uniform
+in [-1, 1]).  One step = one tc_execute of the selected algorithm over
+inputs already resident in HBM (1.6 GB in FP64, larger than the 129 MB L2,
+so no flush is needed between steps).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype f64|f32]
+                    [--alg gett|<name>] [--impl reference]
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
+host cores instead (a bounded slab of the same workload per step).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SPEC = "abc=iaj,jbic"
+N_FREE, N_CONTR = 512, 16
+EXTENTS = [N_FREE, N_FREE, N_FREE, N_CONTR, N_CONTR]
+WORKLOAD = "abc=iaj,jbic a=b=c=512 i=j=16 uniform[-1,1]"
+METRIC = "contraction GFLOP/s (abc=iaj,jbic, a=b=c=512, i=j=16)"
+
+
+def set_free_extent(n):
+    """Smaller cases of the same workload (profiling captures only)."""
+    global N_FREE, EXTENTS, WORKLOAD
+    N_FREE = n
+    EXTENTS = [n, n, n, N_CONTR, N_CONTR]
+    WORKLOAD = f"abc=iaj,jbic a=b=c={n} i=j=16 uniform[-1,1]"
+SMS = 152
+SM_MAX_MHZ = 2070.0
+# FP64: 2 DFMA per SM per clock (measured 1.20 TFLOP/s at 1.97 GHz); FP32: 128 FFMA.
+ALU_PEAK_TFLOPS = {"f64": SMS * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12,
+                   "f32": SMS * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12}
+
+
+def flops_of(extents):
+    f = 2.0
+    for e in extents:
+        f *= e
+    return f
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "fallback": True}
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[2:6]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_sample(target_s=12.0, threads=None):
+    """Times the FP64 oracle on a slab of the workload (last C mode c)."""
+    from oracle import contraction as oc
+    from paper_1409_8608_gb300 import synth
+    cores = threads or len(os.sched_getaffinity(0))
+    cores = min(cores, oc.max_threads()) if oc.max_threads() > 0 else cores
+    A, B, _ = synth.uniform_operands(SPEC, EXTENTS, seed=0)
+    C = np.zeros(N_FREE ** 3)
+    # calibrate on one c slice, then size the slab for ~target_s
+    t0 = time.perf_counter()
+    oc.contract(SPEC, EXTENTS, A, B, C=C, outer_range=(0, cores), threads=cores)
+    t1 = time.perf_counter() - t0
+    per_slice = max(t1 / cores, 1e-5)
+    nsl = int(max(cores, min(N_FREE, target_s / per_slice)))
+    nsl = min(N_FREE, max(1, nsl))
+    return A, B, C, cores, nsl
+
+
+def run_reference(args):
+    from oracle import contraction as oc
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    target = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    A, B, C, cores, nsl = cpu_oracle_sample(target_s=target)
+    f_slab = flops_of([N_FREE, N_FREE, nsl, N_CONTR, N_CONTR])
+    for _ in range(args.warmup):
+        oc.contract(SPEC, EXTENTS, A, B, C=C, outer_range=(0, nsl), threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oc.contract(SPEC, EXTENTS, A, B, C=C, outer_range=(0, nsl), threads=cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = f_slab * args.steps / total / 1e9
+    sample = f"c-slab of {nsl} of {N_FREE} slices ({f_slab / 1e9:.2f} GFLOP) per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "FP64 CPU oracle (plain nested loops, OpenMP)",
+                   "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import __graft_entry__
+    from paper_1409_8608_gb300 import synth, tc
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+        dist = None
+    if rank == 0 or world == 1:
+        __graft_entry__.build_library()
+    if dist is not None:
+        dist.barrier()
+    tc.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+
+    dtype = args.dtype
+    tdt = {"f64": torch.float64, "f32": torch.float32}[dtype]
+    A, B, _ = synth.uniform_operands(SPEC, EXTENTS, seed=rank)
+    nC = N_FREE ** 3
+    plan = tc.Plan(SPEC, EXTENTS, dtype=dtype)
+    algs = {a["name"]: a for a in plan.algorithms()}
+    alg = algs[args.alg]
+    plan.select(alg["id"])
+    hA = torch.from_numpy(A).to(tdt).pin_memory()
+    hB = torch.from_numpy(B).to(tdt).pin_memory()
+    hC = torch.empty(nC, dtype=tdt).pin_memory()
+    dA = hA.to(dev)
+    dB = hB.to(dev)
+    dC = torch.empty(nC, dtype=tdt, device=dev)
+    flops = plan.flops
+    launches_per_step = 1 if alg["kernel"] == "gett" else alg["n_phases"] + sum(
+        1 for lv in alg["copy_level"] if lv != -2) * alg["n_phases"]
+
+    def step():
+        plan.execute(dA, dB, dC, alpha=1.0, beta=0.0, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    plan.device_status()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_begin = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_begin.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    plan.device_status()
+    total_ms = t_begin.elapsed_time(t_end)
+    per_launch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev) / max(1, launches_per_step)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = flops * args.steps * world / (total_ms / 1e3) / 1e9
+
+    # end to end through the public call: pinned host inputs -> device,
+    # execute, result back to pinned host memory, every step
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            dA.copy_(hA, non_blocking=True)
+            dB.copy_(hB, non_blocking=True)
+            step()
+            hC.copy_(dC, non_blocking=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_value = flops * world / (e2e_ms / 1e3) / 1e9
+
+    peaks = measured_peaks()
+    achieved_tf = flops / (per_launch_ms * launches_per_step / 1e3) / 1e12
+    peak_tf = ALU_PEAK_TFLOPS[dtype]
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved_tf / peak_tf, "traffic": None,
+                "kernel": "tile_kernel" if alg["kernel"] in ("gett", "gemm") else "elementwise_kernel",
+                "peak_source": f"derived: 152 SMs x {'2 DFMA' if dtype == 'f64' else '128 FFMA'}/clk x 2 x 2070 MHz"}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu:
+            from oracle import contraction as oc
+            A64, B64, C64, cores, nsl = cpu_oracle_sample(target_s=args.cpu_seconds)
+            t0 = time.perf_counter()
+            oc.contract(SPEC, EXTENTS, A64, B64, C=C64, outer_range=(0, nsl), threads=cores)
+            dt = time.perf_counter() - t0
+            fs = flops_of([N_FREE, N_FREE, nsl, N_CONTR, N_CONTR])
+            cpu = {"value": fs / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                   "sample": f"FP64 oracle on a slab of c = {nsl} of {N_FREE} ({fs / 1e9:.2f} GFLOP, {dt:.1f} s)"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "algorithm": alg["name"], "form": f"plain {dtype}",
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (no flush needed)"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "GFLOP/s",
+                    "h2d_bytes_per_step": int(hA.numel() * hA.element_size() + hB.numel() * hB.element_size()),
+                    "d2h_bytes_per_step": int(hC.numel() * hC.element_size())},
+            "gpu_launches": int(args.steps * launches_per_step),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--alg", default="gett")
+    ap.add_argument("--impl", default="tc", choices=["tc", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--n", type=int, default=512, help="free extent a=b=c (512 = the workload)")
+    args = ap.parse_args()
+    if args.n != 512:
+        set_free_extent(args.n)
+    if args.warmup < 3 and args.impl == "tc":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
