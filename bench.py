@@ -199,20 +199,62 @@ def run_gpu(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(device=dev)
 
-    dtype = args.dtype
-    tdt = {"f64": torch.float64, "f32": torch.float32}[dtype]
     A, B, _ = synth.uniform_operands(SPEC, EXTENTS, seed=rank)
+    res = measure_form(args, args.dtype, args.alg, A, B, dev, stream, dist, world, tc)
+    plain = None
+    if args.dtype != "f64" and not args.no_plain:
+        plain = measure_form(args, "f64", "gett", A, B, dev, stream, dist, world, tc,
+                             steps=min(args.steps, 5), e2e=False)
+    if rank == 0:
+        line = dict(res["line"])
+        line["n_gpus"] = world
+        if plain is not None:
+            pl = plain["line"]
+            line["plain_f64"] = {"value": pl["value"], "unit": "GFLOP/s", "algorithm": "gett",
+                                 "ms_per_step": pl["ms_per_step"], "roofline": pl["roofline"],
+                                 "speedup_of_chosen": line["value"] / pl["value"]}
+        if world == 1 and not args.no_cpu:
+            from oracle import contraction as oc
+            A64, B64, C64, cores, nsl = cpu_oracle_sample(target_s=args.cpu_seconds)
+            t0 = time.perf_counter()
+            oc.contract(SPEC, EXTENTS, A64, B64, C=C64, outer_range=(0, nsl), threads=cores)
+            dt = time.perf_counter() - t0
+            fs = flops_of([N_FREE, N_FREE, nsl, N_CONTR, N_CONTR])
+            line["cpu_baseline"] = {
+                "value": fs / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                "sample": f"FP64 oracle on a slab of c = {nsl} of {N_FREE} ({fs / 1e9:.2f} GFLOP, {dt:.1f} s)"}
+        else:
+            line["cpu_baseline"] = None
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+TORCH_IN = {"f64": "float64", "f32": "float32", "tf32": "float32", "bf16x3": "float32",
+            "bf16": "bfloat16", "f16": "float16"}
+TENSOR_FORMS = ("tf32", "bf16", "f16", "bf16x3")
+
+
+def measure_form(args, dtype, alg_name, A, B, dev, stream, dist, world, tc, steps=None, e2e=True):
+    """Times one form (dtype + algorithm) of the workload; returns its line."""
+    import torch
+    steps = steps or args.steps
+    tin = getattr(torch, TORCH_IN[dtype])
+    tout = torch.float64 if dtype == "f64" else torch.float32
     nC = N_FREE ** 3
     plan = tc.Plan(SPEC, EXTENTS, dtype=dtype)
+    if dtype == "bf16x3":
+        plan.set_split(args.products)
     algs = {a["name"]: a for a in plan.algorithms()}
-    alg = algs[args.alg]
+    alg = algs[alg_name]
     plan.select(alg["id"])
-    hA = torch.from_numpy(A).to(tdt).pin_memory()
-    hB = torch.from_numpy(B).to(tdt).pin_memory()
-    hC = torch.empty(nC, dtype=tdt).pin_memory()
+    hA = torch.from_numpy(A).to(tin).pin_memory()
+    hB = torch.from_numpy(B).to(tin).pin_memory()
+    hC = torch.empty(nC, dtype=tout).pin_memory()
     dA = hA.to(dev)
     dB = hB.to(dev)
-    dC = torch.empty(nC, dtype=tdt, device=dev)
+    dC = torch.empty(nC, dtype=tout, device=dev)
     flops = plan.flops
     launches_per_step = 1 if alg["kernel"] == "gett" else alg["n_phases"] + sum(
         1 for lv in alg["copy_level"] if lv != -2) * alg["n_phases"]
@@ -223,18 +265,19 @@ def run_gpu(args):
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
+    args_steps = steps
     torch.cuda.synchronize()
     plan.device_status()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+          for _ in range(args_steps)]
     with ClockSampler(torch.cuda.current_device()) as clk:
         t_begin = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
         t_begin.record(stream)
-        for k in range(args.steps):
+        for k in range(args_steps):
             ev[k][0].record(stream)
             step()
             ev[k][1].record(stream)
@@ -250,12 +293,12 @@ def run_gpu(args):
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = flops * args.steps * world / (total_ms / 1e3) / 1e9
+    ms_per_step = total_ms / args_steps
+    value = flops * args_steps * world / (total_ms / 1e3) / 1e9
 
     # end to end through the public call: pinned host inputs -> device,
     # execute, result back to pinned host memory, every step
-    e2e_steps = max(2, min(args.steps, 5))
+    e2e_steps = max(2, min(args_steps, 5)) if e2e else 0
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -268,48 +311,49 @@ def run_gpu(args):
             hC.copy_(dC, non_blocking=True)
         e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    e2e_value = flops * world / (e2e_ms / 1e3) / 1e9
+    e2e_value = None
+    if e2e_steps:
+        e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        e2e_value = flops * world / (e2e_ms / 1e3) / 1e9
 
     peaks = measured_peaks()
-    achieved_tf = flops / (per_launch_ms * launches_per_step / 1e3) / 1e12
-    peak_tf = ALU_PEAK_TFLOPS[dtype]
-    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": achieved_tf / peak_tf, "traffic": None,
-                "kernel": "tile_kernel" if alg["kernel"] in ("gett", "gemm") else "elementwise_kernel",
-                "peak_source": f"derived: 152 SMs x {'2 DFMA' if dtype == 'f64' else '128 FFMA'}/clk x 2 x 2070 MHz"}
-
-    if rank == 0:
-        cpu = None
-        if world == 1 and not args.no_cpu:
-            from oracle import contraction as oc
-            A64, B64, C64, cores, nsl = cpu_oracle_sample(target_s=args.cpu_seconds)
-            t0 = time.perf_counter()
-            oc.contract(SPEC, EXTENTS, A64, B64, C=C64, outer_range=(0, nsl), threads=cores)
-            dt = time.perf_counter() - t0
-            fs = flops_of([N_FREE, N_FREE, nsl, N_CONTR, N_CONTR])
-            cpu = {"value": fs / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-                   "sample": f"FP64 oracle on a slab of c = {nsl} of {N_FREE} ({fs / 1e9:.2f} GFLOP, {dt:.1f} s)"}
-        line = {
-            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": dtype, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "algorithm": alg["name"], "form": f"plain {dtype}",
-                       "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (no flush needed)"},
-            "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "GFLOP/s",
-                    "h2d_bytes_per_step": int(hA.numel() * hA.element_size() + hB.numel() * hB.element_size()),
-                    "d2h_bytes_per_step": int(hC.numel() * hC.element_size())},
-            "gpu_launches": int(args.steps * launches_per_step),
-            "clocks": clk.summary(),
-        }
-        print(json.dumps(line), flush=True)
+    launch_s = per_launch_ms * launches_per_step / 1e3
+    if dtype in TENSOR_FORMS:
+        products = args.products if dtype == "bf16x3" else 1
+        work = flops * products
+        peak_tf = peaks["bf16_tflops"] * (0.5 if dtype == "tf32" else 1.0)
+        achieved_tf = work / launch_s / 1e12
+        roofline = {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": achieved_tf / peak_tf, "traffic": None, "kernel": "gett_tc_kernel",
+                    "work": f"{products} slice products x 2*prod(extents) = {work / 1e9:.1f} GFLOP per launch",
+                    "peak_source": "MEASURED_PEAKS bf16_tflops (burst)" + (" x 0.5 (TF32 nominal ratio)" if dtype == "tf32" else "")
+                    + (" (fallback)" if peaks.get("fallback") else " (measured)")}
+    else:
+        achieved_tf = flops / launch_s / 1e12
+        peak_tf = ALU_PEAK_TFLOPS[dtype]
+        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": achieved_tf / peak_tf, "traffic": None,
+                    "kernel": "tile_kernel" if alg["kernel"] in ("gett", "gemm") else "elementwise_kernel",
+                    "peak_source": f"derived: 152 SMs x {'2 DFMA' if dtype == 'f64' else '128 FFMA'}/clk x 2 x 2070 MHz"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args_steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "algorithm": alg["name"],
+                   "form": ("split-BF16 x%d products, FP32 I/O" % args.products) if dtype == "bf16x3" else f"{dtype}",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (no flush needed)"},
+        "roofline": roofline,
+        "e2e": None if e2e_value is None else {
+            "value": e2e_value, "unit": "GFLOP/s",
+            "h2d_bytes_per_step": int(hA.numel() * hA.element_size() + hB.numel() * hB.element_size()),
+            "d2h_bytes_per_step": int(hC.numel() * hC.element_size())},
+        "gpu_launches": int(args_steps * launches_per_step),
+        "clocks": clk.summary(),
+    }
     plan.close()
-    if dist is not None:
-        dist.destroy_process_group()
-    return 0
+    return {"line": line}
 
 
 def main():
@@ -317,7 +361,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--dtype", default="bf16x3", choices=["f64", "f32", "tf32", "bf16", "f16", "bf16x3"])
+    ap.add_argument("--products", type=int, default=6)
+    ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--alg", default="gett")
     ap.add_argument("--impl", default="tc", choices=["tc", "reference"])
     ap.add_argument("--no-cpu", action="store_true")

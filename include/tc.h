@@ -155,6 +155,11 @@ tc_status tc_execute(tc_plan plan, const void *alpha, const void *A,
  * the plan last ran on): TC_SUCCESS or TC_ERROR_TIMEOUT. */
 tc_status tc_plan_device_status(tc_plan plan);
 
+/* TC_BF16X3 plans: number of BF16 slice products kept per multiply,
+ * 3 (weights 1, 2^-8), 6 (adds 2^-16, the default) or 9 (all).  Other
+ * values give TC_ERROR_INVALID_ARGUMENT; other dtypes ignore the setting. */
+tc_status tc_plan_set_split(tc_plan plan, int32_t products);
+
 /* 2 * product of all extents. */
 tc_status tc_plan_flops(tc_plan plan, double *flops);
 

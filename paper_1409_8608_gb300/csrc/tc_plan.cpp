@@ -388,6 +388,14 @@ tc_status tc_algorithm_workspace(tc_plan plan, int32_t alg_id, size_t *bytes) {
     return TC_SUCCESS;
 }
 
+tc_status tc_plan_set_split(tc_plan plan, int32_t products) {
+    if (!plan) return fail(TC_ERROR_INVALID_ARGUMENT, "plan is NULL");
+    if (products != 3 && products != 6 && products != 9)
+        return fail(TC_ERROR_INVALID_ARGUMENT, "split products must be 3, 6 or 9");
+    plan->p.split_products = products;
+    return TC_SUCCESS;
+}
+
 tc_status tc_plan_flops(tc_plan plan, double *flops) {
     if (!plan || !flops) return fail(TC_ERROR_INVALID_ARGUMENT, "NULL argument");
     double f = 2.0;

@@ -63,6 +63,7 @@ SIGNATURES = {
     "tc_execute": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "tc_plan_device_status": (ctypes.c_int, [_VP]),
     "tc_plan_flops": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "tc_plan_set_split": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tc_last_error": (ctypes.c_char_p, []),
 }
@@ -180,6 +181,10 @@ def tc_plan_device_status(plan):
     _check(load().tc_plan_device_status(plan), "tc_plan_device_status")
 
 
+def tc_plan_set_split(plan, products):
+    _check(load().tc_plan_set_split(plan, int(products)), "tc_plan_set_split")
+
+
 def tc_plan_flops(plan):
     v = ctypes.c_double()
     _check(load().tc_plan_flops(plan, ctypes.byref(v)), "tc_plan_flops")
@@ -213,6 +218,9 @@ class Plan:
 
     def execute(self, A, B, C, alpha=1.0, beta=0.0, stream=None):
         tc_execute(self.handle, alpha, A, B, beta, C, stream, self.dtype)
+
+    def set_split(self, products):
+        tc_plan_set_split(self.handle, products)
 
     def device_status(self):
         tc_plan_device_status(self.handle)

@@ -1,0 +1,175 @@
+"""GPU parity of the tensor-core GETT (algorithm 0; tcgen05 + TMEM) for the
+TF32, BF16, FP16 and split-BF16 (BF16X3) dtypes against the FP64 oracle.
+
+Bounds: integer inputs in [-8, 8] are exact in every input format and their
+sums stay exact in the FP32 accumulator, so those results must be bit-exact.
+For uniform inputs the oracle runs on the inputs as the kernel sees them
+(rounded to BF16 / FP16, TF32-rounded to nearest with ties away), and the
+only error left is the FP32 accumulation, bounded componentwise by
+gamma(K+1) * (|A||B|) with u = 2**-24.  For BF16X3 the oracle runs on the
+FP32 inputs; the 6-product split adds at most about 3 * 2**-24 per term
+(the dropped slice products and the split remainder), so the bound is
+(K + 4) * 2**-24 * (|A||B|)."""
+import numpy as np
+import pytest
+
+from oracle import contraction as oc
+from paper_1409_8608_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def tcmod():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1409_8608_gb300 import tc
+    tc.load()
+    return tc
+
+
+def tf32_rna(x):
+    """Round FP32 to TF32 (10 mantissa bits), nearest with ties away."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return b.view(np.float32).astype(np.float64)
+
+
+def device_inputs(dtype, A, B):
+    dev = torch.device("cuda:0")
+    if dtype == "bf16":
+        tA, tB = torch.from_numpy(A).to(torch.bfloat16), torch.from_numpy(B).to(torch.bfloat16)
+        seen = (tA.double().numpy(), tB.double().numpy())
+    elif dtype == "f16":
+        tA, tB = torch.from_numpy(A).to(torch.float16), torch.from_numpy(B).to(torch.float16)
+        seen = (tA.double().numpy(), tB.double().numpy())
+    else:
+        tA, tB = torch.from_numpy(A).float(), torch.from_numpy(B).float()
+        if dtype == "tf32":
+            seen = (tf32_rna(tA.numpy()), tf32_rna(tB.numpy()))
+        else:
+            seen = (tA.double().numpy(), tB.double().numpy())
+    return tA.to(dev), tB.to(dev), seen
+
+
+def run_gett(tc, spec, ext, dtype, dA, dB, C0=None, alpha=1.0, beta=0.0, products=None):
+    plan = tc.Plan(spec, ext, dtype=dtype)
+    if products is not None:
+        plan.set_split(products)
+    plan.select(0)
+    n = synth.dense_sizes(spec, ext)[0]
+    if C0 is None:
+        dC = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda:0")
+    else:
+        dC = torch.from_numpy(C0).float().to("cuda:0")
+    plan.execute(dA, dB, dC, alpha=alpha, beta=beta)
+    torch.cuda.synchronize()
+    plan.device_status()
+    plan.close()
+    return dC.double().cpu().numpy()
+
+
+def ksize(spec, ext):
+    c, a, b = oc.parse_spec(spec)
+    e = dict(zip(oc.index_order(spec), ext))
+    k = 1
+    for x in a:
+        if x in b and x not in c:
+            k *= e[x]
+    return k
+
+
+CASES = [
+    ("abc=ai,ibc", [200, 30, 20, 40]),        # 2 M tiles, 3 N tiles (ragged), K tail
+    ("abc=iaj,jbic", [130, 40, 9, 5, 7]),     # permuted operands, K = 35
+    ("ab=aij,jib", [257, 129, 16, 8]),        # M and N tails, K = 128
+    ("abc=ai,ibc", [64, 64, 64, 8]),          # the small plain shape, K < one stage
+]
+DTYPES = ["bf16", "f16", "tf32", "bf16x3"]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("spec,ext", CASES)
+def test_gett_exact_on_integers(tcmod, spec, ext, dtype):
+    A, B, _ = synth.integer_operands(spec, ext, seed=1)
+    want = oc.contract(spec, ext, A, B)
+    dA, dB, _ = device_inputs(dtype, A, B)
+    got = run_gett(tcmod, spec, ext, dtype, dA, dB)
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, (dtype, bad[:5], got[bad[:5]], want[bad[:5]])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("spec,ext", CASES)
+def test_gett_within_bound_on_uniform(tcmod, spec, ext, dtype):
+    A, B, _ = synth.uniform_operands(spec, ext, seed=0)
+    dA, dB, (Ar, Br) = device_inputs(dtype, A, B)
+    want = oc.contract(spec, ext, Ar, Br)
+    scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
+    K = ksize(spec, ext)
+    bound = (K + 4) * U32 if dtype == "bf16x3" else (K + 1) * U32 / (1 - (K + 1) * U32)
+    got = run_gett(tcmod, spec, ext, dtype, dA, dB)
+    err = float(np.max(np.abs(got - want) / scale))
+    assert err <= bound, (dtype, err, bound)
+
+
+def test_split_products_order_accuracy(tcmod):
+    # more slice products never hurt; 3 products stay below 2**-16
+    # relative, 6 and 9 reach the floor set by the FP32 accumulator
+    spec, ext = "ab=aij,jib", [256, 256, 16, 16]
+    A, B, _ = synth.uniform_operands(spec, ext, seed=3)
+    dA, dB, (Ar, Br) = device_inputs("bf16x3", A, B)
+    want = oc.contract(spec, ext, Ar, Br)
+    scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
+    errs = {}
+    for p in (3, 6, 9):
+        got = run_gett(tcmod, spec, ext, "bf16x3", dA, dB, products=p)
+        errs[p] = float(np.max(np.abs(got - want) / scale))
+    assert errs[3] < 4 * 2.0 ** -16
+    assert errs[6] <= (256 + 4) * U32 and errs[9] <= (256 + 4) * U32
+    assert errs[6] <= errs[3] and errs[9] <= 1.5 * errs[6]
+    with pytest.raises(tcmod.TcError):
+        tcmod.Plan(spec, ext, dtype="bf16x3").set_split(4)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "tf32", "bf16x3"])
+def test_gett_alpha_beta(tcmod, dtype):
+    spec, ext = "abc=iaj,jbic", [70, 33, 5, 6, 4]
+    A, B, C0 = synth.integer_operands(spec, ext, seed=2, with_c=True)
+    S = oc.contract(spec, ext, A, B)
+    dA, dB, _ = device_inputs(dtype, A, B)
+    for alpha, beta in ((2.0, 0.5), (-1.0, 1.0), (0.25, -2.0)):
+        got = run_gett(tcmod, spec, ext, dtype, dA, dB, C0=C0, alpha=alpha, beta=beta)
+        assert np.array_equal(got, alpha * S + beta * C0), (alpha, beta)
+
+
+def test_nest_algorithms_refuse_tensor_dtypes(tcmod):
+    plan = tcmod.Plan("abc=ai,ibc", [8, 8, 8, 4], dtype="bf16x3")
+    plan.select(1)
+    d = torch.zeros(512, device="cuda:0")
+    with pytest.raises(tcmod.TcError) as e:
+        plan.execute(d, d, d)
+    assert tcmod.STATUS_NAMES[e.value.status] == "TC_ERROR_UNSUPPORTED_DTYPE"
+    plan.close()
+
+
+def test_large_bench_shape_sampled(tcmod):
+    # the permuted plain workload at its full size (a=b=c=512, i=j=16) in
+    # BF16X3, checked on sampled outputs computed one by one
+    spec, ext = "abc=iaj,jbic", [512, 512, 512, 16, 16]
+    A, B, _ = synth.uniform_operands(spec, ext, seed=0)
+    dA, dB, (Ar, Br) = device_inputs("bf16x3", A, B)
+    got = run_gett(tcmod, spec, ext, "bf16x3", dA, dB)
+    rng = np.random.default_rng(1)
+    pts = np.stack([rng.integers(0, 512, 4000) for _ in range(3)], axis=1)
+    want = oc.contract_points(spec, ext, Ar, Br, pts, threads=4)
+    scale = oc.contract_points(spec, ext, np.abs(Ar), np.abs(Br), pts, threads=4)
+    lin = pts[:, 0] + 512 * pts[:, 1] + 512 * 512 * pts[:, 2]
+    err = float(np.max(np.abs(got[lin] - want) / scale))
+    assert err <= (256 + 4) * U32, err
+    assert np.isfinite(got).all()
