@@ -246,6 +246,8 @@ def measure_form(args, dtype, alg_name, A, B, dev, stream, dist, world, tc, step
     plan = tc.Plan(SPEC, EXTENTS, dtype=dtype)
     if dtype == "bf16x3":
         plan.set_split(args.products)
+    if dtype in TENSOR_FORMS and args.bn:
+        plan.set_gett_tile(args.bn)
     algs = {a["name"]: a for a in plan.algorithms()}
     alg = algs[alg_name]
     plan.select(alg["id"])
@@ -363,6 +365,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--dtype", default="bf16x3", choices=["f64", "f32", "tf32", "bf16", "f16", "bf16x3"])
     ap.add_argument("--products", type=int, default=6)
+    ap.add_argument("--bn", type=int, default=0, help="tensor-core GETT tile width (0: auto)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--alg", default="gett")
     ap.add_argument("--impl", default="tc", choices=["tc", "reference"])

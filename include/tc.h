@@ -160,6 +160,17 @@ tc_status tc_plan_device_status(tc_plan plan);
  * values give TC_ERROR_INVALID_ARGUMENT; other dtypes ignore the setting. */
 tc_status tc_plan_set_split(tc_plan plan, int32_t products);
 
+/* Tensor-core GETT tile width along N: 128 or 256 columns of C per tile
+ * (the tile is 128 x width), or 0 to choose by N (256 when N >= 256).
+ * Other values give TC_ERROR_INVALID_ARGUMENT. */
+tc_status tc_plan_set_gett_tile(tc_plan plan, int32_t width);
+
+/* Tensor-core GETT input path: 1 (default) streams each operand that a
+ * TMA tensor map can describe through cp.async.bulk.tensor into a staging
+ * ring; 0 loads every operand with ordinary global loads.  Results are the
+ * same either way. */
+tc_status tc_plan_set_gett_tma(tc_plan plan, int32_t enable);
+
 /* 2 * product of all extents. */
 tc_status tc_plan_flops(tc_plan plan, double *flops);
 

@@ -4,17 +4,28 @@
 // index.  FP64 / FP32 run the SIMT tiled form (tc_exec.cu); the tensor-core
 // dtypes run here on the 5th-generation tensor cores:
 //
-//   producer warps 0-7   load A/B tiles from global memory through the
-//                        operands' own strides (no transpose pass, any
-//                        permutation), convert or split them and store the
+// The kernel is persistent (one CTA per SM walks the tile list, M tiles
+// fastest so that CTAs sharing a B tile run together) and warp-specialised:
+//
+//   TMA warp 13          streams each operand's stage box (tile rows x 16 K
+//                        positions, any permutation of the operand's modes,
+//                        described by a CUtensorMap over its own strides: no
+//                        transpose pass) into a staging ring with
+//                        cp.async.bulk.tensor and mbarrier transaction counts;
+//   converter warps 4-11 convert or split the staged inputs (or, for an
+//                        operand TMA cannot describe, load it straight from
+//                        global memory through its strides) and store the
 //                        canonical no-swizzle K-major core-matrix layout
-//                        (8 rows x 16 bytes per core matrix) in shared memory;
-//   MMA warp 8           one elected thread issues tcgen05.mma (kind::f16 for
+//                        (8 rows x 16 bytes per core matrix) in a ring of
+//                        operand stages;
+//   MMA warp 12          one elected thread issues tcgen05.mma (kind::f16 for
 //                        BF16/FP16 and the split-BF16 slices, kind::tf32) into
-//                        an FP32 accumulator in tensor memory, and signals
-//                        stage reuse / completion with tcgen05.commit;
-//   epilogue warps 0-7   tcgen05.ld the accumulator, apply alpha and beta*C
-//                        and store FP32 C.
+//                        one of two FP32 accumulators in tensor memory, and
+//                        signals stage reuse / tile completion with
+//                        tcgen05.commit;
+//   epilogue warps 0-3   tcgen05.ld the finished accumulator, apply alpha and
+//                        beta*C and store FP32 C while the MMA warp already
+//                        fills the other accumulator.
 //
 // Split-BF16 ("BF16X3"): each FP32 input x is split into three BF16 slices
 // x = h0 + h1 + h2 (h0 = rn(x), h1 = rn(x - h0), h2 = rn(x - h0 - h1)); the
@@ -24,6 +35,8 @@
 // Every wait on an mbarrier is bounded (%globaltimer); on expiry the kernel
 // records TC_ERROR_TIMEOUT in the plan's status word, stops issuing work,
 // drains what it issued, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -45,11 +58,16 @@ namespace {
 enum GettKind { GK_BF16X3 = 0, GK_BF16 = 1, GK_F16 = 2, GK_TF32 = 3 };
 
 constexpr int kBM = 128;                  // accumulator rows = TMEM lanes
-constexpr int kBK = 32;                   // K elements per pipeline stage
-constexpr int kProducerWarps = 8;
+constexpr int kBK = 32;                   // K elements per stage, global-load path
+constexpr int kBKT = 16;                  // K elements per stage, TMA path
+constexpr int kEpiWarps = 4;              // warps 0-3
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kProducerWarps = 8;         // warps 4-11
 constexpr int kProducerThreads = kProducerWarps * 32;
-constexpr int kMmaWarp = kProducerWarps;  // warp 8
-constexpr int kThreads = kProducerThreads + 32;
+constexpr int kMmaWarp = kEpiWarps + kProducerWarps;  // warp 12
+constexpr int kTmaWarp = kMmaWarp + 1;                // warp 13
+constexpr int kThreads = (kTmaWarp + 1) * 32;
+constexpr int kTmaRank = 5;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 
 struct GettDesc {
@@ -64,9 +82,23 @@ struct GettDesc {
     float *C;
     float alpha, beta;
     int init;         // 1: C = alpha*acc + beta*C, 2: C = alpha*acc
-    int a_kfast, b_kfast;
+    int a_map, b_map; // producer mapping: 0 rows across lanes, 1 K chunks
+                      // across lanes, 2 16-byte vectors along K
     int nprod;        // split products (BF16X3)
+    int64_t num_tiles;
     int *status;
+    // TMA staging (per operand 0 = A, 1 = B): enabled flag, the tensor-map
+    // dimension of each row mode and of each K mode with its coordinate
+    // multiplier, the staging offset of tile row r (r * srow) and of the
+    // stage's K position k (sk[k]), and whether sk runs in aligned fours.
+    int tma[2];
+    int row_dim[2][kMaxModes];
+    int k_dim[2][kMaxModes];
+    int64_t k_mul[2][kMaxModes];
+    int srow[2];
+    int sk[2][kBKT];
+    int sk_vec4[2];
+    uint32_t tma_bytes;  // staged bytes per stage (both operands)
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -113,6 +145,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     return true;
 }
 
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+// One box of a rank-5 tensor map into shared memory; completion is
+// counted in bytes on the mbarrier.
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            const int32_t (&c)[5]) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4])
+        : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -129,16 +180,17 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Producer-only barrier that also ORs a predicate across the producers.
-__device__ __forceinline__ bool producers_sync_or(bool pred) {
+// Named barrier over one warp role that also ORs a predicate across it.
+template <int ID, int COUNT>
+__device__ __forceinline__ bool role_sync_or(bool pred) {
     uint32_t out;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"
-        "barrier.cta.red.or.pred q, 1, %2, p;\n\t"
+        "barrier.cta.red.or.pred q, %2, %3, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(out)
-        : "r"((uint32_t)pred), "n"(kProducerThreads)
+        : "r"((uint32_t)pred), "n"(ID), "n"(COUNT)
         : "memory");
     return out != 0;
 }
@@ -213,34 +265,37 @@ __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
     return r;
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
 
 // ------------------------------------------------------------------ layout
-template <int KIND>
+template <int KIND, int BK>
 struct KindTraits {
     static constexpr int kElemBytes = KIND == GK_TF32 ? 4 : 2;  // smem operand element
     static constexpr int kSlices = KIND == GK_BF16X3 ? 3 : 1;
     static constexpr int kChunk = 16 / kElemBytes;              // K elements per 16-byte row
-    static constexpr int kKc = kBK / kChunk;                    // core matrices along K per stage
-    static constexpr int kKsteps = kBK * kElemBytes / 32;       // MMA instructions along K per stage
+    static constexpr int kKc = BK / kChunk;                     // core matrices along K per stage
+    static constexpr int kKsteps = BK * kElemBytes / 32;        // MMA instructions along K per stage
     static constexpr uint32_t kFmt = KIND == GK_TF32 ? 2u : (KIND == GK_F16 ? 0u : 1u);
-    using In = typename std::conditional<KIND == GK_BF16 ? true : false, __nv_bfloat16,
+    using In = typename std::conditional<KIND == GK_BF16, __nv_bfloat16,
                                          typename std::conditional<KIND == GK_F16, __half, float>::type>::type;
+    static constexpr int kInBytes = sizeof(In);
+    static constexpr int kVec = 16 / kInBytes;                  // input elements per 16-byte load
 };
 
-template <int KIND, int BN, int STAGES>
+template <int KIND, int BN, int STAGES, int BK, bool TMA>
 struct SmemPlan {
-    using T = KindTraits<KIND>;
-    static constexpr int kATile = kBM * kBK * T::kElemBytes;   // one slice
-    static constexpr int kBTile = BN * kBK * T::kElemBytes;
+    using T = KindTraits<KIND, BK>;
+    static constexpr int kATile = kBM * BK * T::kElemBytes;    // one slice
+    static constexpr int kBTile = BN * BK * T::kElemBytes;
     static constexpr int kStage = T::kSlices * (kATile + kBTile);
     static constexpr int kOpBytes = STAGES * kStage;
-    static constexpr int kKTab = STAGES * kBK * 8 * 2;
-    static constexpr int kRowTab = (kBM + BN) * 8 * 2;
-    static constexpr int kBars = (2 * STAGES + 1) * 8 + 16;
-    static constexpr int kTotal = kOpBytes + kKTab + kRowTab + kBars;
+    static constexpr int kStgA = TMA ? kBM * BK * T::kInBytes : 0;  // staged input box
+    static constexpr int kStgB = TMA ? BN * BK * T::kInBytes : 0;
+    static constexpr int kStgBytes = STAGES * (kStgA + kStgB);
+    static constexpr int kKTab = STAGES * BK * 8 * 2;
+    static constexpr int kRowTab = 2 * (kBM + BN) * 8;          // converters, double-buffered
+    static constexpr int kColTab = 2 * BN * 8;                  // epilogue, double-buffered
+    static constexpr int kBars = (4 * STAGES + 5) * 8 + 16;
+    static constexpr int kTotal = kOpBytes + kStgBytes + kKTab + kRowTab + kColTab + kBars;
 };
 
 __device__ __forceinline__ void decode(int64_t x, int n, const int64_t *ext, const int64_t *s1,
@@ -254,230 +309,444 @@ __device__ __forceinline__ void decode(int64_t x, int n, const int64_t *ext, con
     }
 }
 
-// Loads CH consecutive K elements of one operand row and writes the
-// converted / split 16-byte rows into every slice.
-template <int KIND>
-__device__ __forceinline__ void produce_chunk(const typename KindTraits<KIND>::In *__restrict__ src,
-                                              int64_t rowoff, const int64_t *koff, char *dst,
-                                              int slice_stride) {
-    using T = KindTraits<KIND>;
-    constexpr int CH = T::kChunk;
+// x = h0 + h1 + h2 for two values at once: cvt.rn.bf16x2 rounds a pair,
+// the widening back to FP32 is exact, so the remainders are exact.
+__device__ __forceinline__ void split3x2(float x0, float x1, uint32_t &w0, uint32_t &w1, uint32_t &w2) {
+    __nv_bfloat162 h0 = __floats2bfloat162_rn(x0, x1);
+    float2 f0 = __bfloat1622float2(h0);
+    const float r0 = x0 - f0.x, r1 = x1 - f0.y;
+    __nv_bfloat162 h1 = __floats2bfloat162_rn(r0, r1);
+    float2 f1 = __bfloat1622float2(h1);
+    __nv_bfloat162 h2 = __floats2bfloat162_rn(r0 - f1.x, r1 - f1.y);
+    w0 = *(uint32_t *)&h0;
+    w1 = *(uint32_t *)&h1;
+    w2 = *(uint32_t *)&h2;
+}
+
+// Converts N (4 or 8) FP32 values into the 16-bit slices or TF32 words
+// and stores them at dst (one slice after another, slice_stride apart).
+template <int KIND, int N>
+__device__ __forceinline__ void store_converted(const float (&x)[N], char *dst, int slice_stride) {
     if constexpr (KIND == GK_BF16X3) {
-        float x[CH];
+        uint32_t w0[N / 2], w1[N / 2], w2[N / 2];
 #pragma unroll
-        for (int e = 0; e < CH; ++e) {
-            int64_t ko = koff[e];
-            x[e] = (rowoff >= 0 && ko >= 0) ? __ldg(src + rowoff + ko) : 0.0f;
+        for (int e = 0; e < N; e += 2) split3x2(x[e], x[e + 1], w0[e / 2], w1[e / 2], w2[e / 2]);
+        if constexpr (N == 8) {
+            *(uint4 *)(dst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+            *(uint4 *)(dst + slice_stride) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+            *(uint4 *)(dst + 2 * slice_stride) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+        } else {
+            *(uint2 *)(dst) = make_uint2(w0[0], w0[1]);
+            *(uint2 *)(dst + slice_stride) = make_uint2(w1[0], w1[1]);
+            *(uint2 *)(dst + 2 * slice_stride) = make_uint2(w2[0], w2[1]);
         }
-        uint32_t w0[CH / 2], w1[CH / 2], w2[CH / 2];
-#pragma unroll
-        for (int e = 0; e < CH; e += 2) {
-            __nv_bfloat16 h0a = __float2bfloat16_rn(x[e]);
-            float r1a = x[e] - __bfloat162float(h0a);
-            __nv_bfloat16 h1a = __float2bfloat16_rn(r1a);
-            __nv_bfloat16 h2a = __float2bfloat16_rn(r1a - __bfloat162float(h1a));
-            __nv_bfloat16 h0b = __float2bfloat16_rn(x[e + 1]);
-            float r1b = x[e + 1] - __bfloat162float(h0b);
-            __nv_bfloat16 h1b = __float2bfloat16_rn(r1b);
-            __nv_bfloat16 h2b = __float2bfloat16_rn(r1b - __bfloat162float(h1b));
-            w0[e / 2] = pack_bf16(h0a, h0b);
-            w1[e / 2] = pack_bf16(h1a, h1b);
-            w2[e / 2] = pack_bf16(h2a, h2b);
-        }
-        *(uint4 *)(dst) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-        *(uint4 *)(dst + slice_stride) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-        *(uint4 *)(dst + 2 * slice_stride) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-    } else if constexpr (KIND == GK_TF32) {
-        uint32_t w[CH];
-#pragma unroll
-        for (int e = 0; e < CH; ++e) {
-            int64_t ko = koff[e];
-            float v = (rowoff >= 0 && ko >= 0) ? __ldg(src + rowoff + ko) : 0.0f;
-            w[e] = f32_to_tf32(v);
-        }
-        *(uint4 *)(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-    } else {
-        unsigned short h[CH];
-#pragma unroll
-        for (int e = 0; e < CH; ++e) {
-            int64_t ko = koff[e];
-            const unsigned short *s16 = (const unsigned short *)src;
-            h[e] = (rowoff >= 0 && ko >= 0) ? __ldg(s16 + rowoff + ko) : (unsigned short)0;
-        }
-        uint32_t w[CH / 2];
-#pragma unroll
-        for (int e = 0; e < CH; e += 2) w[e / 2] = (uint32_t)h[e] | ((uint32_t)h[e + 1] << 16);
-        *(uint4 *)(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {  // TF32: N == 4
+        *(uint4 *)(dst) = make_uint4(f32_to_tf32(x[0]), f32_to_tf32(x[1]), f32_to_tf32(x[2]),
+                                     f32_to_tf32(x[3]));
     }
 }
 
-template <int KIND, int BN, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1) gett_tc_kernel(const GettDesc d) {
-    using T = KindTraits<KIND>;
-    using SP = SmemPlan<KIND, BN, STAGES>;
+// Global-load path: one operand's share of a stage (ROWS rows x BK K
+// elements), loads first (all in flight), then conversion and stores.
+// MAP 2: 16-byte vector loads along K (contiguity and alignment checked on
+// the host); MAP 1: K chunks across lanes; MAP 0: rows across lanes.  Maps 0
+// and 1 load through the offset tables one element at a time (any strides).
+template <int KIND, int BK, int ROWS, int MAP>
+__device__ __forceinline__ void produce_operand(const typename KindTraits<KIND, BK>::In *__restrict__ src,
+                                                const int64_t *rowoff, const int64_t *koff, char *tile,
+                                                int slice_stride, int pt) {
+    using T = KindTraits<KIND, BK>;
+    constexpr int KC = T::kKc, CH = T::kChunk;
+    constexpr bool kFloatIn = KIND == GK_BF16X3 || KIND == GK_TF32;
+    if constexpr (MAP == 2) {
+        constexpr int UPR = BK / T::kVec;  // 16-byte loads per row per stage
+        constexpr int NU = ROWS * UPR / kProducerThreads;
+        static_assert(NU * kProducerThreads == ROWS * UPR, "even split");
+        uint4 v[NU];
+#pragma unroll
+        for (int i = 0; i < NU; ++i) {
+            const int u = pt + i * kProducerThreads;
+            const int row = u / UPR, k = (u % UPR) * T::kVec;
+            const int64_t ro = rowoff[row], ko = koff[k];
+            v[i] = (ro >= 0 && ko >= 0) ? __ldg((const uint4 *)(src + ro + ko)) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int i = 0; i < NU; ++i) {
+            const int u = pt + i * kProducerThreads;
+            const int row = u / UPR, k = (u % UPR) * T::kVec;
+            const int kc = k / CH, byte = (k % CH) * T::kElemBytes;
+            char *dst = tile + (kc * (ROWS / 8) + row / 8) * 128 + (row % 8) * 16 + byte;
+            if constexpr (kFloatIn) {
+                float x[4] = {__uint_as_float(v[i].x), __uint_as_float(v[i].y), __uint_as_float(v[i].z),
+                              __uint_as_float(v[i].w)};
+                store_converted<KIND, 4>(x, dst, slice_stride);
+            } else {
+                *(uint4 *)(dst) = v[i];
+            }
+        }
+    } else {
+        constexpr int NC = ROWS * KC / kProducerThreads;
+        static_assert(NC * kProducerThreads == ROWS * KC, "even split");
+        using L = typename std::conditional<kFloatIn, float, unsigned short>::type;
+        const L *s = (const L *)src;
+        L x[NC][CH];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            const int c = pt + i * kProducerThreads;
+            const int row = MAP == 1 ? c / KC : c % ROWS;
+            const int kc = MAP == 1 ? c % KC : c / ROWS;
+            const int64_t ro = rowoff[row];
+#pragma unroll
+            for (int e = 0; e < CH; ++e) {
+                const int64_t ko = koff[kc * CH + e];
+                x[i][e] = (ro >= 0 && ko >= 0) ? __ldg(s + ro + ko) : L(0);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            const int c = pt + i * kProducerThreads;
+            const int row = MAP == 1 ? c / KC : c % ROWS;
+            const int kc = MAP == 1 ? c % KC : c / ROWS;
+            char *dst = tile + (kc * (ROWS / 8) + row / 8) * 128 + (row % 8) * 16;
+            if constexpr (kFloatIn) {
+                store_converted<KIND, CH>(x[i], dst, slice_stride);
+            } else {
+                uint32_t w[CH / 2];
+#pragma unroll
+                for (int e = 0; e < CH; e += 2) w[e / 2] = (uint32_t)x[i][e] | ((uint32_t)x[i][e + 1] << 16);
+                *(uint4 *)(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+    }
+}
+
+template <int KIND, int BK, int ROWS>
+__device__ __forceinline__ void produce_any(const typename KindTraits<KIND, BK>::In *__restrict__ src,
+                                            const int64_t *rowoff, const int64_t *koff, char *tile,
+                                            int slice_stride, int map, int pt) {
+    if (map == 2) produce_operand<KIND, BK, ROWS, 2>(src, rowoff, koff, tile, slice_stride, pt);
+    else if (map == 1) produce_operand<KIND, BK, ROWS, 1>(src, rowoff, koff, tile, slice_stride, pt);
+    else produce_operand<KIND, BK, ROWS, 0>(src, rowoff, koff, tile, slice_stride, pt);
+}
+
+// TMA path: converts one operand's staged box (ROWS rows x BK K positions,
+// laid out as the box's dimensions) into the core-matrix layout.  Row r of
+// the tile sits at r * srow, K position k at sk[k] (elements); rows past the
+// operand's extent were filled with zeros by the TMA unit.
+template <int KIND, int BK, int ROWS>
+__device__ __forceinline__ void convert_staged(const char *stg, int srow, const int *sk, int vec4,
+                                               char *tile, int slice_stride, int pt) {
+    using T = KindTraits<KIND, BK>;
+    using In = typename T::In;
+    constexpr int KC = T::kKc, CH = T::kChunk;
+    constexpr int NC = ROWS * KC / kProducerThreads;
+    static_assert(NC * kProducerThreads == ROWS * KC, "even split");
+    constexpr bool kFloatIn = KIND == GK_BF16X3 || KIND == GK_TF32;
+    const In *s = (const In *)stg;
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        const int c = pt + i * kProducerThreads;
+        const int row = c % ROWS, kc = c / ROWS;  // rows across lanes: conflict-free stores
+        char *dst = tile + (kc * (ROWS / 8) + row / 8) * 128 + (row % 8) * 16;
+        const In *base = s + row * srow;
+        if constexpr (kFloatIn) {
+            float x[CH];
+            if (vec4) {
+#pragma unroll
+                for (int e = 0; e < CH; e += 4) {
+                    float4 v = *(const float4 *)(base + sk[kc * CH + e]);
+                    x[e] = v.x;
+                    x[e + 1] = v.y;
+                    x[e + 2] = v.z;
+                    x[e + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < CH; ++e) x[e] = base[sk[kc * CH + e]];
+            }
+            store_converted<KIND, CH>(x, dst, slice_stride);
+        } else {
+            const unsigned short *b16 = (const unsigned short *)base;
+            uint32_t w[CH / 2];
+#pragma unroll
+            for (int e = 0; e < CH; e += 2)
+                w[e / 2] = (uint32_t)b16[sk[kc * CH + e]] | ((uint32_t)b16[sk[kc * CH + e + 1]] << 16);
+            *(uint4 *)(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+template <int KIND, int BN, int STAGES, int BK, bool TMA>
+__global__ void __launch_bounds__(kThreads, 1)
+gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
+    using T = KindTraits<KIND, BK>;
+    using SP = SmemPlan<KIND, BN, STAGES, BK, TMA>;
     using In = typename T::In;
     extern __shared__ __align__(1024) char smem[];
     char *ops = smem;
-    int64_t *kA = (int64_t *)(smem + SP::kOpBytes);          // [STAGES][kBK]
-    int64_t *kB = kA + STAGES * kBK;
-    int64_t *rowA = kB + STAGES * kBK;                        // [kBM]
-    int64_t *cM = rowA + kBM;
-    int64_t *rowB = cM + kBM;                                 // [BN]
-    int64_t *cN = rowB + BN;
-    uint64_t *full = (uint64_t *)(cN + BN);
-    uint64_t *empty = full + STAGES;
-    uint64_t *accum = empty + STAGES;
-    uint32_t *tmem_slot = (uint32_t *)(accum + 1);
+    char *stg = smem + SP::kOpBytes;                          // [STAGES][A box | B box]
+    int64_t *kA = (int64_t *)(stg + SP::kStgBytes);           // [STAGES][BK]
+    int64_t *kB = kA + STAGES * BK;
+    int64_t *rowA = kB + STAGES * BK;                         // [2][kBM]
+    int64_t *rowB = rowA + 2 * kBM;                           // [2][BN]
+    int64_t *cN = rowB + 2 * BN;                              // [2][BN]
+    uint64_t *full = (uint64_t *)(cN + 2 * BN);               // operand stage filled
+    uint64_t *empty = full + STAGES;                          // operand stage consumed
+    uint64_t *sfull = empty + STAGES;                         // staged box landed
+    uint64_t *sempty = sfull + STAGES;                        // staged box converted
+    uint64_t *tfull = sempty + STAGES;                        // [2]
+    uint64_t *tempty = tfull + 2;                             // [2]
+    uint64_t *drain = tempty + 2;
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int64_t tile_m = blockIdx.x % d.tiles_m;
-    const int64_t tile_n = blockIdx.x / d.tiles_m;
-    const int64_t m0 = tile_m * kBM, n0 = tile_n * BN;
-    const int nkt = (int)((d.K + kBK - 1) / kBK);
+    const int nkt = (int)((d.K + BK - 1) / BK);
+    const bool any_tma = TMA && (d.tma[0] || d.tma[1]);
+    const bool any_ldg = !TMA || !d.tma[0] || !d.tma[1];
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], kProducerThreads);
             mbar_init(&empty[s], 1);
+            mbar_init(&sfull[s], 1);
+            mbar_init(&sempty[s], kProducerThreads);
         }
-        mbar_init(accum, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kEpiThreads);
+        }
+        mbar_init(drain, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == kMmaWarp) tmem_alloc(tmem_slot, BN);
-    // row tables
-    for (int i = threadIdx.x; i < kBM; i += kThreads) {
-        int64_t mm = m0 + i, oa = -1, oc = -1;
-        if (mm < d.M) {
-            oa = 0;
-            oc = 0;
-            decode(mm, d.nm, d.m_ext, d.m_sA, d.m_sC, oa, oc);
-        }
-        rowA[i] = oa;
-        cM[i] = oc;
-    }
-    for (int j = threadIdx.x; j < BN; j += kThreads) {
-        int64_t nn = n0 + j, ob = -1, oc = -1;
-        if (nn < d.N) {
-            ob = 0;
-            oc = 0;
-            decode(nn, d.nn, d.n_ext, d.n_sB, d.n_sC, ob, oc);
-        }
-        rowB[j] = ob;
-        cN[j] = oc;
-    }
+    if (warp == kMmaWarp) tmem_alloc(tmem_slot, 2 * BN);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp < kProducerWarps) {
-        // ---------------------------------------------------------- producers
-        const int pt = threadIdx.x;
+    if (warp >= kEpiWarps && warp < kMmaWarp) {
+        // ---------------------------------------------------------- converters
+        const int pt = threadIdx.x - kEpiThreads;
         const In *__restrict__ Ap = (const In *)d.A;
         const In *__restrict__ Bp = (const In *)d.B;
-        constexpr int KC = T::kKc, CH = T::kChunk;
-        for (int t = 0; t < nkt; ++t) {
-            const int s = t % STAGES;
-            bool bad = false;
-            if (t >= STAGES) bad = !mbar_wait(&empty[s], ((t / STAGES) - 1) & 1);
-            if (pt < kBK) {
-                int64_t k = (int64_t)t * kBK + pt, oa = -1, ob = -1;
-                if (k < d.K) {
-                    oa = 0;
-                    ob = 0;
-                    // K modes outermost first: innermost mode fastest
-                    for (int m = d.nk - 1; m >= 0; --m) {
-                        int64_t v = k % d.k_ext[m];
-                        k /= d.k_ext[m];
-                        oa += v * d.k_sA[m];
-                        ob += v * d.k_sB[m];
+        int64_t g = 0;
+        int it = 0;
+        bool stop = false;
+        for (int64_t tile = blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x, ++it) {
+            const int64_t m0 = (tile % d.tiles_m) * kBM, n0 = (tile / d.tiles_m) * BN;
+            int64_t *rA = rowA + (it & 1) * kBM;
+            int64_t *rB = rowB + (it & 1) * BN;
+            for (int kt = 0; kt < nkt; ++kt, ++g) {
+                const int s = (int)(g % STAGES);
+                const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+                bool bad = false;
+                if (g >= STAGES) bad = !mbar_wait(&empty[s], ph ^ 1u);
+                if (any_tma && !bad) bad = !mbar_wait(&sfull[s], ph);
+                if (any_ldg) {
+                    if (kt == 0) {
+                        for (int i = pt; i < kBM; i += kProducerThreads) {
+                            int64_t mm = m0 + i, oa = -1, oc = 0;
+                            if (mm < d.M) {
+                                oa = 0;
+                                decode(mm, d.nm, d.m_ext, d.m_sA, d.m_sC, oa, oc);
+                            }
+                            rA[i] = oa;
+                        }
+                        for (int j = pt; j < BN; j += kProducerThreads) {
+                            int64_t nn = n0 + j, ob = -1, oc = 0;
+                            if (nn < d.N) {
+                                ob = 0;
+                                decode(nn, d.nn, d.n_ext, d.n_sB, d.n_sC, ob, oc);
+                            }
+                            rB[j] = ob;
+                        }
+                    }
+                    if (pt < BK) {
+                        int64_t k = (int64_t)kt * BK + pt, oa = -1, ob = -1;
+                        if (k < d.K) {
+                            oa = 0;
+                            ob = 0;
+                            for (int m = d.nk - 1; m >= 0; --m) {  // innermost K mode fastest
+                                int64_t v = k % d.k_ext[m];
+                                k /= d.k_ext[m];
+                                oa += v * d.k_sA[m];
+                                ob += v * d.k_sB[m];
+                            }
+                        }
+                        kA[s * BK + pt] = oa;
+                        kB[s * BK + pt] = ob;
                     }
                 }
-                kA[s * kBK + pt] = oa;
-                kB[s * kBK + pt] = ob;
-            }
-            if (producers_sync_or(bad || *abort_flag)) {
-                if (pt == 0) {
-                    *abort_flag = 1;
-                    atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
+                if (role_sync_or<1, kProducerThreads>(bad || *abort_flag)) {
+                    if (pt == 0) {
+                        *abort_flag = 1;
+                        atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
+                    }
+                    stop = true;
+                    break;
                 }
-                break;
+                char *stage = ops + s * SP::kStage;
+                char *bstage = stage + T::kSlices * SP::kATile;
+                if (TMA && d.tma[0]) {
+                    convert_staged<KIND, BK, kBM>(stg + s * (SP::kStgA + SP::kStgB), d.srow[0], d.sk[0],
+                                                  d.sk_vec4[0], stage, SP::kATile, pt);
+                } else {
+                    produce_any<KIND, BK, kBM>(Ap, rA, kA + s * BK, stage, SP::kATile, d.a_map, pt);
+                }
+                if (TMA && d.tma[1]) {
+                    convert_staged<KIND, BK, BN>(stg + s * (SP::kStgA + SP::kStgB) + SP::kStgA, d.srow[1],
+                                                 d.sk[1], d.sk_vec4[1], bstage, SP::kBTile, pt);
+                } else {
+                    produce_any<KIND, BK, BN>(Bp, rB, kB + s * BK, bstage, SP::kBTile, d.b_map, pt);
+                }
+                fence_proxy_async_smem();
+                mbar_arrive(&full[s]);
+                if (any_tma) mbar_arrive(&sempty[s]);
             }
-            char *stage = ops + s * SP::kStage;
-            // A rows
-            for (int c = pt; c < kBM * KC; c += kProducerThreads) {
-                int row, kc;
-                if (d.a_kfast) { row = c / KC; kc = c % KC; }
-                else { row = c % kBM; kc = c / kBM; }
-                char *dst = stage + (kc * (kBM / 8) + row / 8) * 128 + (row % 8) * 16;
-                produce_chunk<KIND>(Ap, rowA[row], kA + s * kBK + kc * CH, dst, SP::kATile);
-            }
-            // B rows
-            char *bst = stage + T::kSlices * SP::kATile;
-            for (int c = pt; c < BN * KC; c += kProducerThreads) {
-                int row, kc;
-                if (d.b_kfast) { row = c / KC; kc = c % KC; }
-                else { row = c % BN; kc = c / BN; }
-                char *dst = bst + (kc * (BN / 8) + row / 8) * 128 + (row % 8) * 16;
-                produce_chunk<KIND>(Bp, rowB[row], kB + s * kBK + kc * CH, dst, SP::kBTile);
-            }
-            fence_proxy_async_smem();
-            mbar_arrive(&full[s]);
         }
-    } else if (lane == 0) {
-        // ---------------------------------------------------------- MMA issuer
-        constexpr uint32_t idesc = (1u << 4) | (T::kFmt << 7) | (T::kFmt << 10) |
-                                   ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
-        constexpr uint32_t lboA = (kBM / 8) * 128, lboB = (BN / 8) * 128;
-        const int pa[9] = {0, 0, 1, 0, 1, 2, 1, 2, 2};
-        const int pb[9] = {0, 1, 0, 2, 1, 0, 2, 1, 2};
-        const int nprod = KIND == GK_BF16X3 ? d.nprod : 1;
-        const uint32_t base = smem_u32(ops);
-        for (int t = 0; t < nkt; ++t) {
-            const int s = t % STAGES;
-            if (*abort_flag || !mbar_wait(&full[s], (t / STAGES) & 1)) {
+    } else if (warp == kTmaWarp) {
+        // ---------------------------------------------------------- TMA issue
+        if (TMA && any_tma && lane == 0) {
+            int64_t g = 0;
+            bool stop = false;
+            for (int64_t tile = blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x) {
+                const int64_t m0 = (tile % d.tiles_m) * kBM, n0 = (tile / d.tiles_m) * BN;
+                int32_t rc[2][kTmaRank] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
+                {
+                    int64_t r = m0;
+                    for (int m = 0; m < d.nm; ++m) {
+                        rc[0][d.row_dim[0][m]] = (int32_t)(r % d.m_ext[m]);
+                        r /= d.m_ext[m];
+                    }
+                    r = n0;
+                    for (int m = 0; m < d.nn; ++m) {
+                        rc[1][d.row_dim[1][m]] = (int32_t)(r % d.n_ext[m]);
+                        r /= d.n_ext[m];
+                    }
+                }
+                for (int kt = 0; kt < nkt; ++kt, ++g) {
+                    const int s = (int)(g % STAGES);
+                    if (g >= STAGES && (*abort_flag || !mbar_wait(&sempty[s], (uint32_t)(((g / STAGES) - 1) & 1)))) {
+                        stop = true;
+                        break;
+                    }
+                    int32_t c[2][kTmaRank];
+                    for (int o = 0; o < 2; ++o)
+                        for (int x = 0; x < kTmaRank; ++x) c[o][x] = rc[o][x];
+                    int64_t k = (int64_t)kt * BK;
+                    for (int m = d.nk - 1; m >= 0; --m) {
+                        const int64_t v = k % d.k_ext[m];
+                        k /= d.k_ext[m];
+                        for (int o = 0; o < 2; ++o) c[o][d.k_dim[o][m]] += (int32_t)(v * d.k_mul[o][m]);
+                    }
+                    char *box = stg + s * (SP::kStgA + SP::kStgB);
+                    mbar_arrive_expect_tx(&sfull[s], d.tma_bytes);
+                    if (d.tma[0]) tma_load_5d(box, &tmA, &sfull[s], c[0]);
+                    if (d.tma[1]) tma_load_5d(box + SP::kStgA, &tmB, &sfull[s], c[1]);
+                }
+            }
+            if (stop) {
                 *abort_flag = 1;
                 atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
-                break;
             }
-            tc_fence_after();
-            const uint32_t sa = base + s * SP::kStage;
-            const uint32_t sb = sa + T::kSlices * SP::kATile;
+        }
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = (1u << 4) | (T::kFmt << 7) | (T::kFmt << 10) |
+                                       ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+            constexpr uint32_t lboA = (kBM / 8) * 128, lboB = (BN / 8) * 128;
+            const int pa[9] = {0, 0, 1, 0, 1, 2, 1, 2, 2};
+            const int pb[9] = {0, 1, 0, 2, 1, 0, 2, 1, 2};
+            const int nprod = KIND == GK_BF16X3 ? d.nprod : 1;
+            const uint32_t base = smem_u32(ops);
+            int64_t g = 0;
+            int it = 0;
+            bool stop = false;
+            for (int64_t tile = blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x, ++it) {
+                const int buf = it & 1;
+                if (it >= 2 && !mbar_wait(&tempty[buf], (uint32_t)(((it / 2) - 1) & 1))) {
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)(buf * BN);
+                for (int kt = 0; kt < nkt; ++kt, ++g) {
+                    const int s = (int)(g % STAGES);
+                    if (*abort_flag || !mbar_wait(&full[s], (uint32_t)((g / STAGES) & 1))) {
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = base + s * SP::kStage;
+                    const uint32_t sb = sa + T::kSlices * SP::kATile;
 #pragma unroll
-            for (int ks = 0; ks < T::kKsteps; ++ks) {
-                for (int q = 0; q < nprod; ++q) {
-                    uint64_t ad = smem_desc(sa + pa[q] * SP::kATile + ks * 2 * lboA, lboA, 128);
-                    uint64_t bd = smem_desc(sb + pb[q] * SP::kBTile + ks * 2 * lboB, lboB, 128);
-                    mma_issue<KIND>(tmem, ad, bd, idesc, (t | ks | q) != 0);
+                    for (int ks = 0; ks < T::kKsteps; ++ks) {
+                        for (int q = 0; q < nprod; ++q) {
+                            uint64_t ad = smem_desc(sa + pa[q] * SP::kATile + ks * 2 * lboA, lboA, 128);
+                            uint64_t bd = smem_desc(sb + pb[q] * SP::kBTile + ks * 2 * lboB, lboB, 128);
+                            mma_issue<KIND>(dt, ad, bd, idesc, (kt | ks | q) != 0);
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&tfull[buf]);  // arrives when this tile's MMAs are done
+            }
+            if (stop) {
+                *abort_flag = 1;
+                atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
+            }
+            // nothing issued may still run when the tensor memory is freed
+            mma_commit(drain);
+            mbar_wait(drain, 0);
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int et = threadIdx.x;  // 0..127 = accumulator row = TMEM lane
+        float *__restrict__ C = d.C;
+        int it = 0;
+        for (int64_t tile = blockIdx.x; tile < d.num_tiles; tile += gridDim.x, ++it) {
+            const int64_t m0 = (tile % d.tiles_m) * kBM, n0 = (tile / d.tiles_m) * BN;
+            int64_t *cn = cN + (it & 1) * BN;
+            for (int j = et; j < BN; j += kEpiThreads) {
+                int64_t nn = n0 + j, ob = 0, oc = -1;
+                if (nn < d.N) {
+                    oc = 0;
+                    decode(nn, d.nn, d.n_ext, d.n_sB, d.n_sC, ob, oc);
+                }
+                cn[j] = oc;
+            }
+            int64_t om = -1;
+            {
+                int64_t mm = m0 + et, oa = 0;
+                if (mm < d.M) {
+                    om = 0;
+                    decode(mm, d.nm, d.m_ext, d.m_sA, d.m_sC, oa, om);
                 }
             }
-            mma_commit(&empty[s]);
-        }
-        mma_commit(accum);  // fires once every issued MMA has completed
-    }
-
-    // -------------------------------------------------------------- epilogue
-    if (warp < kProducerWarps) {
-        const bool ok = mbar_wait(accum, 0);
-        if (!ok) {
-            *abort_flag = 1;
-            atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
-        }
-        tc_fence_after();
-        if (ok && !*abort_flag) {
-            const int quarter = warp % 4, half = warp / 4;
-            const int row = quarter * 32 + lane;
-            const int64_t om = cM[row];
-            float *__restrict__ C = d.C;
-            for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
+            if (role_sync_or<2, kEpiThreads>(*abort_flag)) break;
+            const int buf = it & 1;
+            bool ok = mbar_wait(&tfull[buf], (uint32_t)((it / 2) & 1));
+            ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld needs the whole warp
+            if (!ok) {
+                *abort_flag = 1;
+                atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
+                continue;  // the next role barrier sees the abort
+            }
+            tc_fence_after();
+            const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * BN);
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
                 uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, r);
+                tmem_ld32(lane_base + (uint32_t)c0, r);
                 if (om >= 0) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int64_t on = cN[c0 + j];
+                        const int64_t on = cn[c0 + j];
                         if (on < 0) continue;
                         float v = d.alpha * __uint_as_float(r[j]);
                         if (d.init == 1) v = fmaf(d.beta, C[om + on], v);
@@ -485,41 +754,238 @@ __global__ void __launch_bounds__(kThreads, 1) gett_tc_kernel(const GettDesc d) 
                     }
                 }
             }
+            tc_fence_before();
+            mbar_arrive(&tempty[buf]);
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == kMmaWarp) {
         tc_fence_after();
-        tmem_dealloc(tmem, BN);
+        tmem_dealloc(tmem, 2 * BN);
     }
 }
 
 // ------------------------------------------------------------------ host side
-template <int KIND, int BN, int STAGES>
-tc_status launch_gett(const GettDesc &d, cudaStream_t st) {
-    using SP = SmemPlan<KIND, BN, STAGES>;
+int g_gett_sms = 0;
+
+template <int KIND, int BN, int STAGES, int BK, bool TMA>
+tc_status launch_gett(const GettDesc &d, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
+    using SP = SmemPlan<KIND, BN, STAGES, BK, TMA>;
     static_assert(SP::kTotal <= 227 * 1024, "shared memory budget");
-    auto kern = gett_tc_kernel<KIND, BN, STAGES>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SP::kTotal);
+    // at least 116 KB so that one CTA (and one tensor-memory allocation of
+    // 2*BN columns) occupies each SM
+    constexpr int kSmem = SP::kTotal > 116 * 1024 ? SP::kTotal : 116 * 1024;
+    auto kern = gett_tc_kernel<KIND, BN, STAGES, BK, TMA>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
-    int64_t grid = d.tiles_m * d.tiles_n;
-    if (grid > 0x7FFFFFFF) return fail(TC_ERROR_INVALID_EXTENT, "too many GETT tiles");
-    kern<<<(unsigned)grid, kThreads, SP::kTotal, st>>>(d);
+    if (g_gett_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_gett_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_gett_sms <= 0) g_gett_sms = 1;
+    }
+    const int64_t grid = std::min<int64_t>(d.num_tiles, g_gett_sms);
+    kern<<<(unsigned)grid, kThreads, kSmem, st>>>(d, ta, tb);
     e = cudaGetLastError();
     return e == cudaSuccess ? TC_SUCCESS : fail(TC_ERROR_CUDA, cudaGetErrorString(e));
 }
 
 template <int KIND>
-tc_status launch_kind(GettDesc &d, int bn, cudaStream_t st) {
-    if (bn == 256) {
-        d.tiles_n = (d.N + 255) / 256;
-        if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 256, 2>(d, st);
-        else return launch_gett<KIND, 256, 4>(d, st);
+tc_status launch_kind(GettDesc &d, int bn, bool tma, const CUtensorMap &ta, const CUtensorMap &tb,
+                      cudaStream_t st) {
+    d.tiles_n = (d.N + bn - 1) / bn;
+    d.num_tiles = d.tiles_m * d.tiles_n;
+    if (tma) {  // 16-K stages, staged input boxes, BN = 256
+        if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 256, 3, kBKT, true>(d, ta, tb, st);
+        else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 256, 3, kBKT, true>(d, ta, tb, st);
+        else return launch_gett<KIND, 256, 5, kBKT, true>(d, ta, tb, st);
     }
-    d.tiles_n = (d.N + 127) / 128;
-    if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 128, 4>(d, st);
-    else return launch_gett<KIND, 128, 6>(d, st);
+    if (bn == 256) {
+        if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 256, 2, kBK, false>(d, ta, tb, st);
+        else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 256, 3, kBK, false>(d, ta, tb, st);
+        else return launch_gett<KIND, 256, 6, kBK, false>(d, ta, tb, st);
+    }
+    if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 128, 4, kBK, false>(d, ta, tb, st);
+    else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 128, 6, kBK, false>(d, ta, tb, st);
+    else return launch_gett<KIND, 128, 8, kBK, false>(d, ta, tb, st);
+}
+
+// Distinct 32-byte sectors one warp touches on its first load under a
+// global-load mapping (0: rows across lanes, 1: K chunks across lanes).
+int64_t sectors_for(int map, int rows, int chunk, int elem_bytes, int nrow_modes,
+                    const int64_t *row_ext, const int64_t *row_s, int nk, const int64_t *k_ext,
+                    const int64_t *k_s) {
+    const int KC = kBK / chunk;
+    std::vector<int64_t> secs;
+    for (int lane = 0; lane < 32; ++lane) {
+        int row, kc;
+        if (map == 1) { row = lane / KC; kc = lane % KC; }
+        else { row = lane % rows; kc = lane / rows; }
+        int64_t r = row, off = 0;
+        for (int m = 0; m < nrow_modes; ++m) {
+            off += (r % row_ext[m]) * row_s[m];
+            r /= row_ext[m];
+        }
+        int64_t k = (int64_t)kc * chunk;
+        for (int m = nk - 1; m >= 0; --m) {
+            off += (k % k_ext[m]) * k_s[m];
+            k /= k_ext[m];
+        }
+        secs.push_back(off * elem_bytes / 32);
+    }
+    std::sort(secs.begin(), secs.end());
+    return std::unique(secs.begin(), secs.end()) - secs.begin();
+}
+
+// 16-byte vector loads along K are legal when the innermost K mode is
+// contiguous, its extent is a multiple of the vector, every other stride of
+// the operand is a multiple of the vector and the base is 16-byte aligned.
+bool vec_ok(const void *base, int vec, int nrow_modes, const int64_t *row_s, int nk, const int64_t *k_ext,
+            const int64_t *k_s) {
+    if (nk == 0 || ((uintptr_t)base & 15) != 0) return false;
+    if (k_s[nk - 1] != 1 || k_ext[nk - 1] % vec != 0) return false;
+    for (int m = 0; m < nrow_modes; ++m)
+        if (row_s[m] % vec != 0) return false;
+    for (int m = 0; m < nk - 1; ++m)
+        if (k_s[m] % vec != 0) return false;
+    return true;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool encoder() {
+    if (!g_encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    return true;
+}
+
+// Describes one input as a rank-5 TMA tensor over its own modes and stride
+// so that one box is one pipeline stage: ROWS tile rows along its first row
+// mode, the stage's BK K positions along its K modes.  Returns false when
+// TMA cannot describe it (the operand then takes the global-load path).
+// nrow/row_ext/row_s: the operand's row modes (M for A, N for B), first
+// mode fastest; K modes as in the descriptor (outermost first).
+bool plan_tma_operand(const Plan &p, int opnd, const void *base, int in_bytes, int rows, int nrow,
+                      const int64_t *row_ext, const int64_t *row_s, int nk, const int64_t *k_ext,
+                      const int64_t *k_s, GettDesc &d, CUtensorMap &map) {
+    const int o = opnd == OP_A ? 0 : 1;
+    if (((uintptr_t)base & 15) != 0 || nrow < 1) return false;
+    if (row_ext[0] % rows != 0) return false;  // tiles must be boxes of the first row mode
+    // the stage's K positions: whole innermost K modes, then part of the next
+    int64_t cover = 1;
+    std::vector<int64_t> kbox(nk, 1);
+    int m = nk - 1;
+    for (; m >= 0 && cover < kBKT; --m) {
+        if (cover * k_ext[m] <= kBKT) {
+            kbox[m] = k_ext[m];
+            cover *= k_ext[m];
+        } else {
+            if (k_ext[m] % (kBKT / cover) != 0 || kBKT % cover != 0) return false;
+            kbox[m] = kBKT / cover;
+            cover = kBKT;
+        }
+    }
+    int64_t K = 1;
+    for (int x = 0; x < nk; ++x) K *= k_ext[x];
+    if (cover != kBKT && cover != K) return false;
+    // tensor dimensions: the operand's own modes (split K modes share one),
+    // the stride-1 mode first
+    struct Dim { int64_t ext, stride; int64_t box; };
+    std::vector<Dim> dims;
+    auto dim_of_stride = [&](int64_t stride) -> int {
+        for (size_t x = 0; x < dims.size(); ++x)
+            if (dims[x].stride == stride) return (int)x;
+        return -1;
+    };
+    const Layout &L = p.op[opnd];
+    for (int x = 0; x < L.n; ++x) dims.push_back({p.ext[L.idx[x]], L.stride[x], 1});
+    std::stable_sort(dims.begin(), dims.end(), [](const Dim &a, const Dim &b) { return a.stride < b.stride; });
+    if (dims.empty() || dims[0].stride != 1 || (int)dims.size() > kTmaRank) return false;
+    for (int x = 0; x < nrow; ++x) {
+        int dd = dim_of_stride(row_s[x]);
+        if (dd < 0) return false;
+        d.row_dim[o][x] = dd;
+        if (x == 0) dims[dd].box = rows;
+    }
+    for (int x = 0; x < nk; ++x) {
+        // a split K mode has stride = base stride * inner extent: map it to
+        // the tensor dimension of its base stride with a multiplier
+        int dd = dim_of_stride(k_s[x]);
+        int64_t mul = 1;
+        if (dd < 0) {
+            for (size_t y = 0; y < dims.size() && dd < 0; ++y)
+                if (dims[y].stride > 0 && k_s[x] % dims[y].stride == 0 && k_s[x] / dims[y].stride < dims[y].ext &&
+                    dims[y].ext % (k_s[x] / dims[y].stride) == 0) {
+                    dd = (int)y;
+                    mul = k_s[x] / dims[y].stride;
+                }
+            if (dd < 0) return false;
+        }
+        d.k_dim[o][x] = dd;
+        d.k_mul[o][x] = mul;
+        if (kbox[x] > 1) dims[dd].box = std::max<int64_t>(dims[dd].box, kbox[x] * mul);
+    }
+    // box limits and the 16-byte rules
+    for (auto &dm : dims)
+        if (dm.box > 256) return false;
+    if ((dims[0].box * in_bytes) % 16 != 0) return false;
+    for (size_t x = 1; x < dims.size(); ++x)
+        if ((dims[x].stride * in_bytes) % 16 != 0) return false;
+    // staging offsets: box laid out with dimension 0 fastest
+    std::vector<int64_t> bstride(dims.size(), 1);
+    for (size_t x = 1; x < dims.size(); ++x) bstride[x] = bstride[x - 1] * dims[x - 1].box;
+    int64_t box_elems = bstride.back() * dims.back().box;
+    if (box_elems != (int64_t)rows * kBKT && box_elems != (int64_t)rows * K) return false;
+    d.srow[o] = (int)bstride[d.row_dim[o][0]];
+    bool v4 = true;
+    for (int k = 0; k < kBKT; ++k) {
+        int64_t kk = k, off = 0;
+        bool valid = k < K;
+        for (int x = nk - 1; x >= 0; --x) {
+            int64_t v = kk % kbox[x];
+            kk /= kbox[x];
+            off += v * d.k_mul[o][x] * bstride[d.k_dim[o][x]];
+        }
+        d.sk[o][k] = valid ? (int)off : 0;
+        if (k % 4 == 0 && (off % 4 != 0)) v4 = false;
+        if (k % 4 != 0 && off != d.sk[o][k - 1] + 1) v4 = false;
+    }
+    if (d.srow[o] % 4 != 0 || in_bytes != 4) v4 = false;
+    d.sk_vec4[o] = v4 ? 1 : 0;
+    if (K < kBKT) return false;  // zero-padded K positions would read staged data
+    // encode (rank 5: unused dimensions have extent 1)
+    if (!encoder()) return false;
+    cuuint64_t gdim[kTmaRank], gstride[kTmaRank - 1];
+    cuuint32_t box[kTmaRank], estr[kTmaRank];
+    int64_t span = 16;
+    for (auto &dm : dims) span = std::max<int64_t>(span, dm.stride * dm.ext * in_bytes);
+    span = (span + 15) / 16 * 16;
+    for (int x = 0; x < kTmaRank; ++x) {
+        const bool real = x < (int)dims.size();
+        gdim[x] = real ? (cuuint64_t)dims[x].ext : 1;
+        box[x] = real ? (cuuint32_t)dims[x].box : 1;
+        estr[x] = 1;
+        if (x > 0) gstride[x - 1] = real ? (cuuint64_t)(dims[x].stride * in_bytes) : (cuuint64_t)span;
+    }
+    CUtensorMapDataType dt = in_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                           : (p.dtype == TC_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    CUresult r = g_encode(&map, dt, kTmaRank, const_cast<void *>(base), gdim, gstride, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    for (int x = (int)dims.size(); x < kTmaRank; ++x) {
+        // unused dimensions: nothing maps there
+    }
+    return true;
 }
 
 }  // namespace
@@ -543,19 +1009,50 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
         return ids;
     };
     std::vector<int> mi = by_c_stride(p.freeA), ni = by_c_stride(p.freeB);
-    // K order: the innermost K mode is the contracted index with the smallest
-    // stride in the larger input, so that operand streams along K
+    const int in_bytes = (p.dtype == TC_BF16 || p.dtype == TC_F16) ? 2 : 4;
+    const int vec = 16 / in_bytes;
+    // K order.  The innermost K mode is the contracted index with the
+    // smallest stride in the larger input, so that operand streams along K.
+    // When the other input is contiguous along a different contracted index
+    // (A = iaj against B = jbic), the innermost index is split into
+    // (outer, vec) and the other input's contiguous index goes between them:
+    // a K stage then covers several values of it (whole 32-byte sectors, or
+    // a TMA box at least 16 bytes wide) while the larger input keeps 16-byte
+    // vectors.
     int64_t sizeA = 1, sizeB = 1;
     for (int m = 0; m < p.op[OP_A].n; ++m) sizeA *= p.ext[p.op[OP_A].idx[m]];
     for (int m = 0; m < p.op[OP_B].n; ++m) sizeB *= p.ext[p.op[OP_B].idx[m]];
-    const int big = sizeB >= sizeA ? OP_B : OP_A;
+    const int big = sizeB >= sizeA ? OP_B : OP_A, small = big == OP_B ? OP_A : OP_B;
     std::vector<int> ki(p.contracted);
     std::stable_sort(ki.begin(), ki.end(), [&](int x, int y) {
         return p.op[big].stride_of(x) > p.op[big].stride_of(y);
     });
+    struct KMode { int64_t ext, sA, sB; };
+    std::vector<KMode> kmodes;
+    for (int id : ki) kmodes.push_back({p.ext[id], p.op[OP_A].stride_of(id), p.op[OP_B].stride_of(id)});
+    if (ki.size() >= 2) {
+        const int inner = ki.back();
+        int other = -1;
+        for (int id : ki)
+            if (id != inner && p.op[small].stride_of(id) == 1) other = id;
+        const int64_t ein = p.ext[inner];
+        if (other >= 0 && p.op[big].stride_of(inner) == 1 && ein % vec == 0 && ein > vec &&
+            p.op[small].stride_of(inner) != 1) {
+            std::vector<KMode> km;
+            for (int id : ki)
+                if (id != inner && id != other)
+                    km.push_back({p.ext[id], p.op[OP_A].stride_of(id), p.op[OP_B].stride_of(id)});
+            const int64_t sAi = p.op[OP_A].stride_of(inner), sBi = p.op[OP_B].stride_of(inner);
+            km.push_back({ein / vec, sAi * vec, sBi * vec});
+            km.push_back({p.ext[other], p.op[OP_A].stride_of(other), p.op[OP_B].stride_of(other)});
+            km.push_back({(int64_t)vec, sAi, sBi});
+            kmodes = km;
+        }
+    }
     d.nm = (int)mi.size();
     d.nn = (int)ni.size();
-    d.nk = (int)ki.size();
+    d.nk = (int)kmodes.size();
+    if (d.nk > kMaxModes) return fail(TC_ERROR_INVALID_SPEC, "too many contracted modes for GETT");
     d.M = d.N = d.K = 1;
     for (int m = 0; m < d.nm; ++m) {
         int id = mi[m];
@@ -572,16 +1069,34 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
         d.N *= p.ext[id];
     }
     for (int m = 0; m < d.nk; ++m) {
-        int id = ki[m];
-        d.k_ext[m] = p.ext[id];
-        d.k_sA[m] = p.op[OP_A].stride_of(id);
-        d.k_sB[m] = p.op[OP_B].stride_of(id);
-        d.K *= p.ext[id];
+        d.k_ext[m] = kmodes[m].ext;
+        d.k_sA[m] = kmodes[m].sA;
+        d.k_sB[m] = kmodes[m].sB;
+        d.K *= kmodes[m].ext;
     }
-    const int64_t kinA = d.nk ? d.k_sA[d.nk - 1] : 1, kinB = d.nk ? d.k_sB[d.nk - 1] : 1;
-    const int64_t rowA = d.nm ? d.m_sA[0] : INT64_MAX, rowB = d.nn ? d.n_sB[0] : INT64_MAX;
-    d.a_kfast = kinA <= rowA;
-    d.b_kfast = kinB <= rowB;
+    const int chunk = p.dtype == TC_TF32 ? 4 : 8;
+    int bn = p.gett_bn == 128 || p.gett_bn == 256 ? p.gett_bn : (d.N >= 256 ? 256 : 128);
+    // TMA staging for each operand TMA can describe (tiles of 128 x 256)
+    CUtensorMap tmA, tmB;
+    std::memset(&tmA, 0, sizeof(tmA));
+    std::memset(&tmB, 0, sizeof(tmB));
+    bool tma = false;
+    if (p.gett_tma && bn == 256) {
+        d.tma[0] = plan_tma_operand(p, OP_A, A, in_bytes, kBM, d.nm, d.m_ext, d.m_sA, d.nk, d.k_ext, d.k_sA, d, tmA);
+        d.tma[1] = plan_tma_operand(p, OP_B, B, in_bytes, 256, d.nn, d.n_ext, d.n_sB, d.nk, d.k_ext, d.k_sB, d, tmB);
+        tma = d.tma[0] || d.tma[1];
+        d.tma_bytes = (uint32_t)((d.tma[0] ? kBM * kBKT * in_bytes : 0) + (d.tma[1] ? 256 * kBKT * in_bytes : 0));
+    }
+    // global-load mappings (used by operands without TMA staging)
+    auto pick = [&](const void *base, int rows, int nrow, const int64_t *rext, const int64_t *rs,
+                    const int64_t *ks) {
+        if (vec_ok(base, vec, nrow, rs, d.nk, d.k_ext, ks)) return 2;
+        int64_t s0 = sectors_for(0, rows, chunk, in_bytes, nrow, rext, rs, d.nk, d.k_ext, ks);
+        int64_t s1 = sectors_for(1, rows, chunk, in_bytes, nrow, rext, rs, d.nk, d.k_ext, ks);
+        return s1 < s0 ? 1 : 0;
+    };
+    d.a_map = pick(A, kBM, d.nm, d.m_ext, d.m_sA, d.k_sA);
+    d.b_map = pick(B, bn, d.nn, d.n_ext, d.n_sB, d.k_sB);
     d.A = A;
     d.B = B;
     d.C = (float *)C;
@@ -591,13 +1106,12 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     d.nprod = p.split_products;
     d.status = p.dev_status;
     d.tiles_m = (d.M + kBM - 1) / kBM;
-    const int bn = d.N >= 256 ? 256 : 128;
     cudaStream_t st = (cudaStream_t)stream;
     switch (p.dtype) {
-    case TC_BF16X3: return launch_kind<GK_BF16X3>(d, bn, st);
-    case TC_BF16: return launch_kind<GK_BF16>(d, bn, st);
-    case TC_F16: return launch_kind<GK_F16>(d, bn, st);
-    case TC_TF32: return launch_kind<GK_TF32>(d, bn, st);
+    case TC_BF16X3: return launch_kind<GK_BF16X3>(d, bn, tma, tmA, tmB, st);
+    case TC_BF16: return launch_kind<GK_BF16>(d, bn, tma, tmA, tmB, st);
+    case TC_F16: return launch_kind<GK_F16>(d, bn, tma, tmA, tmB, st);
+    case TC_TF32: return launch_kind<GK_TF32>(d, bn, tma, tmA, tmB, st);
     default: return fail(TC_ERROR_UNSUPPORTED_DTYPE, "dtype has no tensor-core GETT");
     }
 }

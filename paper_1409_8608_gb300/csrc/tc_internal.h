@@ -57,6 +57,8 @@ struct Plan {
     std::vector<Algorithm> algs;    // algs[0] is the fused GETT
     int selected = 0;
     int split_products = 6;         // TC_BF16X3: 3, 6 or 9 slice products
+    int gett_bn = 0;                // tensor-core GETT tile width (0: by N)
+    int gett_tma = 1;               // tensor-core GETT: TMA staging where legal
     // device resources, created lazily by the first execute
     int device = -1;
     void *workspace = nullptr;

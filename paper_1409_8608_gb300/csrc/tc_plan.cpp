@@ -396,6 +396,21 @@ tc_status tc_plan_set_split(tc_plan plan, int32_t products) {
     return TC_SUCCESS;
 }
 
+tc_status tc_plan_set_gett_tile(tc_plan plan, int32_t width) {
+    if (!plan) return fail(TC_ERROR_INVALID_ARGUMENT, "plan is NULL");
+    if (width != 0 && width != 128 && width != 256)
+        return fail(TC_ERROR_INVALID_ARGUMENT, "GETT tile width must be 0, 128 or 256");
+    plan->p.gett_bn = width;
+    return TC_SUCCESS;
+}
+
+tc_status tc_plan_set_gett_tma(tc_plan plan, int32_t enable) {
+    if (!plan) return fail(TC_ERROR_INVALID_ARGUMENT, "plan is NULL");
+    if (enable != 0 && enable != 1) return fail(TC_ERROR_INVALID_ARGUMENT, "enable must be 0 or 1");
+    plan->p.gett_tma = enable;
+    return TC_SUCCESS;
+}
+
 tc_status tc_plan_flops(tc_plan plan, double *flops) {
     if (!plan || !flops) return fail(TC_ERROR_INVALID_ARGUMENT, "NULL argument");
     double f = 2.0;

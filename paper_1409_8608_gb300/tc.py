@@ -64,6 +64,8 @@ SIGNATURES = {
     "tc_plan_device_status": (ctypes.c_int, [_VP]),
     "tc_plan_flops": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "tc_plan_set_split": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "tc_plan_set_gett_tile": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "tc_plan_set_gett_tma": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tc_last_error": (ctypes.c_char_p, []),
 }
@@ -185,6 +187,14 @@ def tc_plan_set_split(plan, products):
     _check(load().tc_plan_set_split(plan, int(products)), "tc_plan_set_split")
 
 
+def tc_plan_set_gett_tile(plan, width):
+    _check(load().tc_plan_set_gett_tile(plan, int(width)), "tc_plan_set_gett_tile")
+
+
+def tc_plan_set_gett_tma(plan, enable):
+    _check(load().tc_plan_set_gett_tma(plan, int(enable)), "tc_plan_set_gett_tma")
+
+
 def tc_plan_flops(plan):
     v = ctypes.c_double()
     _check(load().tc_plan_flops(plan, ctypes.byref(v)), "tc_plan_flops")
@@ -221,6 +231,12 @@ class Plan:
 
     def set_split(self, products):
         tc_plan_set_split(self.handle, products)
+
+    def set_gett_tile(self, width):
+        tc_plan_set_gett_tile(self.handle, width)
+
+    def set_gett_tma(self, enable):
+        tc_plan_set_gett_tma(self.handle, enable)
 
     def device_status(self):
         tc_plan_device_status(self.handle)

@@ -173,3 +173,45 @@ def test_large_bench_shape_sampled(tcmod):
     err = float(np.max(np.abs(got[lin] - want) / scale))
     assert err <= (256 + 4) * U32, err
     assert np.isfinite(got).all()
+
+
+TMA_CASES = [
+    ("abc=iaj,jbic", [256, 512, 3, 16, 16]),  # the permuted workload's layout: split K order
+    ("ab=aij,jib", [256, 512, 16, 16]),       # M-contiguous A, K-contiguous B
+    ("abc=ai,ibc", [128, 256, 3, 64]),        # the precision-form layout
+]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("spec,ext", TMA_CASES)
+def test_tma_staging_matches_global_loads_bitwise(tcmod, spec, ext, dtype):
+    # both input paths must hand the tensor cores the same operand bits
+    A, B, _ = synth.uniform_operands(spec, ext, seed=4)
+    dA, dB, (Ar, Br) = device_inputs(dtype, A, B)
+    n = synth.dense_sizes(spec, ext)[0]
+    outs = []
+    for tma in (1, 0):
+        plan = tcmod.Plan(spec, ext, dtype=dtype)
+        plan.set_gett_tma(tma)
+        dC = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda:0")
+        plan.execute(dA, dB, dC)
+        torch.cuda.synchronize()
+        plan.device_status()
+        plan.close()
+        outs.append(dC.double().cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]), float(np.nanmax(np.abs(outs[0] - outs[1])))
+    want = oc.contract(spec, ext, Ar, Br)
+    scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
+    K = ksize(spec, ext)
+    bound = (K + 4) * U32 if dtype == "bf16x3" else (K + 1) * U32 / (1 - (K + 1) * U32)
+    assert float(np.max(np.abs(outs[0] - want) / scale)) <= bound
+
+
+def test_tma_integers_exact(tcmod):
+    spec, ext = "abc=iaj,jbic", [256, 256, 2, 16, 16]
+    A, B, _ = synth.integer_operands(spec, ext, seed=6)
+    want = oc.contract(spec, ext, A, B)
+    for dtype in DTYPES:
+        dA, dB, _ = device_inputs(dtype, A, B)
+        got = run_gett(tcmod, spec, ext, dtype, dA, dB)
+        assert np.array_equal(got, want), dtype
