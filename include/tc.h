@@ -174,6 +174,89 @@ tc_status tc_plan_set_gett_tma(tc_plan plan, int32_t enable);
 /* 2 * product of all extents. */
 tc_status tc_plan_flops(tc_plan plan, double *flops);
 
+/* ---- Performance prediction (Section 3) ------------------------------
+ *
+ * The analysis runs at one of two granularities:
+ *   0  the paper's: the algorithm's sliced loops around one BLAS call;
+ *   1  the device's: the device-wide phases (contracted loops that enclose
+ *      a free loop) around one phase launch.
+ * Sizes are in units of elem_size bytes per element (pass 1 to count
+ * elements, as the paper's worked example does); cache_size and line_size
+ * use the same unit (the L2 and its 128-byte line on the device). */
+
+typedef struct {
+    int32_t kind;       /* 0 steady state (prefetch emulated, Section 3.3),
+                           1 prefetch failure once per line (Section 3.4),
+                           2 first iteration of loop `depth` (Section 3.5) */
+    int32_t depth;      /* loop position of a first-iteration case, else -1 */
+    int64_t count;      /* invocations this case stands for; the counts of
+                           all cases sum to the product of the loop extents */
+    int32_t omit;       /* 1 when the setup touches operands only */
+    int32_t n_items;    /* length of the setup list */
+} tc_pred_case;
+
+typedef struct {
+    int32_t kind;       /* 0 touch an operand slice, 1 remote region */
+    int32_t operand;    /* 0 A, 1 B, 2 C; -1 for a remote region */
+    int64_t size;       /* in the caller's unit */
+} tc_setup_item;
+
+/* Access distances (Section 3.2) of the kernel's A, B and C slices in the
+ * steady state: for each, the summed size of the regions touched since its
+ * previous access.  dist receives 3 values (A, B, C). */
+tc_status tc_access_distances(tc_plan plan, int32_t alg_id, int32_t granularity,
+                              int64_t elem_size, int64_t *dist);
+
+/* The prediction cases of one algorithm (steady, prefetch failure, first
+ * iterations), each with its invocation count and setup-list length. */
+tc_status tc_prediction_cases(tc_plan plan, int32_t alg_id, int32_t granularity,
+                              int64_t elem_size, int64_t cache_size, int64_t line_size,
+                              tc_pred_case *out, int32_t capacity, int32_t *count);
+
+/* The setup list of case `case_index` (Section 3.2): operands in order of
+ * decreasing access distance, each followed by a remote region so that
+ * what follows an operand sums to its distance, cut at the front to at
+ * most 5/4 of cache_size. */
+tc_status tc_setup_list(tc_plan plan, int32_t alg_id, int32_t granularity, int32_t case_index,
+                        int64_t elem_size, int64_t cache_size, int64_t line_size,
+                        tc_setup_item *out, int32_t capacity, int32_t *count);
+
+/* Predicts the run time (seconds) of algorithms without running them
+ * (Section 3 on the device): for each case of the device-granularity
+ * analysis (first phase, steady phases) the setup list is replayed with
+ * touch kernels and L2-sized remote reads, then one representative phase
+ * runs over a few waves of its work, timed ten times with CUDA events; the
+ * median, scaled to the whole phase and weighted by the case's count, sums
+ * to the prediction.  The GETT runs a few waves of its real tiles.
+ * alg_ids: n ids, or NULL for every algorithm (seconds then holds
+ * tc_algorithm_count entries).  A, B, C: device buffers laid out as the plan
+ * describes, or NULL for zero-filled scratch the call allocates and frees.
+ * seconds[i] < 0 marks an algorithm that cannot run with the plan's dtype
+ * (the loop nests run in FP64 and FP32 only).  Synchronises the stream.
+ * The results stay in the plan for tc_plan_select_best. */
+tc_status tc_predict(tc_plan plan, const int32_t *alg_ids, int32_t n, const void *A,
+                     const void *B, void *C, double *seconds, void *stream);
+
+/* Selects the algorithm with the smallest prediction of the last
+ * tc_predict (ties: lower id) and stores its id in *best (may be NULL). */
+tc_status tc_plan_select_best(tc_plan plan, int32_t *best);
+
+/* Autotuner for the tensor-core GETT: predicts every tile configuration
+ * (tile width 128 or 256, TMA staging on or off) with the same
+ * micro-benchmark and keeps the fastest in the plan, reporting it in
+ * *width and *tma (either may be NULL).  Results are cached per (spec,
+ * extents, strides, dtype, split products, device); a cached plan key is
+ * answered without running anything.  FP64/FP32 plans have nothing to tune
+ * (width 0, tma 1).  Clears the plan's stored predictions. */
+tc_status tc_autotune(tc_plan plan, const void *A, const void *B, void *C, void *stream,
+                      int32_t *width, int32_t *tma);
+
+/* Writes / merges the process-wide tuning cache as JSON lines
+ * ({"key": ..., "gett_tile": ..., "gett_tma": ...}), so that re-planning
+ * in a later process is free. */
+tc_status tc_tuning_cache_save(const char *path);
+tc_status tc_tuning_cache_load(const char *path);
+
 /* Static description of a status code.  Never NULL. */
 const char *tc_status_string(tc_status status);
 

@@ -435,7 +435,7 @@ tc_status launch_gather(const GatherDesc &g, cudaStream_t st) {
 
 template <typename T>
 tc_status launch_copy(const Plan &p, int o, const OpView &v, const char *src_base,
-                      void *dst, bool scatter, cudaStream_t st) {
+                      void *dst, bool scatter, cudaStream_t st, double frac = 1.0) {
     GatherDesc g;
     std::memset(&g, 0, sizeof(g));
     g.n = (int)v.copy_ids.size();
@@ -447,7 +447,7 @@ tc_status launch_copy(const Plan &p, int o, const OpView &v, const char *src_bas
         g.ss[m] = scatter ? ws : orig;
         g.sd[m] = scatter ? orig : ws;
     }
-    g.total = v.elems;
+    g.total = frac >= 1.0 ? v.elems : std::max<int64_t>(1, (int64_t)(v.elems * frac));
     g.src = scatter ? dst : src_base;
     g.dst = scatter ? (void *)src_base : dst;
     return launch_gather<T>(g, st);
@@ -455,7 +455,7 @@ tc_status launch_copy(const Plan &p, int o, const OpView &v, const char *src_bas
 
 template <typename T>
 tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *B,
-                   T beta, T *C, cudaStream_t st) {
+                   T beta, T *C, cudaStream_t st, const Probe *probe) {
     NestLayout L = layout_for(p, alg);
     char *ws = (char *)p.workspace;
     const char *base[3] = {(const char *)A, (const char *)B, (const char *)C};
@@ -514,19 +514,20 @@ tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *
     // run every phase on the workspace, scatter back at the end
     void *Cptr = C;
     tc_status s;
+    const bool first_probe = !probe || probe->first;
+    const double frac0 = probe ? probe->fraction : 1.0;
     if (L.view[OP_C].copied) {
         Cptr = ws + L.ws_offset[OP_C];
-        if (init0 != 2) {
-            s = launch_copy<T>(p, OP_C, L.view[OP_C], base[OP_C], Cptr, false, st);
+        if (init0 != 2 && first_probe) {
+            s = launch_copy<T>(p, OP_C, L.view[OP_C], base[OP_C], Cptr, false, st, frac0);
             if (s != TC_SUCCESS) return s;
         }
     }
 
     const int nph = (int)L.phase_pos.size();
-    std::vector<int64_t> ph(nph, 0);
-    bool first = true;
-    int changed_from = 0;  // outermost phase digit that changed
-    for (;;) {
+    // one phase: its copies, then its kernel over `frac` of the work
+    auto run_phase = [&](const std::vector<int64_t> &ph, bool first, int changed_from,
+                         double frac) -> tc_status {
         // operand bases for this phase: fixed contracted indices applied
         const char *opb[2];
         for (int o = 0; o < 2; ++o) {
@@ -545,13 +546,14 @@ tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *
                     if (L.phase_pos[k] <= level) redo = true;
             }
             if (redo) {
-                s = launch_copy<T>(p, o, L.view[o], opb[o], dst, false, st);
-                if (s != TC_SUCCESS) return s;
+                tc_status cs = launch_copy<T>(p, o, L.view[o], opb[o], dst, false, st, frac);
+                if (cs != TC_SUCCESS) return cs;
             }
             if (o == 0) Aeff = dst;
             else Beff = dst;
         }
         const int init = first ? init0 : 0;
+        auto cut = [&](int64_t n) { return frac >= 1.0 ? n : std::max<int64_t>(1, (int64_t)(n * frac)); };
         if (tiled) {
             td.A = Aeff;
             td.B = Beff;
@@ -561,25 +563,42 @@ tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *
                 constexpr int BM = 64, BN = 64;
                 td.tiles_m = (td.M + BM - 1) / BM;
                 td.tiles_n = (td.N + BN - 1) / BN;
-                int64_t grid = td.tiles_m * td.tiles_n * ntasks;
+                int64_t grid = cut(td.tiles_m * td.tiles_n * ntasks);
                 tile_kernel<T, 64, 64, 16, 4, 4><<<(unsigned)grid, 256, 0, st>>>(td);
             } else {
                 constexpr int BM = 128, BN = 128;
                 td.tiles_m = (td.M + BM - 1) / BM;
                 td.tiles_n = (td.N + BN - 1) / BN;
-                int64_t grid = td.tiles_m * td.tiles_n * ntasks;
+                int64_t grid = cut(td.tiles_m * td.tiles_n * ntasks);
                 tile_kernel<T, 128, 128, 8, 8, 8><<<(unsigned)grid, 256, 0, st>>>(td);
             }
         } else {
-            pd.A = Aeff;
-            pd.B = Beff;
-            pd.C = Cptr;
-            pd.init = init;
-            int64_t grid = grid_for(pd.total, 256);
-            elementwise_kernel<T><<<(unsigned)grid, 256, 0, st>>>(pd);
+            PhaseDesc q = pd;
+            q.A = Aeff;
+            q.B = Beff;
+            q.C = Cptr;
+            q.init = init;
+            q.total = cut(pd.total);
+            int64_t grid = grid_for(q.total, 256);
+            elementwise_kernel<T><<<(unsigned)grid, 256, 0, st>>>(q);
         }
         cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+        return e == cudaSuccess ? TC_SUCCESS : fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+    };
+
+    if (probe) {
+        std::vector<int64_t> ph(nph, 0);
+        for (int k = 0; k < nph && k < (int)probe->phase.size(); ++k)
+            ph[k] = std::min<int64_t>(probe->phase[k], p.ext[alg.loops[L.phase_pos[k]]] - 1);
+        return run_phase(ph, probe->first, probe->changed_from, probe->fraction);
+    }
+
+    std::vector<int64_t> ph(nph, 0);
+    bool first = true;
+    int changed_from = 0;  // outermost phase digit that changed
+    for (;;) {
+        s = run_phase(ph, first, changed_from, 1.0);
+        if (s != TC_SUCCESS) return s;
         first = false;
         // advance the phase odometer (innermost phase loop fastest)
         int k = nph - 1;
@@ -602,7 +621,7 @@ tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *
 // of A, N = free indices of B, K = contracted indices.
 template <typename T>
 tc_status run_gett_simt(Plan &p, T alpha, const T *A, const T *B, T beta, T *C,
-                        cudaStream_t st) {
+                        cudaStream_t st, const Probe *probe) {
     TileDesc td;
     std::memset(&td, 0, sizeof(td));
     auto by_c_stride = [&](std::vector<int> ids) {
@@ -644,20 +663,48 @@ tc_status run_gett_simt(Plan &p, T alpha, const T *A, const T *B, T beta, T *C,
     int64_t kinB = td.red.n ? td.red.sB[td.red.n - 1] : 0;
     td.a_m_fast = td.m.n ? (td.m.sA[0] <= kinA || kinA == 0) : 0;
     td.b_n_fast = td.n.n ? (td.n.sB[0] <= kinB || kinB == 0) : 0;
+    auto cut = [&](int64_t n) {
+        return !probe || probe->fraction >= 1.0 ? n : std::max<int64_t>(1, (int64_t)(n * probe->fraction));
+    };
     if (sizeof(T) == 8) {
         td.tiles_m = (td.M + 63) / 64;
         td.tiles_n = (td.N + 63) / 64;
-        tile_kernel<T, 64, 64, 16, 4, 4><<<(unsigned)(td.tiles_m * td.tiles_n), 256, 0, st>>>(td);
+        tile_kernel<T, 64, 64, 16, 4, 4><<<(unsigned)cut(td.tiles_m * td.tiles_n), 256, 0, st>>>(td);
     } else {
         td.tiles_m = (td.M + 127) / 128;
         td.tiles_n = (td.N + 127) / 128;
-        tile_kernel<T, 128, 128, 8, 8, 8><<<(unsigned)(td.tiles_m * td.tiles_n), 256, 0, st>>>(td);
+        tile_kernel<T, 128, 128, 8, 8, 8><<<(unsigned)cut(td.tiles_m * td.tiles_n), 256, 0, st>>>(td);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? TC_SUCCESS : fail(TC_ERROR_CUDA, cudaGetErrorString(e));
 }
 
 }  // namespace
+
+int64_t nest_phase_items(const Plan &p, const Algorithm &alg, bool *tiled) {
+    NestLayout L = layout_for(p, alg);
+    int64_t ntasks = 1;
+    for (int id : L.task_ids) ntasks *= p.ext[id];
+    if (alg.kernel == TC_KERNEL_GEMM) {
+        *tiled = true;
+        const int64_t bm = p.dtype == TC_F64 ? 64 : 128;
+        return ((p.ext[L.out_ids[0]] + bm - 1) / bm) * ((p.ext[L.out_ids[1]] + bm - 1) / bm) * ntasks;
+    }
+    *tiled = false;
+    int64_t nout = 1;
+    for (int id : L.out_ids) nout *= p.ext[id];
+    return nout * ntasks;
+}
+
+int64_t gett_items(const Plan &p) {
+    int64_t M = 1, N = 1;
+    for (int id : p.freeA) M *= p.ext[id];
+    for (int id : p.freeB) N *= p.ext[id];
+    if (p.dtype == TC_F64) return ((M + 63) / 64) * ((N + 63) / 64);
+    if (p.dtype == TC_F32) return ((M + 127) / 128) * ((N + 127) / 128);
+    const int64_t bn = p.gett_bn ? p.gett_bn : (N >= 256 ? 256 : 128);
+    return ((M + 127) / 128) * ((N + bn - 1) / bn);
+}
 
 size_t nest_workspace_bytes(const Plan &p, const Algorithm &alg) {
     return layout_for(p, alg).ws_bytes;
@@ -692,7 +739,7 @@ tc_status ensure_device_resources(Plan &p, size_t workspace_bytes) {
 }
 
 tc_status exec_nest(Plan &p, const Algorithm &alg, const void *alpha, const void *A,
-                    const void *B, const void *beta, void *C, void *stream) {
+                    const void *B, const void *beta, void *C, void *stream, const Probe *probe) {
     if (p.dtype != TC_F64 && p.dtype != TC_F32)
         return fail(TC_ERROR_UNSUPPORTED_DTYPE,
                     "the loop-nest algorithms run in FP64 or FP32; use GETT (id 0) for tensor-core dtypes");
@@ -702,22 +749,22 @@ tc_status exec_nest(Plan &p, const Algorithm &alg, const void *alpha, const void
     cudaStream_t st = (cudaStream_t)stream;
     if (p.dtype == TC_F64)
         return run_nest<double>(p, alg, *(const double *)alpha, (const double *)A,
-                                (const double *)B, *(const double *)beta, (double *)C, st);
+                                (const double *)B, *(const double *)beta, (double *)C, st, probe);
     return run_nest<float>(p, alg, *(const float *)alpha, (const float *)A, (const float *)B,
-                           *(const float *)beta, (float *)C, st);
+                           *(const float *)beta, (float *)C, st, probe);
 }
 
 tc_status exec_gett_simt(Plan &p, const void *alpha, const void *A, const void *B,
-                         const void *beta, void *C, void *stream) {
+                         const void *beta, void *C, void *stream, const Probe *probe) {
     tc_status s = ensure_device_resources(p, 0);
     if (s != TC_SUCCESS) return s;
     p.last_stream = stream;
     cudaStream_t st = (cudaStream_t)stream;
     if (p.dtype == TC_F64)
         return run_gett_simt<double>(p, *(const double *)alpha, (const double *)A,
-                                     (const double *)B, *(const double *)beta, (double *)C, st);
+                                     (const double *)B, *(const double *)beta, (double *)C, st, probe);
     return run_gett_simt<float>(p, *(const float *)alpha, (const float *)A, (const float *)B,
-                                *(const float *)beta, (float *)C, st);
+                                *(const float *)beta, (float *)C, st, probe);
 }
 
 }  // namespace tc

@@ -50,9 +50,6 @@
 
 namespace tc {
 
-tc_status exec_gett_simt(Plan &p, const void *alpha, const void *A, const void *B,
-                         const void *beta, void *C, void *stream);
-
 namespace {
 
 enum GettKind { GK_BF16X3 = 0, GK_BF16 = 1, GK_F16 = 2, GK_TF32 = 3 };
@@ -99,6 +96,7 @@ struct GettDesc {
     int sk[2][kBKT];
     int sk_vec4[2];
     uint32_t tma_bytes;  // staged bytes per stage (both operands)
+    double tile_frac;    // micro-benchmark: run this fraction of the tiles
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -796,6 +794,7 @@ tc_status launch_kind(GettDesc &d, int bn, bool tma, const CUtensorMap &ta, cons
                       cudaStream_t st) {
     d.tiles_n = (d.N + bn - 1) / bn;
     d.num_tiles = d.tiles_m * d.tiles_n;
+    if (d.tile_frac < 1.0) d.num_tiles = std::max<int64_t>(1, (int64_t)(d.num_tiles * d.tile_frac));
     if (tma) {  // 16-K stages, staged input boxes, BN = 256
         if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 256, 3, kBKT, true>(d, ta, tb, st);
         else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 256, 3, kBKT, true>(d, ta, tb, st);
@@ -995,8 +994,8 @@ size_t gett_workspace_bytes(const Plan &) { return 0; }
 void gett_release(Plan &) {}
 
 tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, const void *beta,
-                    void *C, void *stream) {
-    if (p.dtype == TC_F64 || p.dtype == TC_F32) return exec_gett_simt(p, alpha, A, B, beta, C, stream);
+                    void *C, void *stream, const Probe *probe) {
+    if (p.dtype == TC_F64 || p.dtype == TC_F32) return exec_gett_simt(p, alpha, A, B, beta, C, stream, probe);
     tc_status s = ensure_device_resources(p, 0);
     if (s != TC_SUCCESS) return s;
     p.last_stream = stream;
@@ -1106,6 +1105,7 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     d.nprod = p.split_products;
     d.status = p.dev_status;
     d.tiles_m = (d.M + kBM - 1) / kBM;
+    d.tile_frac = probe ? probe->fraction : 1.0;
     cudaStream_t st = (cudaStream_t)stream;
     switch (p.dtype) {
     case TC_BF16X3: return launch_kind<GK_BF16X3>(d, bn, tma, tmA, tmB, st);

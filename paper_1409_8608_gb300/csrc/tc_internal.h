@@ -66,6 +66,20 @@ struct Plan {
     int *dev_status = nullptr;      // bounded-wait status word
     void *last_stream = nullptr;
     void *gett_state = nullptr;     // owned by the GETT executor
+    void *flush_buf = nullptr;      // predictor: remote regions / L2 flush
+    size_t flush_bytes = 0;
+    std::vector<double> predicted;  // last tc_predict result per algorithm (< 0: none)
+};
+
+// A micro-benchmark run of one algorithm (Section 3 restated for the
+// device): a nest runs one phase -- its copies and its kernel -- given by
+// the values of the phase loops, over `fraction` of the phase's work; the
+// GETT runs `fraction` of its tiles.
+struct Probe {
+    std::vector<int64_t> phase;  // phase-loop values, outermost first
+    bool first = true;           // the contraction's first phase (C from beta)
+    int changed_from = 0;        // outermost phase loop that advanced
+    double fraction = 1.0;
 };
 
 // error reporting (thread-local message)
@@ -78,10 +92,14 @@ size_t elem_bytes_c(tc_dtype dt);
 // device-side executors (tc_exec.cu, tc_gett.cu)
 tc_status exec_nest(Plan &p, const Algorithm &alg, const void *alpha,
                     const void *A, const void *B, const void *beta, void *C,
-                    void *stream);
+                    void *stream, const Probe *probe = nullptr);
 size_t nest_workspace_bytes(const Plan &p, const Algorithm &alg);
+int64_t nest_phase_items(const Plan &p, const Algorithm &alg, bool *tiled);
+int64_t gett_items(const Plan &p);
 tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B,
-                    const void *beta, void *C, void *stream);
+                    const void *beta, void *C, void *stream, const Probe *probe = nullptr);
+tc_status exec_gett_simt(Plan &p, const void *alpha, const void *A, const void *B,
+                         const void *beta, void *C, void *stream, const Probe *probe = nullptr);
 size_t gett_workspace_bytes(const Plan &p);
 void gett_release(Plan &p);
 tc_status ensure_device_resources(Plan &p, size_t workspace_bytes);

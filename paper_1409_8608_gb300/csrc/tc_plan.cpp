@@ -342,6 +342,7 @@ tc_status tc_plan_destroy(tc_plan plan) {
         gett_release(p);
         if (p.workspace) cudaFree(p.workspace);
         if (p.dev_status) cudaFree(p.dev_status);
+        if (p.flush_buf) cudaFree(p.flush_buf);
         cudaSetDevice(cur);
     }
     delete plan;

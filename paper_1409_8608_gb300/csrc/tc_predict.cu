@@ -1,0 +1,456 @@
+// Performance prediction on the device (Section 3 restated for the GPU),
+// algorithm ranking, the GETT autotuner and the tuning cache.
+//
+// The paper times one BLAS call in isolation after a setup that recreates
+// the cache state it meets inside the algorithm, repeats that ten times,
+// takes the median and weights it by the number of calls.  On the device the
+// unit that repeats is one phase launch (a contracted loop enclosing free
+// loops runs as a sequence of launches), so:
+//   * the cases come from the analysis at the device granularity: the first
+//     phase and the steady phases (tc_analysis.cpp), each with its count;
+//   * the setup list of a case is replayed with touch kernels (operand
+//     slices) and reads of a dedicated buffer (remote regions), truncated
+//     at 5/4 of the L2 size queried from the device;
+//   * the timed part is one representative phase -- its copies and its
+//     kernel -- over a fraction of its work of a few waves, scaled back up
+//     (the GETT runs a few waves of its real tiles);
+//   * each case is timed ten times with CUDA events; the median counts.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "tc_analysis.h"
+
+namespace tc {
+namespace {
+
+struct TouchDesc {
+    int n;
+    int64_t ext[kMaxModes];
+    int64_t stride[kMaxModes];  // elements
+    int64_t total;
+    const char *base;
+    int esz;
+};
+
+// Reads every element of a strided slice (brings it into L2).
+__global__ void __launch_bounds__(256) touch_kernel(const TouchDesc t, unsigned *sink) {
+    unsigned acc = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < t.total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e, off = 0;
+        for (int m = 0; m < t.n; ++m) {
+            off += (r % t.ext[m]) * t.stride[m];
+            r /= t.ext[m];
+        }
+        const char *ptr = t.base + off * t.esz;
+        acc ^= t.esz == 8 ? (unsigned)__ldcg((const unsigned long long *)ptr)
+                          : (t.esz == 4 ? __ldcg((const unsigned *)ptr) : (unsigned)__ldcg((const unsigned short *)ptr));
+    }
+    if (acc == 0x9E3779B9u) sink[0] = acc;  // never taken in practice; keeps the loads
+}
+
+// Reads a contiguous remote region (16-byte loads).
+__global__ void __launch_bounds__(256) remote_kernel(const uint4 *buf, int64_t n16, unsigned *sink) {
+    unsigned acc = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n16;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        uint4 v = __ldcg(buf + e);
+        acc ^= v.x ^ v.w;
+    }
+    if (acc == 0x9E3779B9u) sink[0] = acc;
+}
+
+int g_sms = 0;
+int64_t g_l2 = 0;
+
+void device_props() {
+    if (g_sms == 0) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev);
+        g_l2 = v > 0 ? v : (126ll << 20);
+        if (g_sms <= 0) g_sms = 1;
+    }
+}
+
+int64_t blocks_for(int64_t total) {
+    return std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)g_sms * 16));
+}
+
+struct Operands {
+    const void *A, *B;
+    void *C;
+};
+
+size_t elem_size(const Plan &p, int o) { return o == OP_C ? elem_bytes_c(p.dtype) : elem_bytes_ab(p.dtype); }
+
+int64_t span_elems(const Plan &p, int o) {
+    int64_t s = 1;
+    for (int m = 0; m < p.op[o].n; ++m) s += (p.ext[p.op[o].idx[m]] - 1) * p.op[o].stride[m];
+    return s;
+}
+
+// Replays a setup list: operand slices at the probed phase, remote
+// regions from the flush buffer.
+tc_status run_setup(Plan &p, const NestView &v, const std::vector<SetupItem> &setup,
+                    const std::vector<int64_t> &phase, const Operands &ops, unsigned *sink,
+                    cudaStream_t st) {
+    size_t roff = 0;
+    for (const SetupItem &it : setup) {
+        if (it.kind == 1) {
+            int64_t bytes = std::min<int64_t>(it.size, (int64_t)p.flush_bytes);
+            if (roff + bytes > p.flush_bytes) roff = 0;
+            int64_t n16 = bytes / 16;
+            if (n16 > 0)
+                remote_kernel<<<(unsigned)blocks_for(n16), 256, 0, st>>>(
+                    (const uint4 *)((char *)p.flush_buf + roff), n16, sink);
+            roff += (size_t)n16 * 16;
+            continue;
+        }
+        const int o = it.op;
+        TouchDesc t;
+        std::memset(&t, 0, sizeof(t));
+        const Layout &L = p.op[o];
+        int64_t off = 0;
+        for (int m = 0; m < L.n; ++m) {
+            const int id = L.idx[m];
+            if (v.kernel[id]) {
+                t.ext[t.n] = p.ext[id];
+                t.stride[t.n] = L.stride[m];
+                ++t.n;
+            } else {
+                for (size_t d = 0; d < v.loops.size(); ++d)
+                    if (v.loops[d] == id && d < phase.size()) off += phase[d] * L.stride[m];
+            }
+        }
+        t.total = 1;
+        for (int m = 0; m < t.n; ++m) t.total *= t.ext[m];
+        t.esz = (int)elem_size(p, o);
+        const char *base = o == OP_A ? (const char *)ops.A : (o == OP_B ? (const char *)ops.B : (const char *)ops.C);
+        t.base = base + off * t.esz;
+        touch_kernel<<<(unsigned)blocks_for(t.total), 256, 0, st>>>(t, sink);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? TC_SUCCESS : fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+}
+
+tc_status ensure_flush(Plan &p) {
+    device_props();
+    const size_t want = (size_t)(g_l2 * 5 / 4 + (1 << 20));
+    if (p.flush_bytes >= want) return TC_SUCCESS;
+    if (p.flush_buf) cudaFree(p.flush_buf);
+    p.flush_buf = nullptr;
+    p.flush_bytes = 0;
+    cudaError_t e = cudaMalloc(&p.flush_buf, want + 16);
+    if (e != cudaSuccess) return fail(TC_ERROR_OUT_OF_MEMORY, cudaGetErrorString(e));
+    cudaMemset(p.flush_buf, 0, want + 16);
+    p.flush_bytes = want;
+    return TC_SUCCESS;
+}
+
+const int kReps = 10;  // the paper's ten repetitions, median
+
+// Times `probe` after each replay of `setup`; returns the median seconds.
+tc_status time_case(Plan &p, int alg_id, const NestView &v, const std::vector<SetupItem> &setup,
+                    const Probe &probe, const Operands &ops, unsigned *sink, cudaStream_t st, double *sec) {
+    const Algorithm &alg = p.algs[alg_id];
+    const double one = 1.0, zero = 0.0;
+    const float onef = 1.0f, zerof = 0.0f;
+    const void *alpha = p.dtype == TC_F64 ? (const void *)&one : (const void *)&onef;
+    const void *beta = p.dtype == TC_F64 ? (const void *)&zero : (const void *)&zerof;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<double> t;
+    tc_status s = TC_SUCCESS;
+    for (int r = 0; r < kReps + 1 && s == TC_SUCCESS; ++r) {  // the first run warms up
+        s = run_setup(p, v, setup, probe.phase, ops, sink, st);
+        if (s != TC_SUCCESS) break;
+        cudaEventRecord(e0, st);
+        s = alg.kernel == TC_KERNEL_GETT ? exec_gett(p, alpha, ops.A, ops.B, beta, ops.C, st, &probe)
+                                         : exec_nest(p, alg, alpha, ops.A, ops.B, beta, ops.C, st, &probe);
+        cudaEventRecord(e1, st);
+        if (s != TC_SUCCESS) break;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            s = fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+            break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) t.push_back(ms * 1e-3);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != TC_SUCCESS) return s;
+    std::sort(t.begin(), t.end());
+    *sec = t[t.size() / 2];
+    return TC_SUCCESS;
+}
+
+// Fraction of one launch's work that covers about `waves` machine waves.
+double probe_fraction(int64_t items, bool tiled, int gett_tc) {
+    device_props();
+    int64_t target;
+    if (gett_tc) target = (int64_t)g_sms * 2;         // two tiles per persistent CTA
+    else if (tiled) target = (int64_t)g_sms * 8;      // several waves of tiles
+    else target = (int64_t)g_sms * 16 * 256 * 4;      // four grid-stride passes
+    return items <= target ? 1.0 : (double)target / (double)items;
+}
+
+tc_status predict_one(Plan &p, int alg_id, const Operands &ops, unsigned *sink, cudaStream_t st, double *out) {
+    const Algorithm &alg = p.algs[alg_id];
+    const bool tensor = p.dtype != TC_F64 && p.dtype != TC_F32;
+    if (alg.kernel != TC_KERNEL_GETT && tensor) {
+        *out = -1.0;  // the loop nests run in FP64 / FP32 only
+        return TC_SUCCESS;
+    }
+    device_props();
+    const int64_t esz = (int64_t)elem_bytes_ab(p.dtype);
+    if (alg.kernel == TC_KERNEL_GETT) {
+        // no loops: one case, repeated execution (Section 3.2, case 3)
+        Probe pr;
+        pr.first = true;
+        pr.fraction = probe_fraction(gett_items(p), true, tensor ? 1 : 0);
+        NestView v;
+        v.kernel.assign(p.nidx, true);
+        std::vector<SetupItem> none;
+        double t = 0;
+        tc_status s = time_case(p, alg_id, v, none, pr, ops, sink, st, &t);
+        if (s != TC_SUCCESS) return s;
+        *out = t / pr.fraction;
+        return TC_SUCCESS;
+    }
+    tc_status s = ensure_device_resources(p, nest_workspace_bytes(p, alg));
+    if (s != TC_SUCCESS) return s;
+    NestView v = nest_view(p, alg, 1);
+    const int n = (int)v.loops.size();
+    std::vector<Case> cases = analyse(p, alg, 1, esz, g_l2, 128);
+    bool tiled = false;
+    const int64_t items = nest_phase_items(p, alg, &tiled);
+    double total = 0;
+    for (const Case &c : cases) {
+        if (c.count <= 0) continue;
+        Probe pr;
+        pr.phase.assign(n, 0);
+        pr.fraction = probe_fraction(items, tiled, 0);
+        if (n == 0) {
+            pr.first = true;
+        } else if (c.kind == CASE_FIRST) {
+            pr.first = c.depth == 0;
+            pr.changed_from = std::max(0, c.depth - 1);
+            if (c.depth > 0) pr.phase[c.depth - 1] = 1;
+        } else {
+            pr.first = false;
+            pr.changed_from = n - 1;
+            pr.phase[n - 1] = 1;
+        }
+        double t = 0;
+        s = time_case(p, alg_id, v, c.omit ? std::vector<SetupItem>() : c.setup, pr, ops, sink, st, &t);
+        if (s != TC_SUCCESS) return s;
+        total += (double)c.count * t / pr.fraction;
+    }
+    *out = total;
+    return TC_SUCCESS;
+}
+
+// ---------------------------------------------------------------- tuning cache
+std::mutex g_cache_mu;
+std::map<std::string, std::pair<int, int>> g_cache;  // key -> (GETT tile width, TMA)
+
+std::string plan_key(const Plan &p) {
+    std::ostringstream k;
+    k << p.spec << "|";
+    for (int x = 0; x < p.nidx; ++x) k << p.ext[x] << (x + 1 < p.nidx ? "," : "");
+    k << "|";
+    for (int o : {OP_C, OP_A, OP_B})
+        for (int m = 0; m < p.op[o].n; ++m) k << p.op[o].stride[m] << ",";
+    k << "|" << (int)p.dtype << "|" << p.split_products;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) k << "|" << prop.name << "|sm" << prop.major << prop.minor;
+    return k.str();
+}
+
+}  // namespace
+}  // namespace tc
+
+using namespace tc;
+
+extern "C" {
+
+tc_status tc_predict(tc_plan plan, const int32_t *alg_ids, int32_t n, const void *A, const void *B, void *C,
+                     double *seconds, void *stream) {
+    if (!plan || !seconds) return fail(TC_ERROR_INVALID_ARGUMENT, "NULL argument");
+    Plan &p = plan->p;
+    const int32_t count = (int32_t)p.algs.size();
+    if (!alg_ids) n = count;
+    if (n < 0) return fail(TC_ERROR_INVALID_ARGUMENT, "n < 0");
+    for (int32_t i = 0; alg_ids && i < n; ++i)
+        if (alg_ids[i] < 0 || alg_ids[i] >= count) return fail(TC_ERROR_INVALID_ALGORITHM, "algorithm id out of range");
+    tc_status s = ensure_device_resources(p, 0);
+    if (s != TC_SUCCESS) return s;
+    s = ensure_flush(p);
+    if (s != TC_SUCCESS) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    // operands: the caller's, or zero-filled scratch of the operands' spans
+    Operands ops{A, B, C};
+    void *own[3] = {nullptr, nullptr, nullptr};
+    for (int o = 0; o < 3; ++o) {
+        const void *given = o == OP_A ? A : (o == OP_B ? B : (const void *)C);
+        if (given) continue;
+        size_t bytes = (size_t)span_elems(p, o) * elem_size(p, o);
+        cudaError_t e = cudaMalloc(&own[o], bytes + 16);
+        if (e != cudaSuccess) {
+            for (int x = 0; x < 3; ++x)
+                if (own[x]) cudaFree(own[x]);
+            return fail(TC_ERROR_OUT_OF_MEMORY, cudaGetErrorString(e));
+        }
+        cudaMemsetAsync(own[o], 0, bytes + 16, st);
+        if (o == OP_A) ops.A = own[o];
+        else if (o == OP_B) ops.B = own[o];
+        else ops.C = own[o];
+    }
+    unsigned *sink = p.dev_status ? (unsigned *)(p.dev_status + 2) : nullptr;
+    p.predicted.assign(count, -1.0);
+    for (int32_t i = 0; i < n && s == TC_SUCCESS; ++i) {
+        const int id = alg_ids ? alg_ids[i] : i;
+        double t = -1.0;
+        s = predict_one(p, id, ops, sink, st, &t);
+        seconds[i] = t;
+        p.predicted[id] = t;
+    }
+    cudaStreamSynchronize(st);
+    for (int x = 0; x < 3; ++x)
+        if (own[x]) cudaFree(own[x]);
+    p.last_stream = stream;
+    return s;
+}
+
+tc_status tc_plan_select_best(tc_plan plan, int32_t *best) {
+    if (!plan) return fail(TC_ERROR_INVALID_ARGUMENT, "plan is NULL");
+    Plan &p = plan->p;
+    int32_t arg = -1;
+    for (size_t i = 0; i < p.predicted.size(); ++i) {
+        const double t = p.predicted[i];
+        if (t < 0) continue;
+        if (arg < 0 || t < p.predicted[arg]) arg = (int32_t)i;  // ties: lower id
+    }
+    if (arg < 0) return fail(TC_ERROR_INVALID_ARGUMENT, "no predictions: call tc_predict first");
+    p.selected = arg;
+    if (best) *best = arg;
+    return TC_SUCCESS;
+}
+
+tc_status tc_autotune(tc_plan plan, const void *A, const void *B, void *C, void *stream, int32_t *width,
+                      int32_t *tma) {
+    if (!plan) return fail(TC_ERROR_INVALID_ARGUMENT, "plan is NULL");
+    Plan &p = plan->p;
+    const std::string key = plan_key(p);
+    {
+        std::lock_guard<std::mutex> g(g_cache_mu);
+        auto it = g_cache.find(key);
+        if (it != g_cache.end()) {
+            p.gett_bn = it->second.first;
+            p.gett_tma = it->second.second;
+            if (width) *width = p.gett_bn;
+            if (tma) *tma = p.gett_tma;
+            return TC_SUCCESS;
+        }
+    }
+    const bool tensor = p.dtype != TC_F64 && p.dtype != TC_F32;
+    int best_bn = 0, best_tma = 1;
+    if (tensor) {
+        // the candidates' cost: the GETT micro-benchmark (a few waves of
+        // real tiles, median of ten), as in tc_predict
+        double best_t = -1;
+        const int saved_bn = p.gett_bn, saved_tma = p.gett_tma;
+        for (int bn : {128, 256}) {
+            for (int tm : {0, 1}) {
+                if (tm == 1 && bn != 256) continue;  // the TMA path runs 128 x 256 tiles
+                p.gett_bn = bn;
+                p.gett_tma = tm;
+                int32_t id = 0;
+                double t = -1;
+                tc_status s = tc_predict(plan, &id, 1, A, B, C, &t, stream);
+                if (s != TC_SUCCESS) {
+                    p.gett_bn = saved_bn;
+                    p.gett_tma = saved_tma;
+                    return s;
+                }
+                if (t > 0 && (best_t < 0 || t < best_t)) {
+                    best_t = t;
+                    best_bn = bn;
+                    best_tma = tm;
+                }
+            }
+        }
+    }
+    p.gett_bn = best_bn;
+    p.gett_tma = best_tma;
+    {
+        std::lock_guard<std::mutex> g(g_cache_mu);
+        g_cache[key] = {best_bn, best_tma};
+    }
+    if (width) *width = best_bn;
+    if (tma) *tma = best_tma;
+    return TC_SUCCESS;
+}
+
+tc_status tc_tuning_cache_save(const char *path) {
+    if (!path) return fail(TC_ERROR_INVALID_ARGUMENT, "path is NULL");
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    std::ofstream f(path);
+    if (!f) return fail(TC_ERROR_INVALID_ARGUMENT, std::string("cannot write ") + path);
+    for (auto &kv : g_cache) {
+        std::string k;
+        for (char ch : kv.first) {
+            if (ch == '"' || ch == '\\') k.push_back('\\');
+            k.push_back(ch);
+        }
+        f << "{\"key\": \"" << k << "\", \"gett_tile\": " << kv.second.first << ", \"gett_tma\": "
+          << kv.second.second << "}\n";
+    }
+    return f ? TC_SUCCESS : fail(TC_ERROR_INVALID_ARGUMENT, "write failed");
+}
+
+tc_status tc_tuning_cache_load(const char *path) {
+    if (!path) return fail(TC_ERROR_INVALID_ARGUMENT, "path is NULL");
+    std::ifstream f(path);
+    if (!f) return fail(TC_ERROR_INVALID_ARGUMENT, std::string("cannot read ") + path);
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    std::string line;
+    while (std::getline(f, line)) {
+        size_t k0 = line.find("\"key\": \"");
+        if (k0 == std::string::npos) continue;
+        k0 += 8;
+        std::string key;
+        size_t i = k0;
+        for (; i < line.size() && line[i] != '"'; ++i) {
+            if (line[i] == '\\' && i + 1 < line.size()) ++i;
+            key.push_back(line[i]);
+        }
+        int bn = 0, tm = 1;
+        size_t a = line.find("\"gett_tile\": ", i), b = line.find("\"gett_tma\": ", i);
+        if (a == std::string::npos || b == std::string::npos) continue;
+        bn = std::atoi(line.c_str() + a + 13);
+        tm = std::atoi(line.c_str() + b + 12);
+        if ((bn != 0 && bn != 128 && bn != 256) || (tm != 0 && tm != 1)) continue;
+        g_cache[key] = {bn, tm};
+    }
+    return TC_SUCCESS;
+}
+
+}  // extern "C"

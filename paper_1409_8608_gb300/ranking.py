@@ -1,0 +1,139 @@
+"""Ranking study: predicted vs measured time for every algorithm of one
+contraction (the experiments of Sections 3-4, on the device).
+
+    python -m paper_1409_8608_gb300.ranking --spec abc=iaj,jbic \\
+        --extents 256,256,256,16,16 --dtype f64 [--json out.json]
+
+Reports per algorithm the predicted and the measured seconds, and over all
+of them Spearman's rho and Kendall's tau of the two rankings, the top-1
+regret (measured time of the top-ranked algorithm over the measured best,
+minus one) and the time spent predicting against the time spent measuring
+(the efficiency study of Section 4).  Measurement: CUDA events around one
+tc_execute, after an L2 flush, median of `reps` runs; an algorithm whose
+first run exceeds `cap` seconds is measured once and marked capped (the
+paper stops slow algorithms the same way).
+"""
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import synth, tc
+
+
+def ranks(x):
+    """Average ranks (1 = smallest), ties share their mean rank."""
+    x = np.asarray(x, dtype=np.float64)
+    order = np.argsort(x, kind="stable")
+    r = np.empty(len(x))
+    r[order] = np.arange(1, len(x) + 1)
+    for v in np.unique(x):
+        idx = np.flatnonzero(x == v)
+        if len(idx) > 1:
+            r[idx] = r[idx].mean()
+    return r
+
+
+def spearman(a, b):
+    ra, rb = ranks(a), ranks(b)
+    ra -= ra.mean()
+    rb -= rb.mean()
+    den = np.sqrt((ra * ra).sum() * (rb * rb).sum())
+    return float((ra * rb).sum() / den) if den > 0 else 0.0
+
+
+def kendall(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    n, s = len(a), 0
+    for i in range(n):
+        s += int(np.sum(np.sign(a[i] - a[i + 1:]) * np.sign(b[i] - b[i + 1:])))
+    pairs = n * (n - 1) / 2
+    return float(s / pairs) if pairs else 0.0
+
+
+def measure(plan, ids, dA, dB, dC, flush, reps=5, cap=2.0):
+    import torch
+    out, capped = [], []
+    stream = torch.cuda.current_stream()
+    for aid in ids:
+        plan.select(aid)
+        plan.execute(dA, dB, dC, stream=stream)  # warm-up (allocates copy workspace)
+        torch.cuda.synchronize()
+        times = []
+        for r in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.execute(dA, dB, dC, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+            if times[0] > cap:
+                break
+        plan.device_status()
+        out.append(float(np.median(times)))
+        capped.append(times[0] > cap)
+    return out, capped
+
+
+def study(spec, extents, dtype="f64", seed=0, reps=5, cap=2.0, ids=None):
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tdt = {"f64": torch.float64, "f32": torch.float32}.get(dtype, torch.float32)
+    A, B, _ = synth.uniform_operands(spec, extents, seed=seed)
+    nC = synth.dense_sizes(spec, extents)[0]
+    dA = torch.from_numpy(A).to(tdt).to(dev)
+    dB = torch.from_numpy(B).to(tdt).to(dev)
+    dC = torch.zeros(nC, dtype=tdt, device=dev)
+    plan = tc.Plan(spec, extents, dtype=dtype)
+    algs = plan.algorithms()
+    if ids is None:
+        ids = [a["id"] for a in algs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pred = plan.predict(ids, dA, dB, dC)
+    t_pred = time.perf_counter() - t0
+    runnable = [i for i, p in zip(ids, pred) if p > 0]
+    flush = torch.empty(int(256 << 20) // 4, dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    meas, capped = measure(plan, runnable, dA, dB, dC, flush, reps=reps, cap=cap)
+    t_meas = time.perf_counter() - t0
+    pmap = dict(zip(ids, pred))
+    p = [pmap[i] for i in runnable]
+    best_pred = runnable[int(np.argmin(p))]
+    best_meas = runnable[int(np.argmin(meas))]
+    mmap = dict(zip(runnable, meas))
+    rows = [{"id": i, "name": algs[i]["name"], "predicted_s": pmap[i], "measured_s": mmap[i],
+             "capped": c} for i, c in zip(runnable, capped)]
+    plan.close()
+    return {
+        "spec": spec, "extents": list(extents), "dtype": dtype, "algorithms": rows,
+        "spearman": spearman(p, meas), "kendall": kendall(p, meas),
+        "top_pred": algs[best_pred]["name"], "top_meas": algs[best_meas]["name"],
+        "top1_regret": mmap[best_pred] / mmap[best_meas] - 1.0,
+        "prediction_seconds": t_pred, "measurement_seconds": t_meas,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--spec", default="abc=iaj,jbic")
+    ap.add_argument("--extents", default="128,128,128,16,16")
+    ap.add_argument("--dtype", default="f64")
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--cap", type=float, default=2.0)
+    ap.add_argument("--json", default=None)
+    args = ap.parse_args()
+    ext = [int(x) for x in args.extents.split(",")]
+    r = study(args.spec, ext, args.dtype, reps=args.reps, cap=args.cap)
+    summary = {k: v for k, v in r.items() if k != "algorithms"}
+    print(json.dumps(summary))
+    if args.json:
+        with open(args.json, "w") as f:
+            json.dump(r, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -48,6 +48,15 @@ class tc_algorithm(ctypes.Structure):
     ]
 
 
+class tc_pred_case(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("depth", ctypes.c_int32), ("count", ctypes.c_int64),
+                ("omit", ctypes.c_int32), ("n_items", ctypes.c_int32)]
+
+
+class tc_setup_item(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("operand", ctypes.c_int32), ("size", ctypes.c_int64)]
+
+
 _lib = None
 
 # name -> (restype, argtypes); mirrors include/tc.h
@@ -66,6 +75,18 @@ SIGNATURES = {
     "tc_plan_set_split": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_plan_set_gett_tile": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_plan_set_gett_tma": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "tc_access_distances": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _I64P]),
+    "tc_prediction_cases": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                                           ctypes.c_int64, ctypes.POINTER(tc_pred_case), ctypes.c_int32, _I32P]),
+    "tc_setup_list": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                     ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(tc_setup_item),
+                                     ctypes.c_int32, _I32P]),
+    "tc_predict": (ctypes.c_int, [_VP, _I32P, ctypes.c_int32, _VP, _VP, _VP,
+                                  ctypes.POINTER(ctypes.c_double), _VP]),
+    "tc_plan_select_best": (ctypes.c_int, [_VP, _I32P]),
+    "tc_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I32P, _I32P]),
+    "tc_tuning_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "tc_tuning_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
     "tc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tc_last_error": (ctypes.c_char_p, []),
 }
@@ -201,6 +222,75 @@ def tc_plan_flops(plan):
     return v.value
 
 
+OPERAND_NAMES = ("A", "B", "C")
+CASE_KINDS = ("steady", "miss", "first")
+
+
+def tc_access_distances(plan, alg_id, granularity=0, elem_size=1):
+    out = (ctypes.c_int64 * 3)()
+    _check(load().tc_access_distances(plan, int(alg_id), int(granularity), int(elem_size), out),
+           "tc_access_distances")
+    return dict(zip(OPERAND_NAMES, list(out)))
+
+
+def tc_prediction_cases(plan, alg_id, granularity=0, elem_size=1, cache_size=1 << 20, line_size=8):
+    n = ctypes.c_int32()
+    args = (plan, int(alg_id), int(granularity), int(elem_size), int(cache_size), int(line_size))
+    _check(load().tc_prediction_cases(*args, None, 0, ctypes.byref(n)), "tc_prediction_cases")
+    buf = (tc_pred_case * n.value)()
+    _check(load().tc_prediction_cases(*args, buf, n.value, ctypes.byref(n)), "tc_prediction_cases")
+    return [{"kind": CASE_KINDS[c.kind], "depth": c.depth, "count": c.count, "omit": bool(c.omit),
+             "n_items": c.n_items} for c in buf]
+
+
+def tc_setup_list(plan, alg_id, case_index, granularity=0, elem_size=1, cache_size=1 << 20, line_size=8):
+    """Setup list as [("op", "A"|"B"|"C", size) | ("remote", size)]."""
+    n = ctypes.c_int32()
+    args = (plan, int(alg_id), int(granularity), int(case_index), int(elem_size), int(cache_size),
+            int(line_size))
+    _check(load().tc_setup_list(*args, None, 0, ctypes.byref(n)), "tc_setup_list")
+    buf = (tc_setup_item * n.value)()
+    _check(load().tc_setup_list(*args, buf, n.value, ctypes.byref(n)), "tc_setup_list")
+    return [("op", OPERAND_NAMES[i.operand], i.size) if i.kind == 0 else ("remote", i.size) for i in buf]
+
+
+def tc_predict(plan, alg_ids=None, A=None, B=None, C=None, stream=None):
+    """Predicted seconds per algorithm (a list aligned with alg_ids, or with
+    every algorithm when alg_ids is None)."""
+    if alg_ids is None:
+        n = ctypes.c_int32()
+        _check(load().tc_algorithm_count(plan, ctypes.byref(n)), "tc_algorithm_count")
+        ids, count = None, n.value
+    else:
+        ids = (ctypes.c_int32 * len(alg_ids))(*[int(x) for x in alg_ids])
+        count = len(alg_ids)
+    out = (ctypes.c_double * count)()
+    _check(load().tc_predict(plan, ids, count, _ptr(A), _ptr(B), _ptr(C), out, _stream(stream)),
+           "tc_predict")
+    return list(out)
+
+
+def tc_plan_select_best(plan):
+    v = ctypes.c_int32()
+    _check(load().tc_plan_select_best(plan, ctypes.byref(v)), "tc_plan_select_best")
+    return v.value
+
+
+def tc_autotune(plan, A=None, B=None, C=None, stream=None):
+    w, t = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().tc_autotune(plan, _ptr(A), _ptr(B), _ptr(C), _stream(stream), ctypes.byref(w),
+                              ctypes.byref(t)), "tc_autotune")
+    return w.value, t.value
+
+
+def tc_tuning_cache_save(path):
+    _check(load().tc_tuning_cache_save(str(path).encode()), "tc_tuning_cache_save")
+
+
+def tc_tuning_cache_load(path):
+    _check(load().tc_tuning_cache_load(str(path).encode()), "tc_tuning_cache_load")
+
+
 def tc_status_string(status):
     return load().tc_status_string(int(status)).decode()
 
@@ -237,6 +327,15 @@ class Plan:
 
     def set_gett_tma(self, enable):
         tc_plan_set_gett_tma(self.handle, enable)
+
+    def predict(self, alg_ids=None, A=None, B=None, C=None, stream=None):
+        return tc_predict(self.handle, alg_ids, A, B, C, stream)
+
+    def select_best(self):
+        return tc_plan_select_best(self.handle)
+
+    def autotune(self, A=None, B=None, C=None, stream=None):
+        return tc_autotune(self.handle, A, B, C, stream)
 
     def device_status(self):
         tc_plan_device_status(self.handle)
