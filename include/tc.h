@@ -151,6 +151,26 @@ tc_status tc_algorithm_workspace(tc_plan plan, int32_t alg_id, size_t *bytes);
 tc_status tc_execute(tc_plan plan, const void *alpha, const void *A,
                      const void *B, const void *beta, void *C, void *stream);
 
+/* tc_execute for callers that must not allocate device memory, such as
+ * code running while another thread captures a CUDA graph in global
+ * capture mode (where cudaMalloc fails), code that works inside a fixed
+ * device-memory budget owned by its own allocator, or latency-critical
+ * loops that cannot afford an allocation.  The paper has no counterpart.
+ *
+ * Runs the selected loop-nest algorithm (ids >= 1, TC_F64 or TC_F32) like
+ * tc_execute, but its copy scratch is a fixed 16 MiB array that every GPU
+ * loading this library holds until the process exits; the plan allocates
+ * nothing.  An algorithm whose copies need more than 16 MiB is refused with
+ * TC_ERROR_INVALID_ARGUMENT (tc_algorithm_workspace gives the need); GETT
+ * (id 0) is refused with TC_ERROR_INVALID_ALGORITHM.  The first call on a
+ * device looks up the array's device address; make that call before any
+ * stream capture.  All calls share the one array: calls whose work
+ * overlaps on the GPU (other streams, other threads) race on it.  Every
+ * scratch element is written before it is read, so nothing needs clearing
+ * between calls. */
+tc_status tc_execute_no_alloc(tc_plan plan, const void *alpha, const void *A,
+                              const void *B, const void *beta, void *C, void *stream);
+
 /* Reads and clears the plan's device status word (waits for the stream
  * the plan last ran on): TC_SUCCESS or TC_ERROR_TIMEOUT. */
 tc_status tc_plan_device_status(tc_plan plan);

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -768,3 +769,76 @@ tc_status exec_gett_simt(Plan &p, const void *alpha, const void *A, const void *
 }
 
 }  // namespace tc
+
+// ---------------------------------------------------------------- no-alloc entry point
+// A variant of the loop-nest executor whose copy workspace lives in a fixed
+// device array instead of memory the plan allocates.  The paper has no
+// counterpart; it serves callers that must not allocate device memory.
+namespace tc {
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;  // 16 MiB per device
+constexpr int kMaxDevices = 64;
+
+// One copy per device that loads the library, held until the process exits.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void *g_static_ptr[kMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per
+// device (host code cannot use the symbol itself as a device pointer).
+tc_status static_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(TC_ERROR_INVALID_ARGUMENT, "device ordinal too large");
+    std::lock_guard<std::mutex> g(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess || !ptr) return fail(TC_ERROR_CUDA, e != cudaSuccess ? cudaGetErrorString(e) : "null symbol address");
+        g_static_ptr[dev] = ptr;
+    }
+    *out = g_static_ptr[dev];
+    return TC_SUCCESS;
+}
+
+}  // namespace
+}  // namespace tc
+
+extern "C" tc_status tc_execute_no_alloc(tc_plan plan, const void *alpha, const void *A, const void *B,
+                                         const void *beta, void *C, void *stream) {
+    using namespace tc;
+    if (!plan) return fail(TC_ERROR_INVALID_ARGUMENT, "plan is NULL");
+    if (!alpha || !beta || !A || !B || !C) return fail(TC_ERROR_INVALID_ARGUMENT, "NULL argument");
+    Plan &p = plan->p;
+    if (p.dtype != TC_F64 && p.dtype != TC_F32)
+        return fail(TC_ERROR_UNSUPPORTED_DTYPE, "tc_execute_no_alloc runs the FP64/FP32 loop-nest algorithms");
+    const Algorithm &alg = p.algs[p.selected];
+    if (alg.kernel == TC_KERNEL_GETT)
+        return fail(TC_ERROR_INVALID_ALGORITHM, "tc_execute_no_alloc runs the loop-nest algorithms (ids >= 1)");
+    const size_t need = nest_workspace_bytes(p, alg);
+    if (need > kStaticScratchBytes)
+        return fail(TC_ERROR_INVALID_ARGUMENT,
+                    "algorithm needs " + std::to_string(need) + " bytes of copy scratch; the static scratch holds " +
+                        std::to_string(kStaticScratchBytes) + " bytes (use tc_execute)");
+    void *scratch = nullptr;
+    tc_status s = static_scratch(&scratch);
+    if (s != TC_SUCCESS) return s;
+    // run the same executor with the workspace pointed at the static array
+    void *saved = p.workspace;
+    const size_t saved_bytes = p.workspace_bytes;
+    p.workspace = scratch;
+    p.workspace_bytes = kStaticScratchBytes;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p.dtype == TC_F64)
+        s = run_nest<double>(p, alg, *(const double *)alpha, (const double *)A, (const double *)B,
+                             *(const double *)beta, (double *)C, st, nullptr);
+    else
+        s = run_nest<float>(p, alg, *(const float *)alpha, (const float *)A, (const float *)B,
+                            *(const float *)beta, (float *)C, st, nullptr);
+    p.workspace = saved;
+    p.workspace_bytes = saved_bytes;
+    return s;
+}

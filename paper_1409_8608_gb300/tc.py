@@ -70,6 +70,7 @@ SIGNATURES = {
     "tc_plan_selected": (ctypes.c_int, [_VP, _I32P]),
     "tc_algorithm_workspace": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
     "tc_execute": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "tc_execute_no_alloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "tc_plan_device_status": (ctypes.c_int, [_VP]),
     "tc_plan_flops": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "tc_plan_set_split": (ctypes.c_int, [_VP, ctypes.c_int32]),
@@ -198,6 +199,12 @@ def tc_execute(plan, alpha, A, B, beta, C, stream=None, dtype="f64"):
     a, b = _scalar(alpha, dtype), _scalar(beta, dtype)
     _check(load().tc_execute(plan, ctypes.addressof(a), _ptr(A), _ptr(B), ctypes.addressof(b),
                              _ptr(C), _stream(stream)), "tc_execute")
+
+
+def tc_execute_no_alloc(plan, alpha, A, B, beta, C, stream=None, dtype="f64"):
+    a, b = _scalar(alpha, dtype), _scalar(beta, dtype)
+    _check(load().tc_execute_no_alloc(plan, ctypes.addressof(a), _ptr(A), _ptr(B), ctypes.addressof(b),
+                                      _ptr(C), _stream(stream)), "tc_execute_no_alloc")
 
 
 def tc_plan_device_status(plan):
