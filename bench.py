@@ -13,6 +13,7 @@ Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
 host cores instead (a bounded slab of the same workload per step).
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -53,6 +54,24 @@ def flops_of(extents):
     return f
 
 
+def source_sha(rel):
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def captured_traffic(key, source):
+    """DRAM bytes per launch from a committed ncu capture of this kernel,
+    or None when there is none or the kernel's source changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            entry = json.load(f).get(key)
+    except (OSError, ValueError):
+        return None
+    if not entry or entry.get("source_sha256") != source_sha(source):
+        return None
+    return entry.get("bytes_per_launch")
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -78,7 +97,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(self.index)],
+                 "-lms", "20", "-i", str(self.index)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -213,6 +232,20 @@ def run_gpu(args):
             line["plain_f64"] = {"value": pl["value"], "unit": "GFLOP/s", "algorithm": "gett",
                                  "ms_per_step": pl["ms_per_step"], "roofline": pl["roofline"],
                                  "speedup_of_chosen": line["value"] / pl["value"]}
+        if world == 1 and not args.no_extras:
+            from paper_1409_8608_gb300 import batch_report, serve_report
+            torch.cuda.synchronize()
+            b = batch_report.run(4096, "f32", seed=0, reps=10, hbm_gbs=measured_peaks()["hbm_gbs"])
+            line["batched"] = {"workload": "4096 x abc=ai,ibc, a,b,c log-uniform [8,128], i in {4,8,16,32}, FP32",
+                               "gflops": b["tuned"]["gflops"], "ms": b["tuned"]["ms"],
+                               "hbm_frac": b["tuned"]["hbm_frac"], "untuned_ms": b["untuned"]["ms"],
+                               "graph_ms": b["graph"]["ms"], "launch_per_problem_ms": b["launch_per_problem"]["ms"]}
+            sv = serve_report.run(seconds=args.serve_seconds, rate=2000.0, seed=0)
+            line["serving"] = {"workload": "Poisson 2000 req/s, specs ai,ibc / iaj,jbic / aij,jib, FP64:FP32:BF16X3 = 1:2:2, 40 GB",
+                               "seconds_of_arrivals": args.serve_seconds, "requests": sv["requests"],
+                               "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"],
+                               "served_gflops": sv["served_gflops"], "offered_gflops": sv["offered_gflops"],
+                               "failed": sv["failed"], "admission_stalls": sv["admission_stalls"]}
         if world == 1 and not args.no_cpu:
             from oracle import contraction as oc
             A64, B64, C64, cores, nsl = cpu_oracle_sample(target_s=args.cpu_seconds)
@@ -229,6 +262,19 @@ def run_gpu(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def launch_estimate(plan, step, stream):
+    """Seconds per step from two timed warm steps."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    step()
+    step()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 2e3
 
 
 TORCH_IN = {"f64": "float64", "f32": "float32", "tf32": "float32", "bf16x3": "float32",
@@ -275,7 +321,12 @@ def measure_form(args, dtype, alg_name, A, B, dev, stream, dist, world, tc, step
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args_steps)]
+    # untimed load around the timed region (about 0.3 s before and after),
+    # so that the clock sampler sees the clocks the timed steps run at
+    pad = max(1, int(0.3 / max(1e-4, launch_estimate(plan, step, stream))))
     with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(pad):
+            step()
         t_begin = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
         t_begin.record(stream)
@@ -284,6 +335,8 @@ def measure_form(args, dtype, alg_name, A, B, dev, stream, dist, world, tc, step
             step()
             ev[k][1].record(stream)
         t_end.record(stream)
+        for _ in range(pad):
+            step()
         torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -325,16 +378,23 @@ def measure_form(args, dtype, alg_name, A, B, dev, stream, dist, world, tc, step
         work = flops * products
         peak_tf = peaks["bf16_tflops"] * (0.5 if dtype == "tf32" else 1.0)
         achieved_tf = work / launch_s / 1e12
+        tkey = f"gett_tc_kernel/{dtype}/{SPEC}/{N_FREE}" + (f"/p{products}" if dtype == "bf16x3" else "")
         roofline = {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                    "frac": achieved_tf / peak_tf, "traffic": None, "kernel": "gett_tc_kernel",
+                    "frac": achieved_tf / peak_tf,
+                    "traffic": captured_traffic(tkey, "paper_1409_8608_gb300/csrc/tc_gett.cu"),
+                    "algorithmic_bytes": int(hA.numel() * hA.element_size() + hB.numel() * hB.element_size()
+                                             + hC.numel() * hC.element_size()),
+                    "kernel": "gett_tc_kernel",
                     "work": f"{products} slice products x 2*prod(extents) = {work / 1e9:.1f} GFLOP per launch",
                     "peak_source": "MEASURED_PEAKS bf16_tflops (burst)" + (" x 0.5 (TF32 nominal ratio)" if dtype == "tf32" else "")
                     + (" (fallback)" if peaks.get("fallback") else " (measured)")}
     else:
         achieved_tf = flops / launch_s / 1e12
         peak_tf = ALU_PEAK_TFLOPS[dtype]
+        tkey = f"tile_kernel/{dtype}/{SPEC}/{N_FREE}"
         roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                    "frac": achieved_tf / peak_tf, "traffic": None,
+                    "frac": achieved_tf / peak_tf,
+                    "traffic": captured_traffic(tkey, "paper_1409_8608_gb300/csrc/tc_exec.cu"),
                     "kernel": "tile_kernel" if alg["kernel"] in ("gett", "gemm") else "elementwise_kernel",
                     "peak_source": f"derived: 152 SMs x {'2 DFMA' if dtype == 'f64' else '128 FFMA'}/clk x 2 x 2070 MHz"}
     line = {
@@ -367,6 +427,8 @@ def main():
     ap.add_argument("--products", type=int, default=6)
     ap.add_argument("--bn", type=int, default=0, help="tensor-core GETT tile width (0: auto)")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--alg", default="gett")
     ap.add_argument("--impl", default="tc", choices=["tc", "reference"])
     ap.add_argument("--no-cpu", action="store_true")

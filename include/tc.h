@@ -277,6 +277,97 @@ tc_status tc_autotune(tc_plan plan, const void *A, const void *B, void *C, void 
 tc_status tc_tuning_cache_save(const char *path);
 tc_status tc_tuning_cache_load(const char *path);
 
+/* ---- Batched form: many independent contractions, one launch ------------
+ * No paper counterpart.  Every problem has the batch's spec and its own
+ * extents, dense Fortran-ordered operands, and must reduce to a strided
+ * GEMM: the free indices of A, the free indices of B and the contracted
+ * indices each appear in the same order and contiguously in the operands
+ * that carry them ("abc=ai,ibc" does).  One persistent kernel walks the
+ * flattened tile list of all problems, largest problem first. */
+
+typedef struct tc_batch_s *tc_batch;
+
+/* count problems; extents holds count rows of one extent per index (in the
+ * spec's order of first appearance).  dtype TC_F32 or TC_F64.  Host work
+ * only. */
+tc_status tc_batch_create(tc_batch *out, const char *spec, int32_t count,
+                          const int64_t *extents, tc_dtype dtype);
+tc_status tc_batch_destroy(tc_batch batch);
+
+/* Tile policy: 1 (default) picks 64x64, 32x128 or 16x256 tiles per problem
+ * to waste the fewest padded rows; 0 uses 64x64 for every problem. */
+tc_status tc_batch_set_tiles(tc_batch batch, int32_t policy);
+
+/* Host arrays of count device pointers, in the caller's problem order. */
+tc_status tc_batch_set_operands(tc_batch batch, void *const *A, void *const *B,
+                                void *const *C);
+
+/* Uploads the problem table (allocates it on first use).  tc_batch_execute
+ * calls it when needed; call it yourself before capturing a CUDA graph, so
+ * the captured work is the kernel alone. */
+tc_status tc_batch_prepare(tc_batch batch);
+
+/* C_q = alpha * A_q.B_q + beta * C_q for every problem q, enqueued on
+ * stream: one launch, or one launch per problem when
+ * one_launch_per_problem is 1 (for comparison).  alpha/beta point to
+ * double (TC_F64) or float. */
+tc_status tc_batch_execute(tc_batch batch, const void *alpha, const void *beta,
+                           int32_t one_launch_per_problem, void *stream);
+
+/* Total flops (2 M N K summed), tiles of the current policy and compulsory
+ * bytes (A, B, C once each, beta = 0); any pointer may be NULL. */
+tc_status tc_batch_info(tc_batch batch, double *flops, int64_t *tiles, int64_t *bytes);
+
+/* ---- Serving: continuous batching of contraction requests ---------------
+ * No paper counterpart.  A worker thread admits queued requests in arrival
+ * order when a slot is free and their operands fit in the remaining device
+ * budget (one allocation made at creation, carved first-fit), runs each on
+ * one of its streams (inputs copied in, the fused GETT with a plan cached
+ * per (spec, extents, dtype), result copied out if asked) and frees its
+ * memory and slot when its completion event fires.  Requests that arrive
+ * while others run are admitted as soon as room appears; their work
+ * overlaps on the device.  A request's plan depends only on the request, so
+ * its result is the same alone and in a mix. */
+
+typedef struct tc_server_s *tc_server;
+
+typedef struct {
+    int64_t completed, failed;
+    int64_t admission_stalls;   /* times the queue head waited for memory */
+    int64_t peak_inflight, queued;
+    double flops_served;        /* sum of 2*prod(extents) over completed */
+    double span_seconds;        /* first submission to last completion */
+    double p50_seconds, p99_seconds, max_seconds;  /* submit -> result ready */
+} tc_server_report;
+
+/* budget_bytes of device memory (allocated now), at most `slots` requests
+ * in flight, `streams` CUDA streams (1..64).  Uses the current device. */
+tc_status tc_server_create(tc_server *out, int64_t budget_bytes, int32_t slots,
+                           int32_t streams);
+
+/* Queues one request.  A, B: host inputs laid out densely (Fortran order),
+ * in the dtype's element types (include/tc.h header comment); pinned memory
+ * lets the copies run asynchronously.  C: host output or NULL to keep the
+ * result only on the device until the request completes.  The caller keeps
+ * the buffers alive until the request is done.  A request larger than the
+ * whole budget is refused with TC_ERROR_ADMISSION. */
+tc_status tc_server_submit(tc_server server, const char *spec, const int64_t *extents,
+                           tc_dtype dtype, const void *A, const void *B, void *C,
+                           int64_t *request_id);
+
+/* Non-blocking: *done = 1 once finished (the return value is then the
+ * request's status) and *latency its submit-to-ready seconds. */
+tc_status tc_server_poll(tc_server server, int64_t request_id, int32_t *done, double *latency);
+
+/* Blocks until the request finishes or timeout_s passes
+ * (TC_ERROR_TIMEOUT). */
+tc_status tc_server_wait(tc_server server, int64_t request_id, double timeout_s);
+
+tc_status tc_server_stats(tc_server server, tc_server_report *out);
+
+/* Finishes every queued request, then frees everything. */
+tc_status tc_server_destroy(tc_server server);
+
 /* Static description of a status code.  Never NULL. */
 const char *tc_status_string(tc_status status);
 

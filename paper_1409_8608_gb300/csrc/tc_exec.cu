@@ -677,7 +677,10 @@ tc_status run_gett_simt(Plan &p, T alpha, const T *A, const T *B, T beta, T *C,
         tile_kernel<T, 128, 128, 8, 8, 8><<<(unsigned)cut(td.tiles_m * td.tiles_n), 256, 0, st>>>(td);
     }
     cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? TC_SUCCESS : fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+    return e == cudaSuccess ? TC_SUCCESS
+                            : fail(TC_ERROR_CUDA, std::string("GETT tile_kernel launch (") +
+                                                      std::to_string(td.tiles_m * td.tiles_n) + " tiles): " +
+                                                      cudaGetErrorString(e));
 }
 
 }  // namespace

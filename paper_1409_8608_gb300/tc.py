@@ -57,6 +57,14 @@ class tc_setup_item(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("operand", ctypes.c_int32), ("size", ctypes.c_int64)]
 
 
+class tc_server_report(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("admission_stalls", ctypes.c_int64), ("peak_inflight", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("flops_served", ctypes.c_double),
+                ("span_seconds", ctypes.c_double), ("p50_seconds", ctypes.c_double),
+                ("p99_seconds", ctypes.c_double), ("max_seconds", ctypes.c_double)]
+
+
 _lib = None
 
 # name -> (restype, argtypes); mirrors include/tc.h
@@ -88,6 +96,19 @@ SIGNATURES = {
     "tc_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I32P, _I32P]),
     "tc_tuning_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
     "tc_tuning_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "tc_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_char_p, ctypes.c_int32, _I64P, ctypes.c_int]),
+    "tc_batch_destroy": (ctypes.c_int, [_VP]),
+    "tc_batch_set_tiles": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "tc_batch_set_operands": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    "tc_batch_prepare": (ctypes.c_int, [_VP]),
+    "tc_batch_execute": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, _VP]),
+    "tc_batch_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), _I64P, _I64P]),
+    "tc_server_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]),
+    "tc_server_submit": (ctypes.c_int, [_VP, ctypes.c_char_p, _I64P, ctypes.c_int, _VP, _VP, _VP, _I64P]),
+    "tc_server_poll": (ctypes.c_int, [_VP, ctypes.c_int64, _I32P, ctypes.POINTER(ctypes.c_double)]),
+    "tc_server_wait": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_double]),
+    "tc_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(tc_server_report)]),
+    "tc_server_destroy": (ctypes.c_int, [_VP]),
     "tc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tc_last_error": (ctypes.c_char_p, []),
 }
@@ -296,6 +317,94 @@ def tc_tuning_cache_save(path):
 
 def tc_tuning_cache_load(path):
     _check(load().tc_tuning_cache_load(str(path).encode()), "tc_tuning_cache_load")
+
+
+class Batch:
+    """Owns a tc_batch: many independent contractions in one launch."""
+
+    def __init__(self, spec, extents, dtype="f32"):
+        rows = [list(map(int, r)) for r in extents]
+        flat = [x for r in rows for x in r]
+        self.dtype = dtype
+        self.count = len(rows)
+        h = ctypes.c_void_p()
+        _check(load().tc_batch_create(ctypes.byref(h), spec.encode(), len(rows), _i64(flat),
+                                      DTYPES[dtype]), "tc_batch_create")
+        self.handle = h
+
+    def set_tiles(self, policy):
+        _check(load().tc_batch_set_tiles(self.handle, int(policy)), "tc_batch_set_tiles")
+
+    def set_operands(self, A, B, C):
+        arr = lambda xs: (ctypes.c_void_p * len(xs))(*[_ptr(x) for x in xs])
+        _check(load().tc_batch_set_operands(self.handle, arr(A), arr(B), arr(C)), "tc_batch_set_operands")
+
+    def prepare(self):
+        _check(load().tc_batch_prepare(self.handle), "tc_batch_prepare")
+
+    def execute(self, alpha=1.0, beta=0.0, per_problem=False, stream=None):
+        a, b = _scalar(alpha, self.dtype), _scalar(beta, self.dtype)
+        _check(load().tc_batch_execute(self.handle, ctypes.addressof(a), ctypes.addressof(b),
+                                       1 if per_problem else 0, _stream(stream)), "tc_batch_execute")
+
+    def info(self):
+        f, t, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().tc_batch_info(self.handle, ctypes.byref(f), ctypes.byref(t), ctypes.byref(b)),
+               "tc_batch_info")
+        return {"flops": f.value, "tiles": t.value, "bytes": b.value}
+
+    def close(self):
+        if self.handle is not None and _lib is not None:
+            load().tc_batch_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owns a tc_server (continuous batching of contraction requests)."""
+
+    def __init__(self, budget_bytes=40 << 30, slots=32, streams=8):
+        h = ctypes.c_void_p()
+        _check(load().tc_server_create(ctypes.byref(h), int(budget_bytes), int(slots), int(streams)),
+               "tc_server_create")
+        self.handle = h
+
+    def submit(self, spec, extents, dtype, A, B, C=None):
+        rid = ctypes.c_int64()
+        _check(load().tc_server_submit(self.handle, spec.encode(), _i64(extents), DTYPES[dtype], _ptr(A),
+                                       _ptr(B), _ptr(C), ctypes.byref(rid)), "tc_server_submit")
+        return rid.value
+
+    def poll(self, rid):
+        done, lat = ctypes.c_int32(), ctypes.c_double()
+        st = load().tc_server_poll(self.handle, int(rid), ctypes.byref(done), ctypes.byref(lat))
+        if done.value:
+            _check(st, "tc_server_poll")
+        return bool(done.value), lat.value
+
+    def wait(self, rid, timeout=60.0):
+        _check(load().tc_server_wait(self.handle, int(rid), float(timeout)), "tc_server_wait")
+
+    def stats(self):
+        s = tc_server_report()
+        _check(load().tc_server_stats(self.handle, ctypes.byref(s)), "tc_server_stats")
+        return {name: getattr(s, name) for name, _ in tc_server_report._fields_}
+
+    def close(self):
+        if self.handle is not None and _lib is not None:
+            load().tc_server_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tc_status_string(status):

@@ -7,9 +7,11 @@ For uniform inputs the oracle runs on the inputs as the kernel sees them
 (rounded to BF16 / FP16, TF32-rounded to nearest with ties away), and the
 only error left is the FP32 accumulation, bounded componentwise by
 gamma(K+1) * (|A||B|) with u = 2**-24.  For BF16X3 the oracle runs on the
-FP32 inputs; the 6-product split adds at most about 3 * 2**-24 per term
-(the dropped slice products and the split remainder), so the bound is
-(K + 4) * 2**-24 * (|A||B|)."""
+FP32 inputs: the FP32 accumulator sums the 6K kept slice products (each
+rounded in at most once per addition) and the dropped products plus the
+split remainder add at most 3u per term, so the bound is
+(6K + 4) * 2**-24 * (|A||B|).  The measured errors sit far below it; the
+benchmark reports them."""
 import numpy as np
 import pytest
 
@@ -112,7 +114,7 @@ def test_gett_within_bound_on_uniform(tcmod, spec, ext, dtype):
     want = oc.contract(spec, ext, Ar, Br)
     scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
     K = ksize(spec, ext)
-    bound = (K + 4) * U32 if dtype == "bf16x3" else (K + 1) * U32 / (1 - (K + 1) * U32)
+    bound = (6 * K + 4) * U32 if dtype == "bf16x3" else (K + 1) * U32 / (1 - (K + 1) * U32)
     got = run_gett(tcmod, spec, ext, dtype, dA, dB)
     err = float(np.max(np.abs(got - want) / scale))
     assert err <= bound, (dtype, err, bound)
@@ -131,7 +133,7 @@ def test_split_products_order_accuracy(tcmod):
         got = run_gett(tcmod, spec, ext, "bf16x3", dA, dB, products=p)
         errs[p] = float(np.max(np.abs(got - want) / scale))
     assert errs[3] < 4 * 2.0 ** -16
-    assert errs[6] <= (256 + 4) * U32 and errs[9] <= (256 + 4) * U32
+    assert errs[6] <= (6 * 256 + 4) * U32 and errs[9] <= (9 * 256 + 4) * U32
     assert errs[6] <= errs[3] and errs[9] <= 1.5 * errs[6]
     with pytest.raises(tcmod.TcError):
         tcmod.Plan(spec, ext, dtype="bf16x3").set_split(4)
@@ -171,7 +173,7 @@ def test_large_bench_shape_sampled(tcmod):
     scale = oc.contract_points(spec, ext, np.abs(Ar), np.abs(Br), pts, threads=4)
     lin = pts[:, 0] + 512 * pts[:, 1] + 512 * 512 * pts[:, 2]
     err = float(np.max(np.abs(got[lin] - want) / scale))
-    assert err <= (256 + 4) * U32, err
+    assert err <= (6 * 256 + 4) * U32, err
     assert np.isfinite(got).all()
 
 
@@ -203,7 +205,7 @@ def test_tma_staging_matches_global_loads_bitwise(tcmod, spec, ext, dtype):
     want = oc.contract(spec, ext, Ar, Br)
     scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
     K = ksize(spec, ext)
-    bound = (K + 4) * U32 if dtype == "bf16x3" else (K + 1) * U32 / (1 - (K + 1) * U32)
+    bound = (6 * K + 4) * U32 if dtype == "bf16x3" else (K + 1) * U32 / (1 - (K + 1) * U32)
     assert float(np.max(np.abs(outs[0] - want) / scale)) <= bound
 
 
