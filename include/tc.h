@@ -191,6 +191,18 @@ tc_status tc_plan_set_gett_tile(tc_plan plan, int32_t width);
  * same either way. */
 tc_status tc_plan_set_gett_tma(tc_plan plan, int32_t enable);
 
+/* TC_BF16X3 plans, tensor-core GETT: compensated accumulation.  With a
+ * chunk of c K elements (a positive multiple of 32) and K > c, each output
+ * is summed on the tensor cores in FP32 over chunks of c contracted
+ * positions, and the chunk sums are added into a float-float (hi, lo) pair
+ * held in tensor memory by an error-free two-sum; the result is hi + lo.
+ * The FP32 accumulation error then grows with c instead of with K.  Such
+ * launches use 128 x 128 tiles whatever tc_plan_set_gett_tile says.
+ * -1 (default) = 256; 0 = off (one FP32 accumulator across all of K).
+ * Other values give TC_ERROR_INVALID_ARGUMENT; other dtypes and the loop
+ * nests ignore the setting.  Beyond the paper, which computes in FP64. */
+tc_status tc_plan_set_compensation(tc_plan plan, int32_t chunk);
+
 /* 2 * product of all extents. */
 tc_status tc_plan_flops(tc_plan plan, double *flops);
 

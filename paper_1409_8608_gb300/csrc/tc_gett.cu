@@ -57,6 +57,7 @@ enum GettKind { GK_BF16X3 = 0, GK_BF16 = 1, GK_F16 = 2, GK_TF32 = 3 };
 constexpr int kBM = 128;                  // accumulator rows = TMEM lanes
 constexpr int kBK = 32;                   // K elements per stage, global-load path
 constexpr int kBKT = 16;                  // K elements per stage, TMA path
+constexpr int64_t kCompChunkK = 256;      // default K chunk of the compensated split-BF16 form
 constexpr int kEpiWarps = 4;              // warps 0-3
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kProducerWarps = 8;         // warps 4-11
@@ -97,6 +98,7 @@ struct GettDesc {
     int sk_vec4[2];
     uint32_t tma_bytes;  // staged bytes per stage (both operands)
     double tile_frac;    // micro-benchmark: run this fraction of the tiles
+    int chunk_stages;    // compensated form: K stages per TMEM chunk
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -255,6 +257,28 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_st32_zero(uint32_t taddr) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+        "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr), "r"(0u)
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
@@ -474,7 +498,12 @@ __device__ __forceinline__ void convert_staged(const char *stg, int srow, const 
     }
 }
 
-template <int KIND, int BN, int STAGES, int BK, bool TMA>
+// COMP (split-BF16 with long K): the MMA accumulates chunks of
+// chunk_stages K stages into two alternating TMEM accumulators; the
+// epilogue folds each finished chunk into a float-float running sum
+// (hi, lo) kept in TMEM (TwoSum), so the FP32 rounding of the accumulator
+// grows with the chunk length instead of with K.
+template <int KIND, int BN, int STAGES, int BK, bool TMA, bool COMP>
 __global__ void __launch_bounds__(kThreads, 1)
 gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
     using T = KindTraits<KIND, BK>;
@@ -500,6 +529,11 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int nkt = (int)((d.K + BK - 1) / BK);
+    constexpr uint32_t kTmemCols = COMP ? 4 * BN : 2 * BN;
+    static_assert(kTmemCols <= 512, "tensor memory columns");
+    // accumulation units per tile: one, or the K chunks of the compensated form
+    const int cstg = COMP ? (d.chunk_stages > 0 ? d.chunk_stages : nkt) : nkt;
+    const int nch = (nkt + cstg - 1) / cstg;
     const bool any_tma = TMA && (d.tma[0] || d.tma[1]);
     const bool any_ldg = !TMA || !d.tma[0] || !d.tma[1];
 
@@ -518,7 +552,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == kMmaWarp) tmem_alloc(tmem_slot, 2 * BN);
+    if (warp == kMmaWarp) tmem_alloc(tmem_slot, kTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -662,36 +696,40 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             const int nprod = KIND == GK_BF16X3 ? d.nprod : 1;
             const uint32_t base = smem_u32(ops);
             int64_t g = 0;
-            int it = 0;
+            int64_t u = 0;  // accumulation units (tiles, or K chunks of tiles)
             bool stop = false;
-            for (int64_t tile = blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x, ++it) {
-                const int buf = it & 1;
-                if (it >= 2 && !mbar_wait(&tempty[buf], (uint32_t)(((it / 2) - 1) & 1))) {
-                    stop = true;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t dt = tmem + (uint32_t)(buf * BN);
-                for (int kt = 0; kt < nkt; ++kt, ++g) {
-                    const int s = (int)(g % STAGES);
-                    if (*abort_flag || !mbar_wait(&full[s], (uint32_t)((g / STAGES) & 1))) {
+            for (int64_t tile = blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x) {
+                for (int c = 0; c < nch && !stop; ++c, ++u) {
+                    const int buf = (int)(u & 1);
+                    if (u >= 2 && !mbar_wait(&tempty[buf], (uint32_t)(((u / 2) - 1) & 1))) {
                         stop = true;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = base + s * SP::kStage;
-                    const uint32_t sb = sa + T::kSlices * SP::kATile;
-#pragma unroll
-                    for (int ks = 0; ks < T::kKsteps; ++ks) {
-                        for (int q = 0; q < nprod; ++q) {
-                            uint64_t ad = smem_desc(sa + pa[q] * SP::kATile + ks * 2 * lboA, lboA, 128);
-                            uint64_t bd = smem_desc(sb + pb[q] * SP::kBTile + ks * 2 * lboB, lboB, 128);
-                            mma_issue<KIND>(dt, ad, bd, idesc, (kt | ks | q) != 0);
+                    const uint32_t dt = tmem + (uint32_t)(buf * BN);
+                    const int kt_end = min(nkt, (c + 1) * cstg);
+                    for (int kt = c * cstg; kt < kt_end; ++kt, ++g) {
+                        const int s = (int)(g % STAGES);
+                        if (*abort_flag || !mbar_wait(&full[s], (uint32_t)((g / STAGES) & 1))) {
+                            stop = true;
+                            break;
                         }
+                        tc_fence_after();
+                        const uint32_t sa = base + s * SP::kStage;
+                        const uint32_t sb = sa + T::kSlices * SP::kATile;
+                        const bool first = kt == c * cstg;
+#pragma unroll
+                        for (int ks = 0; ks < T::kKsteps; ++ks) {
+                            for (int q = 0; q < nprod; ++q) {
+                                uint64_t ad = smem_desc(sa + pa[q] * SP::kATile + ks * 2 * lboA, lboA, 128);
+                                uint64_t bd = smem_desc(sb + pb[q] * SP::kBTile + ks * 2 * lboB, lboB, 128);
+                                mma_issue<KIND>(dt, ad, bd, idesc, !(first && ks == 0 && q == 0));
+                            }
+                        }
+                        mma_commit(&empty[s]);
                     }
-                    mma_commit(&empty[s]);
+                    mma_commit(&tfull[buf]);  // arrives when this unit's MMAs are done
                 }
-                mma_commit(&tfull[buf]);  // arrives when this tile's MMAs are done
             }
             if (stop) {
                 *abort_flag = 1;
@@ -707,6 +745,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         const int et = threadIdx.x;  // 0..127 = accumulator row = TMEM lane
         float *__restrict__ C = d.C;
         int it = 0;
+        int64_t u = 0;
         for (int64_t tile = blockIdx.x; tile < d.num_tiles; tile += gridDim.x, ++it) {
             const int64_t m0 = (tile % d.tiles_m) * kBM, n0 = (tile / d.tiles_m) * BN;
             int64_t *cn = cN + (it & 1) * BN;
@@ -727,54 +766,101 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                 }
             }
             if (role_sync_or<2, kEpiThreads>(*abort_flag)) break;
-            const int buf = it & 1;
-            bool ok = mbar_wait(&tfull[buf], (uint32_t)((it / 2) & 1));
-            ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld needs the whole warp
-            if (!ok) {
-                *abort_flag = 1;
-                atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
-                continue;  // the next role barrier sees the abort
-            }
-            tc_fence_after();
-            const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * BN);
+            const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+            bool aborted = false;
+            for (int c = 0; c < nch; ++c, ++u) {
+                const int buf = (int)(u & 1);
+                bool ok = mbar_wait(&tfull[buf], (uint32_t)((u / 2) & 1));
+                ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld needs the whole warp
+                if (!ok) {
+                    *abort_flag = 1;
+                    atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
+                    aborted = true;
+                    break;  // the next role barrier sees the abort
+                }
+                tc_fence_after();
+                const uint32_t acc = tmem + lane_off + (uint32_t)(buf * BN);
+                const uint32_t hi = tmem + lane_off + (uint32_t)(2 * BN), lo = hi + (uint32_t)BN;
+                const bool last = c == nch - 1;
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(lane_base + (uint32_t)c0, r);
-                if (om >= 0) {
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(acc + (uint32_t)c0, r);
+                    if constexpr (COMP) {
+                        // two 32-register arrays live at a time (r and t)
+                        if (nch > 1) {
+                            if (c == 0) {
+                                tmem_st32(hi + (uint32_t)c0, r);
+                                tmem_st32_zero(lo + (uint32_t)c0);
+                                continue;
+                            }
+                            uint32_t t[32];
+                            if (last) {  // result = hi + (lo + chunk): one rounding per step
+                                tmem_ld32(lo + (uint32_t)c0, t);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int64_t on = cn[c0 + j];
-                        if (on < 0) continue;
-                        float v = d.alpha * __uint_as_float(r[j]);
-                        if (d.init == 1) v = fmaf(d.beta, C[om + on], v);
-                        C[om + on] = v;
+                                for (int j = 0; j < 32; ++j)
+                                    r[j] = __float_as_uint(__fadd_rn(__uint_as_float(t[j]), __uint_as_float(r[j])));
+                                tmem_ld32(hi + (uint32_t)c0, t);
+#pragma unroll
+                                for (int j = 0; j < 32; ++j)
+                                    r[j] = __float_as_uint(__fadd_rn(__uint_as_float(t[j]), __uint_as_float(r[j])));
+                            } else {  // (hi, err) = TwoSum(hi, chunk); lo += err
+                                tmem_ld32(hi + (uint32_t)c0, t);
+#pragma unroll
+                                for (int j = 0; j < 32; ++j) {
+                                    const float a = __uint_as_float(t[j]), b = __uint_as_float(r[j]);
+                                    const float s2 = __fadd_rn(a, b);
+                                    const float bb = __fsub_rn(s2, a);
+                                    t[j] = __float_as_uint(s2);
+                                    r[j] = __float_as_uint(
+                                        __fadd_rn(__fsub_rn(a, __fsub_rn(s2, bb)), __fsub_rn(b, bb)));
+                                }
+                                tmem_st32(hi + (uint32_t)c0, t);
+                                tmem_ld32(lo + (uint32_t)c0, t);
+#pragma unroll
+                                for (int j = 0; j < 32; ++j)
+                                    t[j] = __float_as_uint(__fadd_rn(__uint_as_float(t[j]), __uint_as_float(r[j])));
+                                tmem_st32(lo + (uint32_t)c0, t);
+                                continue;
+                            }
+                        }
+                    }
+                    if (om >= 0) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int64_t on = cn[c0 + j];
+                            if (on < 0) continue;
+                            float v = d.alpha * __uint_as_float(r[j]);
+                            if (d.init == 1) v = fmaf(d.beta, C[om + on], v);
+                            C[om + on] = v;
+                        }
                     }
                 }
+                tc_fence_before();
+                mbar_arrive(&tempty[buf]);
             }
-            tc_fence_before();
-            mbar_arrive(&tempty[buf]);
+            if (aborted) continue;
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == kMmaWarp) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * BN);
+        tmem_dealloc(tmem, kTmemCols);
     }
 }
 
 // ------------------------------------------------------------------ host side
 int g_gett_sms = 0;
 
-template <int KIND, int BN, int STAGES, int BK, bool TMA>
+template <int KIND, int BN, int STAGES, int BK, bool TMA, bool COMP = false>
 tc_status launch_gett(const GettDesc &d, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
     using SP = SmemPlan<KIND, BN, STAGES, BK, TMA>;
     static_assert(SP::kTotal <= 227 * 1024, "shared memory budget");
     // at least 116 KB so that one CTA (and one tensor-memory allocation of
-    // 2*BN columns) occupies each SM
+    // up to 512 columns) occupies each SM
     constexpr int kSmem = SP::kTotal > 116 * 1024 ? SP::kTotal : 116 * 1024;
-    auto kern = gett_tc_kernel<KIND, BN, STAGES, BK, TMA>;
+    auto kern = gett_tc_kernel<KIND, BN, STAGES, BK, TMA, COMP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
     if (g_gett_sms == 0) {
@@ -790,12 +876,23 @@ tc_status launch_gett(const GettDesc &d, const CUtensorMap &ta, const CUtensorMa
 }
 
 template <int KIND>
-tc_status launch_kind(GettDesc &d, int bn, bool tma, const CUtensorMap &ta, const CUtensorMap &tb,
+tc_status launch_kind(GettDesc &d, int bn, bool tma, bool comp, const CUtensorMap &ta, const CUtensorMap &tb,
                       cudaStream_t st) {
     d.tiles_n = (d.N + bn - 1) / bn;
     d.num_tiles = d.tiles_m * d.tiles_n;
     if (d.tile_frac < 1.0) d.num_tiles = std::max<int64_t>(1, (int64_t)(d.num_tiles * d.tile_frac));
-    if (tma) {  // 16-K stages, staged input boxes, BN = 256
+    if constexpr (KIND == GK_BF16X3) {
+        if (comp) {  // 128 x 128 tiles: two chunk accumulators and (hi, lo) fill the tensor memory
+            if (tma) return launch_gett<KIND, 128, 4, kBKT, true, true>(d, ta, tb, st);
+            return launch_gett<KIND, 128, 4, kBK, false, true>(d, ta, tb, st);
+        }
+    }
+    if (tma) {  // 16-K stages, staged input boxes
+        if (bn == 128) {
+            if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 128, 4, kBKT, true>(d, ta, tb, st);
+            else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 128, 6, kBKT, true>(d, ta, tb, st);
+            else return launch_gett<KIND, 128, 8, kBKT, true>(d, ta, tb, st);
+        }
         if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 256, 3, kBKT, true>(d, ta, tb, st);
         else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 256, 3, kBKT, true>(d, ta, tb, st);
         else return launch_gett<KIND, 256, 5, kBKT, true>(d, ta, tb, st);
@@ -1075,17 +1172,23 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     }
     const int chunk = p.dtype == TC_TF32 ? 4 : 8;
     int bn = p.gett_bn == 128 || p.gett_bn == 256 ? p.gett_bn : (d.N >= 256 ? 256 : 128);
-    // TMA staging for each operand TMA can describe (tiles of 128 x 256)
+    // compensated accumulation (split-BF16 only): K chunks of comp_k elements
+    int64_t comp_k = 0;
+    if (p.dtype == TC_BF16X3) comp_k = p.comp_chunk < 0 ? kCompChunkK : p.comp_chunk;
+    const bool comp = comp_k > 0 && d.K > comp_k;
+    if (comp) bn = 128;
+    // TMA staging for each operand TMA can describe (tiles of 128 x bn)
     CUtensorMap tmA, tmB;
     std::memset(&tmA, 0, sizeof(tmA));
     std::memset(&tmB, 0, sizeof(tmB));
     bool tma = false;
-    if (p.gett_tma && bn == 256) {
+    if (p.gett_tma) {
         d.tma[0] = plan_tma_operand(p, OP_A, A, in_bytes, kBM, d.nm, d.m_ext, d.m_sA, d.nk, d.k_ext, d.k_sA, d, tmA);
-        d.tma[1] = plan_tma_operand(p, OP_B, B, in_bytes, 256, d.nn, d.n_ext, d.n_sB, d.nk, d.k_ext, d.k_sB, d, tmB);
+        d.tma[1] = plan_tma_operand(p, OP_B, B, in_bytes, bn, d.nn, d.n_ext, d.n_sB, d.nk, d.k_ext, d.k_sB, d, tmB);
         tma = d.tma[0] || d.tma[1];
-        d.tma_bytes = (uint32_t)((d.tma[0] ? kBM * kBKT * in_bytes : 0) + (d.tma[1] ? 256 * kBKT * in_bytes : 0));
+        d.tma_bytes = (uint32_t)((d.tma[0] ? kBM * kBKT * in_bytes : 0) + (d.tma[1] ? bn * kBKT * in_bytes : 0));
     }
+    if (comp) d.chunk_stages = (int)(comp_k / (tma ? kBKT : kBK));
     // global-load mappings (used by operands without TMA staging)
     auto pick = [&](const void *base, int rows, int nrow, const int64_t *rext, const int64_t *rs,
                     const int64_t *ks) {
@@ -1108,10 +1211,10 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     d.tile_frac = probe ? probe->fraction : 1.0;
     cudaStream_t st = (cudaStream_t)stream;
     switch (p.dtype) {
-    case TC_BF16X3: return launch_kind<GK_BF16X3>(d, bn, tma, tmA, tmB, st);
-    case TC_BF16: return launch_kind<GK_BF16>(d, bn, tma, tmA, tmB, st);
-    case TC_F16: return launch_kind<GK_F16>(d, bn, tma, tmA, tmB, st);
-    case TC_TF32: return launch_kind<GK_TF32>(d, bn, tma, tmA, tmB, st);
+    case TC_BF16X3: return launch_kind<GK_BF16X3>(d, bn, tma, comp, tmA, tmB, st);
+    case TC_BF16: return launch_kind<GK_BF16>(d, bn, tma, comp, tmA, tmB, st);
+    case TC_F16: return launch_kind<GK_F16>(d, bn, tma, comp, tmA, tmB, st);
+    case TC_TF32: return launch_kind<GK_TF32>(d, bn, tma, comp, tmA, tmB, st);
     default: return fail(TC_ERROR_UNSUPPORTED_DTYPE, "dtype has no tensor-core GETT");
     }
 }

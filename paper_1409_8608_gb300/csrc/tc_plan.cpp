@@ -412,6 +412,14 @@ tc_status tc_plan_set_gett_tma(tc_plan plan, int32_t enable) {
     return TC_SUCCESS;
 }
 
+tc_status tc_plan_set_compensation(tc_plan plan, int32_t chunk) {
+    if (!plan) return fail(TC_ERROR_INVALID_ARGUMENT, "plan is NULL");
+    if (chunk < -1 || (chunk > 0 && chunk % 32 != 0))
+        return fail(TC_ERROR_INVALID_ARGUMENT, "compensation chunk must be -1, 0 or a positive multiple of 32");
+    plan->p.comp_chunk = chunk;
+    return TC_SUCCESS;
+}
+
 tc_status tc_plan_flops(tc_plan plan, double *flops) {
     if (!plan || !flops) return fail(TC_ERROR_INVALID_ARGUMENT, "NULL argument");
     double f = 2.0;

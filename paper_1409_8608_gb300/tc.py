@@ -84,6 +84,7 @@ SIGNATURES = {
     "tc_plan_set_split": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_plan_set_gett_tile": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_plan_set_gett_tma": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "tc_plan_set_compensation": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_access_distances": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _I64P]),
     "tc_prediction_cases": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
                                            ctypes.c_int64, ctypes.POINTER(tc_pred_case), ctypes.c_int32, _I32P]),
@@ -242,6 +243,10 @@ def tc_plan_set_gett_tile(plan, width):
 
 def tc_plan_set_gett_tma(plan, enable):
     _check(load().tc_plan_set_gett_tma(plan, int(enable)), "tc_plan_set_gett_tma")
+
+
+def tc_plan_set_compensation(plan, chunk):
+    _check(load().tc_plan_set_compensation(plan, int(chunk)), "tc_plan_set_compensation")
 
 
 def tc_plan_flops(plan):
@@ -443,6 +448,9 @@ class Plan:
 
     def set_gett_tma(self, enable):
         tc_plan_set_gett_tma(self.handle, enable)
+
+    def set_compensation(self, chunk):
+        tc_plan_set_compensation(self.handle, chunk)
 
     def predict(self, alg_ids=None, A=None, B=None, C=None, stream=None):
         return tc_predict(self.handle, alg_ids, A, B, C, stream)

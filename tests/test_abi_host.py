@@ -115,3 +115,20 @@ def test_flops_and_workspace(lib):
     # i'c-gemm copies A[i,:,:] (a x j doubles) once per phase
     assert plan.workspace(algs["i'c-gemm"]) == ((8 * 4 * 8 + 255) // 256) * 256
     plan.close()
+
+
+def test_plan_option_validation(lib):
+    plan = tc.Plan("ab=aij,jib", [8, 8, 4, 4], dtype="bf16x3")
+    for chunk in (-1, 0, 32, 256, 4096):
+        plan.set_compensation(chunk)
+    for chunk in (-2, 16, 100):
+        with pytest.raises(tc.TcError) as e:
+            plan.set_compensation(chunk)
+        assert tc.STATUS_NAMES[e.value.status] == "TC_ERROR_INVALID_ARGUMENT"
+    for width in (0, 128, 256):
+        plan.set_gett_tile(width)
+    with pytest.raises(tc.TcError):
+        plan.set_gett_tile(64)
+    with pytest.raises(tc.TcError):
+        plan.set_gett_tma(2)
+    plan.close()

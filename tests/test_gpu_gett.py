@@ -217,3 +217,83 @@ def test_tma_integers_exact(tcmod):
         dA, dB, _ = device_inputs(dtype, A, B)
         got = run_gett(tcmod, spec, ext, dtype, dA, dB)
         assert np.array_equal(got, want), dtype
+
+
+# Compensated split-BF16 accumulation (K > chunk): each output is summed in
+# FP32 on the tensor cores over chunks of c contracted positions and the
+# chunk sums are added with an error-free two-sum into a float-float pair.
+# The FP32 part of the bound then depends on c, not K: the chunk sum errs
+# by at most (6c + 4)u |A||B| over its terms, the float-float sum of the
+# chunk sums by about 2u^2 per chunk, and the final hi + (lo + x) by 2u,
+# so (6c + 8)u |A||B| bounds the whole.
+COMP_CASES = [
+    ("ab=aij,jib", [200, 136, 24, 24]),        # K = 576: chunks 256, 256, 64; M and N tails
+    ("abc=iaj,jbic", [256, 256, 2, 32, 32]),   # K = 1024, TMA-eligible layout, split K order
+    ("abc=ai,ibc", [130, 7, 9, 300]),          # K = 300 not a stage multiple
+]
+
+
+@pytest.mark.parametrize("chunk", [32, 256])
+@pytest.mark.parametrize("spec,ext", COMP_CASES)
+def test_compensated_within_chunk_bound(tcmod, spec, ext, chunk):
+    A, B, _ = synth.uniform_operands(spec, ext, seed=8)
+    dA, dB, (Ar, Br) = device_inputs("bf16x3", A, B)
+    want = oc.contract(spec, ext, Ar, Br)
+    scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
+    n = synth.dense_sizes(spec, ext)[0]
+    outs = {}
+    for comp, tma in ((chunk, 1), (chunk, 0), (0, 1)):
+        plan = tcmod.Plan(spec, ext, dtype="bf16x3")
+        plan.set_compensation(comp)
+        plan.set_gett_tma(tma)
+        dC = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda:0")
+        plan.execute(dA, dB, dC)
+        torch.cuda.synchronize()
+        plan.device_status()
+        plan.close()
+        outs[(comp, tma)] = dC.double().cpu().numpy()
+    # both input paths issue the same MMAs in the same chunks
+    assert np.array_equal(outs[(chunk, 1)], outs[(chunk, 0)])
+    K = ksize(spec, ext)
+    c = min(chunk, K)
+    err = float(np.max(np.abs(outs[(chunk, 1)] - want) / scale))
+    assert err <= (6 * c + 8) * U32, (err, c)
+    err_off = float(np.max(np.abs(outs[(0, 1)] - want) / scale))
+    assert err_off <= (6 * K + 4) * U32
+
+
+def test_compensated_integers_and_alpha_beta_exact(tcmod):
+    spec, ext = "ab=aij,jib", [136, 200, 20, 20]  # K = 400
+    A, B, C0 = synth.integer_operands(spec, ext, seed=9, with_c=True)
+    S = oc.contract(spec, ext, A, B)
+    dA, dB, _ = device_inputs("bf16x3", A, B)
+    for chunk in (32, 256):
+        plan = tcmod.Plan(spec, ext, dtype="bf16x3")
+        plan.set_compensation(chunk)
+        for alpha, beta in ((1.0, 0.0), (2.0, 0.5), (-0.25, 1.0)):
+            dC = torch.from_numpy(C0).float().to("cuda:0")
+            plan.execute(dA, dB, dC, alpha=alpha, beta=beta)
+            torch.cuda.synchronize()
+            got = dC.double().cpu().numpy()
+            assert np.array_equal(got, alpha * S + beta * C0), (chunk, alpha, beta)
+        plan.device_status()
+        plan.close()
+
+
+@pytest.mark.parametrize("dist", ["uniform", "lognormal"])
+def test_precision_workload_meets_fp32_level(tcmod, dist):
+    # C[a,b] = sum_{i,j} A[a,i,j] B[j,i,b], a=b=4096, i=j=64, split-BF16 with
+    # six slice products and the default compensation, on sampled outputs
+    # computed one by one; the target is 1e-6 relative to |A||B|
+    spec, ext = "ab=aij,jib", [4096, 4096, 64, 64]
+    gen = synth.uniform_operands if dist == "uniform" else synth.lognormal_slice_operands
+    A, B, _ = gen(spec, ext, seed=0 if dist == "uniform" else 1)
+    dA, dB, (Ar, Br) = device_inputs("bf16x3", A, B)
+    got = run_gett(tcmod, spec, ext, "bf16x3", dA, dB)
+    rng = np.random.default_rng(2)
+    pts = np.stack([rng.integers(0, 4096, 3000) for _ in range(2)], axis=1)
+    want = oc.contract_points(spec, ext, Ar, Br, pts, threads=4)
+    scale = oc.contract_points(spec, ext, np.abs(Ar), np.abs(Br), pts, threads=4)
+    err = float(np.max(np.abs(got[pts[:, 0] + 4096 * pts[:, 1]] - want) / scale))
+    assert err <= 1e-6, err
+    assert np.isfinite(got).all()
