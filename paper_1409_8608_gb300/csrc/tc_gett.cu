@@ -303,8 +303,13 @@ struct KindTraits {
     static constexpr int kVec = 16 / kInBytes;                  // input elements per 16-byte load
 };
 
-template <int KIND, int BN, int STAGES, int BK, bool TMA>
+// STAGES: depth of the operand ring (converted tiles the MMA reads);
+// SSTG: depth of the TMA staging ring (0 = no TMA staging).  The staging
+// ring is the deeper one: it covers the load latency.
+template <int KIND, int BN, int STAGES, int BK, int SSTG>
 struct SmemPlan {
+    static constexpr bool TMA = SSTG > 0;
+    static constexpr int kSstg = SSTG > 0 ? SSTG : 1;         // barrier slots
     using T = KindTraits<KIND, BK>;
     static constexpr int kATile = kBM * BK * T::kElemBytes;    // one slice
     static constexpr int kBTile = BN * BK * T::kElemBytes;
@@ -312,11 +317,11 @@ struct SmemPlan {
     static constexpr int kOpBytes = STAGES * kStage;
     static constexpr int kStgA = TMA ? kBM * BK * T::kInBytes : 0;  // staged input box
     static constexpr int kStgB = TMA ? BN * BK * T::kInBytes : 0;
-    static constexpr int kStgBytes = STAGES * (kStgA + kStgB);
+    static constexpr int kStgBytes = SSTG * (kStgA + kStgB);
     static constexpr int kKTab = STAGES * BK * 8 * 2;
     static constexpr int kRowTab = 2 * (kBM + BN) * 8;          // converters, double-buffered
     static constexpr int kColTab = 2 * BN * 8;                  // epilogue, double-buffered
-    static constexpr int kBars = (4 * STAGES + 5) * 8 + 16;
+    static constexpr int kBars = (2 * STAGES + 2 * kSstg + 5) * 8 + 16;
     static constexpr int kTotal = kOpBytes + kStgBytes + kKTab + kRowTab + kColTab + kBars;
 };
 
@@ -503,15 +508,17 @@ __device__ __forceinline__ void convert_staged(const char *stg, int srow, const 
 // epilogue folds each finished chunk into a float-float running sum
 // (hi, lo) kept in TMEM (TwoSum), so the FP32 rounding of the accumulator
 // grows with the chunk length instead of with K.
-template <int KIND, int BN, int STAGES, int BK, bool TMA, bool COMP>
+template <int KIND, int BN, int STAGES, int BK, int SSTG, bool COMP>
 __global__ void __launch_bounds__(kThreads, 1)
 gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
     using T = KindTraits<KIND, BK>;
-    using SP = SmemPlan<KIND, BN, STAGES, BK, TMA>;
+    using SP = SmemPlan<KIND, BN, STAGES, BK, SSTG>;
+    constexpr bool TMA = SP::TMA;
+    constexpr int SS = SP::kSstg;
     using In = typename T::In;
     extern __shared__ __align__(1024) char smem[];
     char *ops = smem;
-    char *stg = smem + SP::kOpBytes;                          // [STAGES][A box | B box]
+    char *stg = smem + SP::kOpBytes;                          // [SSTG][A box | B box]
     int64_t *kA = (int64_t *)(stg + SP::kStgBytes);           // [STAGES][BK]
     int64_t *kB = kA + STAGES * BK;
     int64_t *rowA = kB + STAGES * BK;                         // [2][kBM]
@@ -520,8 +527,8 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     uint64_t *full = (uint64_t *)(cN + 2 * BN);               // operand stage filled
     uint64_t *empty = full + STAGES;                          // operand stage consumed
     uint64_t *sfull = empty + STAGES;                         // staged box landed
-    uint64_t *sempty = sfull + STAGES;                        // staged box converted
-    uint64_t *tfull = sempty + STAGES;                        // [2]
+    uint64_t *sempty = sfull + SS;                            // staged box converted
+    uint64_t *tfull = sempty + SS;                            // [2]
     uint64_t *tempty = tfull + 2;                             // [2]
     uint64_t *drain = tempty + 2;
     uint32_t *tmem_slot = (uint32_t *)(drain + 1);
@@ -539,14 +546,16 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], kProducerThreads);
+            mbar_init(&full[s], kProducerThreads / 32);  // one arrival per converter warp
             mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < SS; ++s) {
             mbar_init(&sfull[s], 1);
-            mbar_init(&sempty[s], kProducerThreads);
+            mbar_init(&sempty[s], kProducerThreads / 32);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], kEpiThreads);
+            mbar_init(&tempty[b], kEpiThreads / 32);  // one arrival per epilogue warp
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -573,9 +582,10 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             for (int kt = 0; kt < nkt; ++kt, ++g) {
                 const int s = (int)(g % STAGES);
                 const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+                const int ss = (int)(g % SS);
                 bool bad = false;
                 if (g >= STAGES) bad = !mbar_wait(&empty[s], ph ^ 1u);
-                if (any_tma && !bad) bad = !mbar_wait(&sfull[s], ph);
+                if (any_tma && !bad) bad = !mbar_wait(&sfull[ss], (uint32_t)((g / SS) & 1));
                 if (any_ldg) {
                     if (kt == 0) {
                         for (int i = pt; i < kBM; i += kProducerThreads) {
@@ -600,11 +610,22 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                         if (k < d.K) {
                             oa = 0;
                             ob = 0;
-                            for (int m = d.nk - 1; m >= 0; --m) {  // innermost K mode fastest
-                                int64_t v = k % d.k_ext[m];
-                                k /= d.k_ext[m];
-                                oa += v * d.k_sA[m];
-                                ob += v * d.k_sB[m];
+                            if (d.K < (int64_t(1) << 31)) {  // 32-bit digits when they fit
+                                uint32_t k32 = (uint32_t)k;
+                                for (int m = d.nk - 1; m >= 0; --m) {  // innermost K mode fastest
+                                    const uint32_t e = (uint32_t)d.k_ext[m];
+                                    const int64_t v = (int64_t)(k32 % e);
+                                    k32 /= e;
+                                    oa += v * d.k_sA[m];
+                                    ob += v * d.k_sB[m];
+                                }
+                            } else {
+                                for (int m = d.nk - 1; m >= 0; --m) {
+                                    int64_t v = k % d.k_ext[m];
+                                    k /= d.k_ext[m];
+                                    oa += v * d.k_sA[m];
+                                    ob += v * d.k_sB[m];
+                                }
                             }
                         }
                         kA[s * BK + pt] = oa;
@@ -622,20 +643,25 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                 char *stage = ops + s * SP::kStage;
                 char *bstage = stage + T::kSlices * SP::kATile;
                 if (TMA && d.tma[0]) {
-                    convert_staged<KIND, BK, kBM>(stg + s * (SP::kStgA + SP::kStgB), d.srow[0], d.sk[0],
+                    convert_staged<KIND, BK, kBM>(stg + ss * (SP::kStgA + SP::kStgB), d.srow[0], d.sk[0],
                                                   d.sk_vec4[0], stage, SP::kATile, pt);
                 } else {
                     produce_any<KIND, BK, kBM>(Ap, rA, kA + s * BK, stage, SP::kATile, d.a_map, pt);
                 }
                 if (TMA && d.tma[1]) {
-                    convert_staged<KIND, BK, BN>(stg + s * (SP::kStgA + SP::kStgB) + SP::kStgA, d.srow[1],
+                    convert_staged<KIND, BK, BN>(stg + ss * (SP::kStgA + SP::kStgB) + SP::kStgA, d.srow[1],
                                                  d.sk[1], d.sk_vec4[1], bstage, SP::kBTile, pt);
                 } else {
                     produce_any<KIND, BK, BN>(Bp, rB, kB + s * BK, bstage, SP::kBTile, d.b_map, pt);
                 }
+                // each lane publishes its stores to the async proxy; the warp's
+                // lanes are ordered by __syncwarp and lane 0 arrives for all
                 fence_proxy_async_smem();
-                mbar_arrive(&full[s]);
-                if (any_tma) mbar_arrive(&sempty[s]);
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&full[s]);
+                    if (any_tma) mbar_arrive(&sempty[ss]);
+                }
             }
         }
     } else if (warp == kTmaWarp) {
@@ -649,29 +675,46 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                 {
                     int64_t r = m0;
                     for (int m = 0; m < d.nm; ++m) {
-                        rc[0][d.row_dim[0][m]] = (int32_t)(r % d.m_ext[m]);
+                        const int32_t v = (int32_t)(r % d.m_ext[m]);
+#pragma unroll
+                        for (int x = 0; x < kTmaRank; ++x)
+                            if (d.row_dim[0][m] == x) rc[0][x] = v;
                         r /= d.m_ext[m];
                     }
                     r = n0;
                     for (int m = 0; m < d.nn; ++m) {
-                        rc[1][d.row_dim[1][m]] = (int32_t)(r % d.n_ext[m]);
+                        const int32_t v = (int32_t)(r % d.n_ext[m]);
+#pragma unroll
+                        for (int x = 0; x < kTmaRank; ++x)
+                            if (d.row_dim[1][m] == x) rc[1][x] = v;
                         r /= d.n_ext[m];
                     }
                 }
                 for (int kt = 0; kt < nkt; ++kt, ++g) {
-                    const int s = (int)(g % STAGES);
-                    if (g >= STAGES && (*abort_flag || !mbar_wait(&sempty[s], (uint32_t)(((g / STAGES) - 1) & 1)))) {
+                    const int s = (int)(g % SS);
+                    if (g >= SS && (*abort_flag || !mbar_wait(&sempty[s], (uint32_t)(((g / SS) - 1) & 1)))) {
                         stop = true;
                         break;
                     }
                     int32_t c[2][kTmaRank];
+#pragma unroll
                     for (int o = 0; o < 2; ++o)
+#pragma unroll
                         for (int x = 0; x < kTmaRank; ++x) c[o][x] = rc[o][x];
-                    int64_t k = (int64_t)kt * BK;
+                    // the host keeps K below 2^31 on this path
+                    uint32_t k = (uint32_t)kt * (uint32_t)BK;
                     for (int m = d.nk - 1; m >= 0; --m) {
-                        const int64_t v = k % d.k_ext[m];
-                        k /= d.k_ext[m];
-                        for (int o = 0; o < 2; ++o) c[o][d.k_dim[o][m]] += (int32_t)(v * d.k_mul[o][m]);
+                        const uint32_t e = (uint32_t)d.k_ext[m];
+                        const uint32_t v = k % e;
+                        k /= e;
+#pragma unroll
+                        for (int o = 0; o < 2; ++o) {
+                            const int dd = d.k_dim[o][m];
+                            const int32_t add = (int32_t)(v * (uint32_t)d.k_mul[o][m]);
+#pragma unroll
+                            for (int x = 0; x < kTmaRank; ++x)
+                                if (dd == x) c[o][x] += add;
+                        }
                     }
                     char *box = stg + s * (SP::kStgA + SP::kStgB);
                     mbar_arrive_expect_tx(&sfull[s], d.tma_bytes);
@@ -691,8 +734,9 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             constexpr uint32_t idesc = (1u << 4) | (T::kFmt << 7) | (T::kFmt << 10) |
                                        ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
             constexpr uint32_t lboA = (kBM / 8) * 128, lboB = (BN / 8) * 128;
-            const int pa[9] = {0, 0, 1, 0, 1, 2, 1, 2, 2};
-            const int pb[9] = {0, 1, 0, 2, 1, 0, 2, 1, 2};
+            // slice pairs in product order (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+            // (1,2) (2,1) (2,2), one nibble per product
+            constexpr uint64_t kPa = 0x221210100ull, kPb = 0x212012010ull;
             const int nprod = KIND == GK_BF16X3 ? d.nprod : 1;
             const uint32_t base = smem_u32(ops);
             int64_t g = 0;
@@ -721,8 +765,9 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
 #pragma unroll
                         for (int ks = 0; ks < T::kKsteps; ++ks) {
                             for (int q = 0; q < nprod; ++q) {
-                                uint64_t ad = smem_desc(sa + pa[q] * SP::kATile + ks * 2 * lboA, lboA, 128);
-                                uint64_t bd = smem_desc(sb + pb[q] * SP::kBTile + ks * 2 * lboB, lboB, 128);
+                                const uint32_t qa = (uint32_t)(kPa >> (4 * q)) & 15u, qb = (uint32_t)(kPb >> (4 * q)) & 15u;
+                                uint64_t ad = smem_desc(sa + qa * SP::kATile + ks * 2 * lboA, lboA, 128);
+                                uint64_t bd = smem_desc(sb + qb * SP::kBTile + ks * 2 * lboB, lboB, 128);
                                 mma_issue<KIND>(dt, ad, bd, idesc, !(first && ks == 0 && q == 0));
                             }
                         }
@@ -837,7 +882,8 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                     }
                 }
                 tc_fence_before();
-                mbar_arrive(&tempty[buf]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
             }
             if (aborted) continue;
         }
@@ -853,14 +899,14 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
 // ------------------------------------------------------------------ host side
 int g_gett_sms = 0;
 
-template <int KIND, int BN, int STAGES, int BK, bool TMA, bool COMP = false>
+template <int KIND, int BN, int STAGES, int BK, int SSTG, bool COMP = false>
 tc_status launch_gett(const GettDesc &d, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
-    using SP = SmemPlan<KIND, BN, STAGES, BK, TMA>;
+    using SP = SmemPlan<KIND, BN, STAGES, BK, SSTG>;
     static_assert(SP::kTotal <= 227 * 1024, "shared memory budget");
     // at least 116 KB so that one CTA (and one tensor-memory allocation of
     // up to 512 columns) occupies each SM
     constexpr int kSmem = SP::kTotal > 116 * 1024 ? SP::kTotal : 116 * 1024;
-    auto kern = gett_tc_kernel<KIND, BN, STAGES, BK, TMA, COMP>;
+    auto kern = gett_tc_kernel<KIND, BN, STAGES, BK, SSTG, COMP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
     if (g_gett_sms == 0) {
@@ -881,30 +927,31 @@ tc_status launch_kind(GettDesc &d, int bn, bool tma, bool comp, const CUtensorMa
     d.tiles_n = (d.N + bn - 1) / bn;
     d.num_tiles = d.tiles_m * d.tiles_n;
     if (d.tile_frac < 1.0) d.num_tiles = std::max<int64_t>(1, (int64_t)(d.num_tiles * d.tile_frac));
+    // <KIND, BN, operand stages, BK, staging stages (0 = no TMA)>
     if constexpr (KIND == GK_BF16X3) {
         if (comp) {  // 128 x 128 tiles: two chunk accumulators and (hi, lo) fill the tensor memory
-            if (tma) return launch_gett<KIND, 128, 4, kBKT, true, true>(d, ta, tb, st);
-            return launch_gett<KIND, 128, 4, kBK, false, true>(d, ta, tb, st);
+            if (tma) return launch_gett<KIND, 128, 3, kBKT, 6, true>(d, ta, tb, st);
+            return launch_gett<KIND, 128, 4, kBK, 0, true>(d, ta, tb, st);
         }
     }
     if (tma) {  // 16-K stages, staged input boxes
         if (bn == 128) {
-            if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 128, 4, kBKT, true>(d, ta, tb, st);
-            else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 128, 6, kBKT, true>(d, ta, tb, st);
-            else return launch_gett<KIND, 128, 8, kBKT, true>(d, ta, tb, st);
+            if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 128, 3, kBKT, 6>(d, ta, tb, st);
+            else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 128, 4, kBKT, 8>(d, ta, tb, st);
+            else return launch_gett<KIND, 128, 6, kBKT, 12>(d, ta, tb, st);
         }
-        if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 256, 3, kBKT, true>(d, ta, tb, st);
-        else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 256, 3, kBKT, true>(d, ta, tb, st);
-        else return launch_gett<KIND, 256, 5, kBKT, true>(d, ta, tb, st);
+        if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 256, 3, kBKT, 4>(d, ta, tb, st);
+        else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 256, 3, kBKT, 5>(d, ta, tb, st);
+        else return launch_gett<KIND, 256, 4, kBKT, 10>(d, ta, tb, st);
     }
     if (bn == 256) {
-        if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 256, 2, kBK, false>(d, ta, tb, st);
-        else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 256, 3, kBK, false>(d, ta, tb, st);
-        else return launch_gett<KIND, 256, 6, kBK, false>(d, ta, tb, st);
+        if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 256, 2, kBK, 0>(d, ta, tb, st);
+        else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 256, 3, kBK, 0>(d, ta, tb, st);
+        else return launch_gett<KIND, 256, 6, kBK, 0>(d, ta, tb, st);
     }
-    if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 128, 4, kBK, false>(d, ta, tb, st);
-    else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 128, 6, kBK, false>(d, ta, tb, st);
-    else return launch_gett<KIND, 128, 8, kBK, false>(d, ta, tb, st);
+    if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 128, 4, kBK, 0>(d, ta, tb, st);
+    else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 128, 6, kBK, 0>(d, ta, tb, st);
+    else return launch_gett<KIND, 128, 8, kBK, 0>(d, ta, tb, st);
 }
 
 // Distinct 32-byte sectors one warp touches on its first load under a
@@ -1182,7 +1229,7 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     std::memset(&tmA, 0, sizeof(tmA));
     std::memset(&tmB, 0, sizeof(tmB));
     bool tma = false;
-    if (p.gett_tma) {
+    if (p.gett_tma && d.K < (int64_t(1) << 31)) {  // 32-bit K positions in the TMA warp
         d.tma[0] = plan_tma_operand(p, OP_A, A, in_bytes, kBM, d.nm, d.m_ext, d.m_sA, d.nk, d.k_ext, d.k_sA, d, tmA);
         d.tma[1] = plan_tma_operand(p, OP_B, B, in_bytes, bn, d.nn, d.n_ext, d.n_sB, d.nk, d.k_ext, d.k_sB, d, tmB);
         tma = d.tma[0] || d.tma[1];
