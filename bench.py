@@ -146,6 +146,18 @@ def dist_setup():
     return world, rank, local
 
 
+def aggregate_over_ranks(total_ms, steps, flops, world, dist=None, device="cpu"):
+    """Whole-job throughput of `world` replicas that each ran `steps` steps of
+    `flops` FLOPs: the slowest rank's time (all-reduce MAX) divides the work
+    of all ranks.  Returns (max total ms, ms per step, GFLOP/s)."""
+    import torch
+    if dist is not None and world > 1:
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, total_ms / steps, flops * steps * world / (total_ms / 1e3) / 1e9
+
+
 def cpu_oracle_sample(target_s=12.0, threads=None):
     """Times the FP64 oracle on a slab of the workload (last C mode c)."""
     from oracle import contraction as oc
@@ -344,12 +356,7 @@ def measure_form(args, dtype, alg_name, A, B, dev, stream, dist, world, tc, step
     plan.device_status()
     total_ms = t_begin.elapsed_time(t_end)
     per_launch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev) / max(1, launches_per_step)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args_steps
-    value = flops * args_steps * world / (total_ms / 1e3) / 1e9
+    total_ms, ms_per_step, value = aggregate_over_ranks(total_ms, args_steps, flops, world, dist, dev)
 
     # end to end through the public call: pinned host inputs -> device,
     # execute, result back to pinned host memory, every step

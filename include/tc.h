@@ -191,6 +191,16 @@ tc_status tc_plan_set_gett_tile(tc_plan plan, int32_t width);
  * same either way. */
 tc_status tc_plan_set_gett_tma(tc_plan plan, int32_t enable);
 
+/* Failure-detection self-test (no paper counterpart).  Launches one CTA on
+ * `stream` whose thread 0 waits on an mbarrier with the bounded wait every
+ * kernel of this library uses, with limit_ns (0 < limit_ns <= 1e10) in place
+ * of the kernels' 2 s; with signal != 0 a thread of another warp arrives
+ * first.  Blocks until the kernel has finished.  Returns TC_ERROR_TIMEOUT
+ * when the wait ran out (the kernel then returns normally and the context
+ * stays usable), TC_SUCCESS when it was signalled, TC_ERROR_INVALID_ARGUMENT
+ * for a limit out of range, TC_ERROR_CUDA on a launch or copy failure. */
+tc_status tc_selftest_bounded_wait(int64_t limit_ns, int32_t signal, void *stream);
+
 /* TC_BF16X3 plans, tensor-core GETT: compensated accumulation.  With a
  * chunk of c K elements (a positive multiple of 32) and K > c, each output
  * is summed on the tensor cores in FP32 over chunks of c contracted

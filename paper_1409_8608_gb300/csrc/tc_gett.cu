@@ -136,11 +136,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Bounded wait: false when the limit expired.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer() - t0 > kWaitLimitNs) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     }
     return true;
 }
@@ -1266,4 +1267,38 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     }
 }
 
+// Bounded-wait self-test: thread 0 waits on an mbarrier with the wait every
+// kernel here uses; with `signal` a thread of another warp arrives first.
+__device__ int g_selftest_status;
+
+__global__ void bounded_wait_selftest_kernel(unsigned long long limit_ns, int signal) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 32 && signal) mbar_arrive(&bar);
+    if (threadIdx.x == 0) g_selftest_status = mbar_wait(&bar, 0, limit_ns) ? (int)TC_SUCCESS : (int)TC_ERROR_TIMEOUT;
+}
+
 }  // namespace tc
+
+extern "C" tc_status tc_selftest_bounded_wait(int64_t limit_ns, int32_t signal, void *stream) {
+    using namespace tc;
+    if (limit_ns <= 0 || limit_ns > 10000000000LL)
+        return fail(TC_ERROR_INVALID_ARGUMENT, "limit_ns must be in (0, 1e10]");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int init = -1;
+    cudaError_t e = cudaMemcpyToSymbolAsync(g_selftest_status, &init, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        bounded_wait_selftest_kernel<<<1, 64, 0, st>>>((unsigned long long)limit_ns, signal != 0);
+        e = cudaGetLastError();
+    }
+    int out = -1;
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(&out, g_selftest_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+    if (out == (int)TC_ERROR_TIMEOUT) return fail(TC_ERROR_TIMEOUT, "bounded wait ran out (self-test)");
+    return out == (int)TC_SUCCESS ? TC_SUCCESS : fail(TC_ERROR_CUDA, "self-test kernel did not report");
+}

@@ -85,6 +85,7 @@ SIGNATURES = {
     "tc_plan_set_gett_tile": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_plan_set_gett_tma": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_plan_set_compensation": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "tc_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _VP]),
     "tc_access_distances": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _I64P]),
     "tc_prediction_cases": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
                                            ctypes.c_int64, ctypes.POINTER(tc_pred_case), ctypes.c_int32, _I32P]),
@@ -243,6 +244,11 @@ def tc_plan_set_gett_tile(plan, width):
 
 def tc_plan_set_gett_tma(plan, enable):
     _check(load().tc_plan_set_gett_tma(plan, int(enable)), "tc_plan_set_gett_tma")
+
+
+def tc_selftest_bounded_wait(limit_ns, signal, stream=None):
+    """Runs the bounded-wait self-test; returns the status (no exception)."""
+    return load().tc_selftest_bounded_wait(int(limit_ns), int(signal), _stream(stream))
 
 
 def tc_plan_set_compensation(plan, chunk):

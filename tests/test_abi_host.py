@@ -132,3 +132,9 @@ def test_plan_option_validation(lib):
     with pytest.raises(tc.TcError):
         plan.set_gett_tma(2)
     plan.close()
+
+
+def test_selftest_rejects_bad_limits(lib):
+    for limit in (0, -5, 20_000_000_000):
+        st = tc.tc_selftest_bounded_wait(limit, 0)
+        assert tc.STATUS_NAMES[st] == "TC_ERROR_INVALID_ARGUMENT"
