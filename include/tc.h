@@ -310,14 +310,18 @@ tc_status tc_tuning_cache_load(const char *path);
 typedef struct tc_batch_s *tc_batch;
 
 /* count problems; extents holds count rows of one extent per index (in the
- * spec's order of first appearance).  dtype TC_F32 or TC_F64.  Host work
- * only. */
+ * spec's order of first appearance).  dtype TC_F32 or TC_F64 (SIMT FMA
+ * chains), or TC_BF16X3 (FP32 operands, split-BF16 with six slice products
+ * on the tensor-core GETT kernel, 128-row tiles).  Host work only. */
 tc_status tc_batch_create(tc_batch *out, const char *spec, int32_t count,
                           const int64_t *extents, tc_dtype dtype);
 tc_status tc_batch_destroy(tc_batch batch);
 
 /* Tile policy: 1 (default) picks 64x64, 32x128 or 16x256 tiles per problem
- * to waste the fewest padded rows; 0 uses 64x64 for every problem. */
+ * to waste the fewest padded rows; 0 uses 64x64 for every problem.  For
+ * TC_BF16X3 the tiles are 128 x w with one w for the batch: policy 1 takes
+ * the w in {128, 256} with the fewest padded columns plus 64 per tile,
+ * policy 0 takes 256. */
 tc_status tc_batch_set_tiles(tc_batch batch, int32_t policy);
 
 /* Host arrays of count device pointers, in the caller's problem order. */
@@ -339,6 +343,12 @@ tc_status tc_batch_execute(tc_batch batch, const void *alpha, const void *beta,
 /* Total flops (2 M N K summed), tiles of the current policy and compulsory
  * bytes (A, B, C once each, beta = 0); any pointer may be NULL. */
 tc_status tc_batch_info(tc_batch batch, double *flops, int64_t *tiles, int64_t *bytes);
+
+/* TC_BF16X3 batches: waits for the stream of the last execute, then reads
+ * and clears the batch's device status word: TC_SUCCESS, or
+ * TC_ERROR_TIMEOUT when a bounded wait in the kernel ran out (the kernel
+ * then stopped early and C is incomplete).  Other dtypes: TC_SUCCESS. */
+tc_status tc_batch_device_status(tc_batch batch);
 
 /* ---- Serving: continuous batching of contraction requests ---------------
  * No paper counterpart.  A worker thread admits queued requests in arrival

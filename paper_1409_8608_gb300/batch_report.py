@@ -45,7 +45,7 @@ def _time(fn, reps, stream):
 def run(count=4096, dtype="f32", seed=0, reps=10, hbm_gbs=6758.5):
     import torch
     rows = problems(count, seed)
-    tdt = {"f32": torch.float32, "f64": torch.float64}[dtype]
+    tdt = {"f32": torch.float32, "f64": torch.float64, "bf16x3": torch.float32}[dtype]
     rng = torch.Generator(device="cuda").manual_seed(seed)
     As, Bs, Cs = [], [], []
     for a, b, c, i in rows:
@@ -79,6 +79,7 @@ def run(count=4096, dtype="f32", seed=0, reps=10, hbm_gbs=6758.5):
         t = _time(lambda: batch.execute(per_problem=True, stream=stream), max(2, reps // 3), stream)
         res["launch_per_problem"] = {"ms": t * 1e3, "gflops": info["flops"] / t / 1e9, "launches": count}
     torch.cuda.synchronize()
+    batch.device_status()
     batch.close()
     return res
 

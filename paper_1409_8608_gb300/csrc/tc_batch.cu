@@ -26,17 +26,6 @@
 
 namespace tc {
 
-struct BatchProblem {
-    int64_t M, N, K;
-    int64_t sAm, sAk, sBk, sBn, sCm, sCn;
-    const void *A;
-    const void *B;
-    void *C;
-    int64_t tile0;    // first tile of this problem in the flattened list
-    int32_t shape;    // 0: 64x64, 1: 32x128, 2: 16x256
-    int32_t tiles_m;
-};
-
 namespace {
 
 constexpr int kBK = 32;  // the whole K of the batched workloads in one round
@@ -170,6 +159,12 @@ struct BatchImpl {
     BatchProblem *dprobs = nullptr;
     int32_t *dtile_prob = nullptr;    // problem slot of every tile
     int64_t dtile_cap = 0;
+    // split-BF16 (tensor-core GETT tiles of 128 x bn)
+    int bn = 128;
+    int nprod = 6;
+    void *ddescs = nullptr;           // one kernel descriptor per problem slot
+    int *dstatus = nullptr;           // bounded-wait status word
+    void *last_stream = nullptr;
     bool dirty = true;
     int device = -1;
     double flops = 0;
@@ -216,6 +211,33 @@ int shape_for(int64_t M, int policy) {
 
 void assign_tiles(BatchImpl &b) {
     int64_t t = 0;
+    if (b.dtype == TC_BF16X3) {
+        // 128 x bn tensor-core tiles, one width for the launch: per problem
+        // (policy 1) the width with the fewest padded columns plus a fixed
+        // per-tile cost of 64 columns, or 256 (policy 0)
+        int bn = 256;
+        if (b.policy == 1) {
+            double best = 0;
+            for (int w : {128, 256}) {
+                double cost = 0;
+                for (const auto &P : b.probs) cost += (double)((P.N + w - 1) / w) * (w + 64);
+                if (w == 128 || cost < best) {
+                    best = cost;
+                    bn = w;
+                }
+            }
+        }
+        b.bn = bn;
+        for (auto &P : b.probs) {
+            P.shape = 0;
+            P.tiles_m = (int32_t)((P.M + 127) / 128);
+            P.tile0 = t;
+            t += (int64_t)P.tiles_m * ((P.N + bn - 1) / bn);
+        }
+        b.total_tiles = t;
+        b.dirty = true;
+        return;
+    }
     for (auto &P : b.probs) {
         P.shape = shape_for(P.M, b.policy);
         const int tm = kShapeM[P.shape], tn = kShapeN[P.shape];
@@ -243,8 +265,8 @@ tc_status tc_batch_create(tc_batch *out, const char *spec, int32_t count, const 
     if (!out) return fail(TC_ERROR_INVALID_ARGUMENT, "out is NULL");
     *out = nullptr;
     if (!spec || !extents || count < 1) return fail(TC_ERROR_INVALID_ARGUMENT, "bad batch arguments");
-    if (dtype != TC_F32 && dtype != TC_F64)
-        return fail(TC_ERROR_UNSUPPORTED_DTYPE, "the batched form runs in FP32 or FP64");
+    if (dtype != TC_F32 && dtype != TC_F64 && dtype != TC_BF16X3)
+        return fail(TC_ERROR_UNSUPPORTED_DTYPE, "the batched form runs in FP32, FP64 or split-BF16");
     tc_batch_s *h = new (std::nothrow) tc_batch_s();
     if (!h) return fail(TC_ERROR_OUT_OF_MEMORY, "host allocation failed");
     BatchImpl &b = h->b;
@@ -253,7 +275,7 @@ tc_status tc_batch_create(tc_batch *out, const char *spec, int32_t count, const 
     b.count = count;
     // classify once (the classes do not depend on the extents)
     tc_plan plan = nullptr;
-    tc_status s = tc_plan_create(&plan, spec, extents, nullptr, dtype);
+    tc_status s = tc_plan_create(&plan, spec, extents, nullptr, dtype == TC_BF16X3 ? TC_F32 : dtype);
     if (s != TC_SUCCESS) {
         delete h;
         return s;
@@ -319,6 +341,8 @@ tc_status tc_batch_destroy(tc_batch batch) {
     if (!batch) return TC_SUCCESS;
     if (batch->b.dprobs) cudaFree(batch->b.dprobs);
     if (batch->b.dtile_prob) cudaFree(batch->b.dtile_prob);
+    if (batch->b.ddescs) cudaFree(batch->b.ddescs);
+    if (batch->b.dstatus) cudaFree(batch->b.dstatus);
     delete batch;
     return TC_SUCCESS;
 }
@@ -374,9 +398,24 @@ tc_status tc_batch_prepare(tc_batch batch) {
         b.dtile_cap = b.total_tiles;
         b.dirty = true;
     }
+    if (b.dtype == TC_BF16X3 && (!b.ddescs || !b.dstatus)) {
+        cudaError_t e = cudaSuccess;
+        if (!b.ddescs) e = cudaMalloc(&b.ddescs, gett_desc_bytes() * b.count);
+        if (e == cudaSuccess && !b.dstatus) e = cudaMalloc(&b.dstatus, 16);
+        if (e == cudaSuccess) e = cudaMemset(b.dstatus, 0, 16);
+        if (e != cudaSuccess) return fail(TC_ERROR_OUT_OF_MEMORY, cudaGetErrorString(e));
+        b.dirty = true;
+    }
     if (b.dirty) {
         cudaError_t e = cudaMemcpy(b.dprobs, b.probs.data(), sizeof(BatchProblem) * b.count, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+        if (b.dtype == TC_BF16X3) {
+            const size_t db = gett_desc_bytes();
+            std::vector<unsigned char> hd(db * b.count);
+            for (int slot = 0; slot < b.count; ++slot) gett_fill_batch_desc(b.probs[slot], b.bn, hd.data() + db * slot);
+            e = cudaMemcpy(b.ddescs, hd.data(), hd.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+        }
         std::vector<int32_t> tp(b.total_tiles);
         for (int slot = 0; slot < b.count; ++slot) {
             const int64_t t1 = slot + 1 < b.count ? b.probs[slot + 1].tile0 : b.total_tiles;
@@ -404,6 +443,23 @@ tc_status tc_batch_execute(tc_batch batch, const void *alpha, const void *beta, 
         if (g_bsms <= 0) g_bsms = 1;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    b.last_stream = stream;
+    if (b.dtype == TC_BF16X3) {
+        const float a = *(const float *)alpha, be = *(const float *)beta;
+        auto run = [&](int64_t t0, int64_t t1) {
+            return gett_launch_batch(b.ddescs, b.dtile_prob, t0, t1, b.bn, a, be, b.nprod, b.dstatus, stream);
+        };
+        if (one_launch_per_problem) {
+            for (int slot = 0; slot < b.count; ++slot) {
+                const int64_t t0 = b.probs[slot].tile0;
+                const int64_t t1 = slot + 1 < b.count ? b.probs[slot + 1].tile0 : b.total_tiles;
+                tc_status s = run(t0, t1);
+                if (s != TC_SUCCESS) return s;
+            }
+            return TC_SUCCESS;
+        }
+        return run(0, b.total_tiles);
+    }
     // persistent grid: exactly the CTAs that fit at once
     int per_sm = 1;
     if (b.dtype == TC_F64)
@@ -447,11 +503,24 @@ tc_status tc_batch_info(tc_batch batch, double *flops, int64_t *tiles, int64_t *
     if (flops) *flops = b.flops;
     if (tiles) *tiles = b.total_tiles;
     if (bytes) {
-        const int64_t es = b.dtype == TC_F64 ? 8 : 4;
+        const int64_t es = b.dtype == TC_F64 ? 8 : 4;  // split-BF16: FP32 I/O
         int64_t t = 0;
         for (const auto &P : b.probs) t += (P.M * P.K + P.K * P.N + P.M * P.N) * es;
         *bytes = t;
     }
+    return TC_SUCCESS;
+}
+
+tc_status tc_batch_device_status(tc_batch batch) {
+    if (!batch) return fail(TC_ERROR_INVALID_ARGUMENT, "batch is NULL");
+    BatchImpl &b = batch->b;
+    if (!b.dstatus) return TC_SUCCESS;
+    int v = 0;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)b.last_stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&v, b.dstatus, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && v != 0) e = cudaMemset(b.dstatus, 0, sizeof(int));
+    if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+    if (v != 0) return fail((tc_status)v, "a bounded wait in the batched kernel ran out");
     return TC_SUCCESS;
 }
 

@@ -72,6 +72,7 @@ struct GettDesc {
     int nm, nn, nk;                       // number of M / N / K modes
     int64_t m_ext[kMaxModes], m_sA[kMaxModes], m_sC[kMaxModes];
     int64_t n_ext[kMaxModes], n_sB[kMaxModes], n_sC[kMaxModes];
+    int n_chain;                          // C offset of column n is n * n_sC[0]
     int64_t k_ext[kMaxModes], k_sA[kMaxModes], k_sB[kMaxModes];  // outermost first
     int64_t M, N, K;
     int64_t tiles_m, tiles_n;
@@ -99,6 +100,13 @@ struct GettDesc {
     uint32_t tma_bytes;  // staged bytes per stage (both operands)
     double tile_frac;    // micro-benchmark: run this fraction of the tiles
     int chunk_stages;    // compensated form: K stages per TMEM chunk
+    // batched form: per-problem descriptors (num_tiles, status, nprod,
+    // alpha, beta and init are the batch's, in this descriptor), the
+    // problem of each tile, and each problem's first tile
+    const GettDesc *probs;
+    const int32_t *tile_prob;
+    int64_t tile0;
+    int64_t tile_begin;  // first tile of this launch (batched form; else 0)
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -255,6 +263,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
           "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
           "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// 64 consecutive columns of this warp's 32 lanes with one wait: the load
+// latency is paid once per 64 columns instead of once per 32.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -504,12 +524,54 @@ __device__ __forceinline__ void convert_staged(const char *stg, int srow, const 
     }
 }
 
+// The descriptor of a tile's problem: the launch's own, or in the batched
+// form the one its tile-to-problem table names.
+template <bool BATCH>
+__device__ __forceinline__ const GettDesc &tile_desc(const GettDesc &d, int64_t tile) {
+    if constexpr (BATCH) return d.probs[d.tile_prob[tile]];
+    else return d;
+}
+
+// Epilogue stores of W accumulator columns c0.. of this thread's row (C
+// offset om, -1 = no row): columns at on0 + j*lin when lin != 0 (the tile's
+// columns form one stride), else through the tile's column table cn
+// (-1 = past N).  C = alpha*acc (init 2) or alpha*acc + beta*C (init 1).
+template <int W>
+__device__ __forceinline__ void store_cols(const uint32_t (&r)[W], float *__restrict__ C, int64_t om, int c0,
+                                           int64_t lin, int64_t on0, int64_t nval, const int64_t *cn,
+                                           float alpha, float beta, int init) {
+    if (om < 0) return;
+    if (lin != 0) {
+        float *p = C + om + on0 + (int64_t)c0 * lin;
+        const int64_t jn = nval - c0;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            if (j < jn) {
+                float v = alpha * __uint_as_float(r[j]);
+                if (init == 1) v = fmaf(beta, *p, v);
+                *p = v;
+            }
+            p += lin;
+        }
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const int64_t on = cn[c0 + j];
+        if (on < 0) continue;
+        float v = alpha * __uint_as_float(r[j]);
+        if (init == 1) v = fmaf(beta, C[om + on], v);
+        C[om + on] = v;
+    }
+}
+
 // COMP (split-BF16 with long K): the MMA accumulates chunks of
 // chunk_stages K stages into two alternating TMEM accumulators; the
 // epilogue folds each finished chunk into a float-float running sum
 // (hi, lo) kept in TMEM (TwoSum), so the FP32 rounding of the accumulator
 // grows with the chunk length instead of with K.
-template <int KIND, int BN, int STAGES, int BK, int SSTG, bool COMP>
+// BATCH: the tiles of many problems in one launch (global-load inputs).
+template <int KIND, int BN, int STAGES, int BK, int SSTG, bool COMP, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1)
 gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
     using T = KindTraits<KIND, BK>;
@@ -571,16 +633,19 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     if (warp >= kEpiWarps && warp < kMmaWarp) {
         // ---------------------------------------------------------- converters
         const int pt = threadIdx.x - kEpiThreads;
-        const In *__restrict__ Ap = (const In *)d.A;
-        const In *__restrict__ Bp = (const In *)d.B;
         int64_t g = 0;
         int it = 0;
         bool stop = false;
-        for (int64_t tile = blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x, ++it) {
-            const int64_t m0 = (tile % d.tiles_m) * kBM, n0 = (tile / d.tiles_m) * BN;
+        for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x, ++it) {
+            const GettDesc &P = tile_desc<BATCH>(d, tile);
+            const int64_t lt = BATCH ? tile - P.tile0 : tile;
+            const int nkt_t = BATCH ? (int)((P.K + BK - 1) / BK) : nkt;
+            const In *__restrict__ Ap = (const In *)P.A;
+            const In *__restrict__ Bp = (const In *)P.B;
+            const int64_t m0 = (lt % P.tiles_m) * kBM, n0 = (lt / P.tiles_m) * BN;
             int64_t *rA = rowA + (it & 1) * kBM;
             int64_t *rB = rowB + (it & 1) * BN;
-            for (int kt = 0; kt < nkt; ++kt, ++g) {
+            for (int kt = 0; kt < nkt_t; ++kt, ++g) {
                 const int s = (int)(g % STAGES);
                 const uint32_t ph = (uint32_t)((g / STAGES) & 1);
                 const int ss = (int)(g % SS);
@@ -591,41 +656,41 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                     if (kt == 0) {
                         for (int i = pt; i < kBM; i += kProducerThreads) {
                             int64_t mm = m0 + i, oa = -1, oc = 0;
-                            if (mm < d.M) {
+                            if (mm < P.M) {
                                 oa = 0;
-                                decode(mm, d.nm, d.m_ext, d.m_sA, d.m_sC, oa, oc);
+                                decode(mm, P.nm, P.m_ext, P.m_sA, P.m_sC, oa, oc);
                             }
                             rA[i] = oa;
                         }
                         for (int j = pt; j < BN; j += kProducerThreads) {
                             int64_t nn = n0 + j, ob = -1, oc = 0;
-                            if (nn < d.N) {
+                            if (nn < P.N) {
                                 ob = 0;
-                                decode(nn, d.nn, d.n_ext, d.n_sB, d.n_sC, ob, oc);
+                                decode(nn, P.nn, P.n_ext, P.n_sB, P.n_sC, ob, oc);
                             }
                             rB[j] = ob;
                         }
                     }
                     if (pt < BK) {
                         int64_t k = (int64_t)kt * BK + pt, oa = -1, ob = -1;
-                        if (k < d.K) {
+                        if (k < P.K) {
                             oa = 0;
                             ob = 0;
-                            if (d.K < (int64_t(1) << 31)) {  // 32-bit digits when they fit
+                            if (P.K < (int64_t(1) << 31)) {  // 32-bit digits when they fit
                                 uint32_t k32 = (uint32_t)k;
-                                for (int m = d.nk - 1; m >= 0; --m) {  // innermost K mode fastest
-                                    const uint32_t e = (uint32_t)d.k_ext[m];
+                                for (int m = P.nk - 1; m >= 0; --m) {  // innermost K mode fastest
+                                    const uint32_t e = (uint32_t)P.k_ext[m];
                                     const int64_t v = (int64_t)(k32 % e);
                                     k32 /= e;
-                                    oa += v * d.k_sA[m];
-                                    ob += v * d.k_sB[m];
+                                    oa += v * P.k_sA[m];
+                                    ob += v * P.k_sB[m];
                                 }
                             } else {
-                                for (int m = d.nk - 1; m >= 0; --m) {
-                                    int64_t v = k % d.k_ext[m];
-                                    k /= d.k_ext[m];
-                                    oa += v * d.k_sA[m];
-                                    ob += v * d.k_sB[m];
+                                for (int m = P.nk - 1; m >= 0; --m) {
+                                    int64_t v = k % P.k_ext[m];
+                                    k /= P.k_ext[m];
+                                    oa += v * P.k_sA[m];
+                                    ob += v * P.k_sB[m];
                                 }
                             }
                         }
@@ -647,13 +712,13 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                     convert_staged<KIND, BK, kBM>(stg + ss * (SP::kStgA + SP::kStgB), d.srow[0], d.sk[0],
                                                   d.sk_vec4[0], stage, SP::kATile, pt);
                 } else {
-                    produce_any<KIND, BK, kBM>(Ap, rA, kA + s * BK, stage, SP::kATile, d.a_map, pt);
+                    produce_any<KIND, BK, kBM>(Ap, rA, kA + s * BK, stage, SP::kATile, P.a_map, pt);
                 }
                 if (TMA && d.tma[1]) {
                     convert_staged<KIND, BK, BN>(stg + ss * (SP::kStgA + SP::kStgB) + SP::kStgA, d.srow[1],
                                                  d.sk[1], d.sk_vec4[1], bstage, SP::kBTile, pt);
                 } else {
-                    produce_any<KIND, BK, BN>(Bp, rB, kB + s * BK, bstage, SP::kBTile, d.b_map, pt);
+                    produce_any<KIND, BK, BN>(Bp, rB, kB + s * BK, bstage, SP::kBTile, P.b_map, pt);
                 }
                 // each lane publishes its stores to the async proxy; the warp's
                 // lanes are ordered by __syncwarp and lane 0 arrives for all
@@ -670,7 +735,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         if (TMA && any_tma && lane == 0) {
             int64_t g = 0;
             bool stop = false;
-            for (int64_t tile = blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x) {
+            for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x) {
                 const int64_t m0 = (tile % d.tiles_m) * kBM, n0 = (tile / d.tiles_m) * BN;
                 int32_t rc[2][kTmaRank] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
                 {
@@ -743,8 +808,10 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             int64_t g = 0;
             int64_t u = 0;  // accumulation units (tiles, or K chunks of tiles)
             bool stop = false;
-            for (int64_t tile = blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x) {
-                for (int c = 0; c < nch && !stop; ++c, ++u) {
+            for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x) {
+                const int nkt_t = BATCH ? (int)((tile_desc<BATCH>(d, tile).K + BK - 1) / BK) : nkt;
+                const int cstg_t = BATCH ? nkt_t : cstg, nch_t = BATCH ? 1 : nch;
+                for (int c = 0; c < nch_t && !stop; ++c, ++u) {
                     const int buf = (int)(u & 1);
                     if (u >= 2 && !mbar_wait(&tempty[buf], (uint32_t)(((u / 2) - 1) & 1))) {
                         stop = true;
@@ -752,8 +819,8 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                     }
                     tc_fence_after();
                     const uint32_t dt = tmem + (uint32_t)(buf * BN);
-                    const int kt_end = min(nkt, (c + 1) * cstg);
-                    for (int kt = c * cstg; kt < kt_end; ++kt, ++g) {
+                    const int kt_end = min(nkt_t, (c + 1) * cstg_t);
+                    for (int kt = c * cstg_t; kt < kt_end; ++kt, ++g) {
                         const int s = (int)(g % STAGES);
                         if (*abort_flag || !mbar_wait(&full[s], (uint32_t)((g / STAGES) & 1))) {
                             stop = true;
@@ -762,7 +829,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                         tc_fence_after();
                         const uint32_t sa = base + s * SP::kStage;
                         const uint32_t sb = sa + T::kSlices * SP::kATile;
-                        const bool first = kt == c * cstg;
+                        const bool first = kt == c * cstg_t;
 #pragma unroll
                         for (int ks = 0; ks < T::kKsteps; ++ks) {
                             for (int q = 0; q < nprod; ++q) {
@@ -789,32 +856,50 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     } else {
         // ---------------------------------------------------------- epilogue
         const int et = threadIdx.x;  // 0..127 = accumulator row = TMEM lane
-        float *__restrict__ C = d.C;
         int it = 0;
         int64_t u = 0;
-        for (int64_t tile = blockIdx.x; tile < d.num_tiles; tile += gridDim.x, ++it) {
-            const int64_t m0 = (tile % d.tiles_m) * kBM, n0 = (tile / d.tiles_m) * BN;
+        for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles; tile += gridDim.x, ++it) {
+            const GettDesc &P = tile_desc<BATCH>(d, tile);
+            const int64_t lt = BATCH ? tile - P.tile0 : tile;
+            const int nch_t = BATCH ? 1 : nch;
+            float *__restrict__ C = P.C;
+            const int64_t m0 = (lt % P.tiles_m) * kBM, n0 = (lt / P.tiles_m) * BN;
             int64_t *cn = cN + (it & 1) * BN;
-            for (int j = et; j < BN; j += kEpiThreads) {
-                int64_t nn = n0 + j, ob = 0, oc = -1;
-                if (nn < d.N) {
-                    oc = 0;
-                    decode(nn, d.nn, d.n_ext, d.n_sB, d.n_sC, ob, oc);
+            // one stride across the tile's columns: no column table
+            const int64_t nval = min((int64_t)BN, P.N - n0);
+            int64_t lin = 0, on0 = 0;
+            if (P.nn == 0) {
+                lin = 0;  // a single column: the table
+            } else if (P.n_chain) {
+                lin = P.n_sC[0];
+                on0 = n0 * lin;
+            } else if ((n0 % P.n_ext[0]) + BN <= P.n_ext[0]) {
+                int64_t ob = 0;
+                decode(n0, P.nn, P.n_ext, P.n_sB, P.n_sC, ob, on0);
+                lin = P.n_sC[0];
+            }
+            if (lin == 0) {
+                for (int j = et; j < BN; j += kEpiThreads) {
+                    int64_t nn = n0 + j, ob = 0, oc = -1;
+                    if (nn < P.N) {
+                        oc = 0;
+                        decode(nn, P.nn, P.n_ext, P.n_sB, P.n_sC, ob, oc);
+                    }
+                    cn[j] = oc;
                 }
-                cn[j] = oc;
             }
             int64_t om = -1;
             {
                 int64_t mm = m0 + et, oa = 0;
-                if (mm < d.M) {
+                if (mm < P.M) {
                     om = 0;
-                    decode(mm, d.nm, d.m_ext, d.m_sA, d.m_sC, oa, om);
+                    decode(mm, P.nm, P.m_ext, P.m_sA, P.m_sC, oa, om);
                 }
             }
             if (role_sync_or<2, kEpiThreads>(*abort_flag)) break;
             const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
             bool aborted = false;
-            for (int c = 0; c < nch; ++c, ++u) {
+            for (int c = 0; c < nch_t; ++c, ++u) {
                 const int buf = (int)(u & 1);
                 bool ok = mbar_wait(&tfull[buf], (uint32_t)((u / 2) & 1));
                 ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld needs the whole warp
@@ -827,59 +912,59 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                 tc_fence_after();
                 const uint32_t acc = tmem + lane_off + (uint32_t)(buf * BN);
                 const uint32_t hi = tmem + lane_off + (uint32_t)(2 * BN), lo = hi + (uint32_t)BN;
-                const bool last = c == nch - 1;
+                const bool last = c == nch_t - 1;
+if constexpr (!COMP) {
 #pragma unroll 1
-                for (int c0 = 0; c0 < BN; c0 += 32) {
-                    uint32_t r[32];
-                    tmem_ld32(acc + (uint32_t)c0, r);
-                    if constexpr (COMP) {
-                        // two 32-register arrays live at a time (r and t)
-                        if (nch > 1) {
-                            if (c == 0) {
-                                tmem_st32(hi + (uint32_t)c0, r);
-                                tmem_st32_zero(lo + (uint32_t)c0);
-                                continue;
-                            }
-                            uint32_t t[32];
-                            if (last) {  // result = hi + (lo + chunk): one rounding per step
-                                tmem_ld32(lo + (uint32_t)c0, t);
-#pragma unroll
-                                for (int j = 0; j < 32; ++j)
-                                    r[j] = __float_as_uint(__fadd_rn(__uint_as_float(t[j]), __uint_as_float(r[j])));
-                                tmem_ld32(hi + (uint32_t)c0, t);
-#pragma unroll
-                                for (int j = 0; j < 32; ++j)
-                                    r[j] = __float_as_uint(__fadd_rn(__uint_as_float(t[j]), __uint_as_float(r[j])));
-                            } else {  // (hi, err) = TwoSum(hi, chunk); lo += err
-                                tmem_ld32(hi + (uint32_t)c0, t);
-#pragma unroll
-                                for (int j = 0; j < 32; ++j) {
-                                    const float a = __uint_as_float(t[j]), b = __uint_as_float(r[j]);
-                                    const float s2 = __fadd_rn(a, b);
-                                    const float bb = __fsub_rn(s2, a);
-                                    t[j] = __float_as_uint(s2);
-                                    r[j] = __float_as_uint(
-                                        __fadd_rn(__fsub_rn(a, __fsub_rn(s2, bb)), __fsub_rn(b, bb)));
-                                }
-                                tmem_st32(hi + (uint32_t)c0, t);
-                                tmem_ld32(lo + (uint32_t)c0, t);
-#pragma unroll
-                                for (int j = 0; j < 32; ++j)
-                                    t[j] = __float_as_uint(__fadd_rn(__uint_as_float(t[j]), __uint_as_float(r[j])));
-                                tmem_st32(lo + (uint32_t)c0, t);
-                                continue;
-                            }
-                        }
+                    for (int c0 = 0; c0 < BN; c0 += 64) {
+                        uint32_t r[64];
+                        tmem_ld64(acc + (uint32_t)c0, r);
+                        store_cols<64>(r, C, om, c0, lin, on0, nval, cn, d.alpha, d.beta, d.init);
                     }
-                    if (om >= 0) {
+                } else {
+#pragma unroll 1
+                    for (int c0 = 0; c0 < BN; c0 += 32) {
+                        uint32_t r[32];
+                        tmem_ld32(acc + (uint32_t)c0, r);
+                        if constexpr (COMP) {
+                            // two 32-register arrays live at a time (r and t)
+                            if (nch_t > 1) {
+                                if (c == 0) {
+                                    tmem_st32(hi + (uint32_t)c0, r);
+                                    tmem_st32_zero(lo + (uint32_t)c0);
+                                    continue;
+                                }
+                                uint32_t t[32];
+                                if (last) {  // result = hi + (lo + chunk): one rounding per step
+                                    tmem_ld32(lo + (uint32_t)c0, t);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int64_t on = cn[c0 + j];
-                            if (on < 0) continue;
-                            float v = d.alpha * __uint_as_float(r[j]);
-                            if (d.init == 1) v = fmaf(d.beta, C[om + on], v);
-                            C[om + on] = v;
+                                    for (int j = 0; j < 32; ++j)
+                                        r[j] = __float_as_uint(__fadd_rn(__uint_as_float(t[j]), __uint_as_float(r[j])));
+                                    tmem_ld32(hi + (uint32_t)c0, t);
+#pragma unroll
+                                    for (int j = 0; j < 32; ++j)
+                                        r[j] = __float_as_uint(__fadd_rn(__uint_as_float(t[j]), __uint_as_float(r[j])));
+                                } else {  // (hi, err) = TwoSum(hi, chunk); lo += err
+                                    tmem_ld32(hi + (uint32_t)c0, t);
+#pragma unroll
+                                    for (int j = 0; j < 32; ++j) {
+                                        const float a = __uint_as_float(t[j]), b = __uint_as_float(r[j]);
+                                        const float s2 = __fadd_rn(a, b);
+                                        const float bb = __fsub_rn(s2, a);
+                                        t[j] = __float_as_uint(s2);
+                                        r[j] = __float_as_uint(
+                                            __fadd_rn(__fsub_rn(a, __fsub_rn(s2, bb)), __fsub_rn(b, bb)));
+                                    }
+                                    tmem_st32(hi + (uint32_t)c0, t);
+                                    tmem_ld32(lo + (uint32_t)c0, t);
+#pragma unroll
+                                    for (int j = 0; j < 32; ++j)
+                                        t[j] = __float_as_uint(__fadd_rn(__uint_as_float(t[j]), __uint_as_float(r[j])));
+                                    tmem_st32(lo + (uint32_t)c0, t);
+                                    continue;
+                                }
+                            }
                         }
+                        store_cols<32>(r, C, om, c0, lin, on0, nval, cn, d.alpha, d.beta, d.init);
                     }
                 }
                 tc_fence_before();
@@ -900,14 +985,14 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
 // ------------------------------------------------------------------ host side
 int g_gett_sms = 0;
 
-template <int KIND, int BN, int STAGES, int BK, int SSTG, bool COMP = false>
+template <int KIND, int BN, int STAGES, int BK, int SSTG, bool COMP = false, bool BATCH = false>
 tc_status launch_gett(const GettDesc &d, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
     using SP = SmemPlan<KIND, BN, STAGES, BK, SSTG>;
     static_assert(SP::kTotal <= 227 * 1024, "shared memory budget");
     // at least 116 KB so that one CTA (and one tensor-memory allocation of
     // up to 512 columns) occupies each SM
     constexpr int kSmem = SP::kTotal > 116 * 1024 ? SP::kTotal : 116 * 1024;
-    auto kern = gett_tc_kernel<KIND, BN, STAGES, BK, SSTG, COMP>;
+    auto kern = gett_tc_kernel<KIND, BN, STAGES, BK, SSTG, COMP, BATCH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
     if (g_gett_sms == 0) {
@@ -916,7 +1001,7 @@ tc_status launch_gett(const GettDesc &d, const CUtensorMap &ta, const CUtensorMa
         cudaDeviceGetAttribute(&g_gett_sms, cudaDevAttrMultiProcessorCount, dev);
         if (g_gett_sms <= 0) g_gett_sms = 1;
     }
-    const int64_t grid = std::min<int64_t>(d.num_tiles, g_gett_sms);
+    const int64_t grid = std::min<int64_t>(d.num_tiles - d.tile_begin, g_gett_sms);
     kern<<<(unsigned)grid, kThreads, kSmem, st>>>(d, ta, tb);
     e = cudaGetLastError();
     return e == cudaSuccess ? TC_SUCCESS : fail(TC_ERROR_CUDA, cudaGetErrorString(e));
@@ -1212,6 +1297,9 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
         d.n_sC[m] = p.op[OP_C].stride_of(id);
         d.N *= p.ext[id];
     }
+    d.n_chain = 1;
+    for (int m = 0; m + 1 < d.nn; ++m)
+        if (d.n_sC[m + 1] != d.n_sC[m] * d.n_ext[m]) d.n_chain = 0;
     for (int m = 0; m < d.nk; ++m) {
         d.k_ext[m] = kmodes[m].ext;
         d.k_sA[m] = kmodes[m].sA;
@@ -1265,6 +1353,64 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     case TC_TF32: return launch_kind<GK_TF32>(d, bn, tma, comp, tmA, tmB, st);
     default: return fail(TC_ERROR_UNSUPPORTED_DTYPE, "dtype has no tensor-core GETT");
     }
+}
+
+// ------------------------------------------------------------ batched form
+size_t gett_desc_bytes() { return sizeof(GettDesc); }
+
+void gett_fill_batch_desc(const BatchProblem &P, int bn, void *out) {
+    GettDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.nm = d.nn = d.nk = 1;
+    d.M = P.M;
+    d.N = P.N;
+    d.K = P.K;
+    d.m_ext[0] = P.M;
+    d.m_sA[0] = P.sAm;
+    d.m_sC[0] = P.sCm;
+    d.n_ext[0] = P.N;
+    d.n_sB[0] = P.sBn;
+    d.n_sC[0] = P.sCn;
+    d.n_chain = 1;
+    d.k_ext[0] = P.K;
+    d.k_sA[0] = P.sAk;
+    d.k_sB[0] = P.sBk;
+    d.A = P.A;
+    d.B = P.B;
+    d.C = (float *)P.C;
+    d.tiles_m = P.tiles_m;
+    d.tiles_n = (P.N + bn - 1) / bn;
+    d.tile0 = P.tile0;
+    auto pick = [&](const void *base, int rows, const int64_t *rext, const int64_t *rs, const int64_t *ks) {
+        if (vec_ok(base, 4, 1, rs, 1, d.k_ext, ks)) return 2;
+        int64_t s0 = sectors_for(0, rows, 8, 4, 1, rext, rs, 1, d.k_ext, ks);
+        int64_t s1 = sectors_for(1, rows, 8, 4, 1, rext, rs, 1, d.k_ext, ks);
+        return s1 < s0 ? 1 : 0;
+    };
+    d.a_map = pick(P.A, kBM, d.m_ext, d.m_sA, d.k_sA);
+    d.b_map = pick(P.B, bn, d.n_ext, d.n_sB, d.k_sB);
+    std::memcpy(out, &d, sizeof(d));
+}
+
+tc_status gett_launch_batch(const void *ddescs, const int32_t *dtile_prob, int64_t t_begin, int64_t t_end, int bn,
+                            float alpha, float beta, int nprod, int *dstatus, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    GettDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.probs = (const GettDesc *)ddescs;
+    d.tile_prob = dtile_prob;
+    d.tile_begin = t_begin;
+    d.num_tiles = t_end;
+    d.alpha = alpha;
+    d.beta = beta;
+    d.init = beta == 0.0f ? 2 : 1;
+    d.nprod = nprod;
+    d.status = dstatus;
+    d.tile_frac = 1.0;
+    CUtensorMap none;
+    std::memset(&none, 0, sizeof(none));
+    if (bn == 128) return launch_gett<GK_BF16X3, 128, 4, kBK, 0, false, true>(d, none, none, st);
+    return launch_gett<GK_BF16X3, 256, 2, kBK, 0, false, true>(d, none, none, st);
 }
 
 // Bounded-wait self-test: thread 0 waits on an mbarrier with the wait every

@@ -105,6 +105,27 @@ size_t gett_workspace_bytes(const Plan &p);
 void gett_release(Plan &p);
 tc_status ensure_device_resources(Plan &p, size_t workspace_bytes);
 
+// One problem of the batched form: a strided GEMM over the merged free
+// modes of A (m), of B (n) and the merged contracted modes (k).
+struct BatchProblem {
+    int64_t M, N, K;
+    int64_t sAm, sAk, sBk, sBn, sCm, sCn;
+    const void *A;
+    const void *B;
+    void *C;
+    int64_t tile0;    // first tile of this problem in the flattened list
+    int32_t shape;    // SIMT tiles 0: 64x64, 1: 32x128, 2: 16x256
+    int32_t tiles_m;
+};
+
+// Batched split-BF16 on the tensor-core GETT kernel: one device descriptor
+// per problem (gett_desc_bytes each, filled by gett_fill_batch_desc for
+// 128 x bn tiles), then one launch over tiles [t_begin, t_end).
+size_t gett_desc_bytes();
+void gett_fill_batch_desc(const BatchProblem &P, int bn, void *out);
+tc_status gett_launch_batch(const void *ddescs, const int32_t *dtile_prob, int64_t t_begin, int64_t t_end, int bn,
+                            float alpha, float beta, int nprod, int *dstatus, void *stream);
+
 }  // namespace tc
 
 struct tc_plan_s {

@@ -105,6 +105,7 @@ SIGNATURES = {
     "tc_batch_prepare": (ctypes.c_int, [_VP]),
     "tc_batch_execute": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, _VP]),
     "tc_batch_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), _I64P, _I64P]),
+    "tc_batch_device_status": (ctypes.c_int, [_VP]),
     "tc_server_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]),
     "tc_server_submit": (ctypes.c_int, [_VP, ctypes.c_char_p, _I64P, ctypes.c_int, _VP, _VP, _VP, _I64P]),
     "tc_server_poll": (ctypes.c_int, [_VP, ctypes.c_int64, _I32P, ctypes.POINTER(ctypes.c_double)]),
@@ -363,6 +364,9 @@ class Batch:
         _check(load().tc_batch_info(self.handle, ctypes.byref(f), ctypes.byref(t), ctypes.byref(b)),
                "tc_batch_info")
         return {"flops": f.value, "tiles": t.value, "bytes": b.value}
+
+    def device_status(self):
+        _check(load().tc_batch_device_status(self.handle), "tc_batch_device_status")
 
     def close(self):
         if self.handle is not None and _lib is not None:

@@ -31,7 +31,7 @@ def problems(count, lo, hi, seed):
 
 
 def make(ext_rows, dtype, seed, integer=False):
-    tdt = {"f32": torch.float32, "f64": torch.float64}[dtype]
+    tdt = {"f32": torch.float32, "f64": torch.float64, "bf16x3": torch.float32}[dtype]
     As, Bs, Cs, host = [], [], [], []
     for q, ext in enumerate(ext_rows):
         gen = synth.integer_operands if integer else synth.uniform_operands
@@ -112,3 +112,78 @@ def test_batch_alpha_beta(tcmod):
 def test_batch_rejects_unmergeable_spec(tcmod):
     with pytest.raises(tcmod.TcError):
         tcmod.Batch("ab=aij,jib", [[4, 4, 2, 2]], "f32")
+
+
+# split-BF16 batches run on the tensor-core GETT kernel (128-row tiles)
+U = 2.0 ** -24
+
+
+def test_batch_bf16x3_exact_on_integers(tcmod):
+    rows = problems(300, 8, 40, seed=4)
+    As, Bs, Cs, host = make(rows, "bf16x3", 40, integer=True)
+    batch = tcmod.Batch(SPEC, rows, "bf16x3")
+    batch.set_operands(As, Bs, Cs)
+    batch.execute()
+    torch.cuda.synchronize()
+    batch.device_status()
+    for ext, (A, B), C in zip(rows, host, Cs):
+        assert np.array_equal(C.double().cpu().numpy(), oc.contract(SPEC, ext, A, B)), ext
+    batch.close()
+
+
+def test_batch_bf16x3_bound_launch_modes_and_graph(tcmod):
+    rows = problems(60, 8, 128, seed=5)
+    As, Bs, Cs, host = make(rows, "bf16x3", 50)
+    batch = tcmod.Batch(SPEC, rows, "bf16x3")
+    batch.set_operands(As, Bs, Cs)
+    batch.execute()
+    torch.cuda.synchronize()
+    batch.device_status()
+    ref = [c.clone() for c in Cs]
+    for (A, B), ext, C in zip(host, rows, ref):
+        Ar, Br = A.astype(np.float32).astype(np.float64), B.astype(np.float32).astype(np.float64)
+        want = oc.contract(SPEC, ext, Ar, Br)
+        scale = oc.contract(SPEC, ext, np.abs(Ar), np.abs(Br))
+        K = ext[3]
+        assert np.max(np.abs(C.double().cpu().numpy() - want) / scale) <= (6 * K + 4) * U, ext
+    # one launch per problem and a captured graph give the same bits
+    batch.execute(per_problem=True)
+    torch.cuda.synchronize()
+    assert all(torch.equal(c, r) for c, r in zip(Cs, ref))
+    for c in Cs:
+        c.fill_(float("nan"))
+    batch.prepare()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        batch.execute(stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert all(torch.equal(c, r) for c, r in zip(Cs, ref))
+    # the other tile width: within the same bound
+    batch.set_tiles(0)
+    batch.execute()
+    torch.cuda.synchronize()
+    batch.device_status()
+    for (A, B), ext, C in zip(host[:20], rows[:20], Cs[:20]):
+        Ar, Br = A.astype(np.float32).astype(np.float64), B.astype(np.float32).astype(np.float64)
+        want = oc.contract(SPEC, ext, Ar, Br)
+        scale = oc.contract(SPEC, ext, np.abs(Ar), np.abs(Br))
+        assert np.max(np.abs(C.double().cpu().numpy() - want) / scale) <= (6 * ext[3] + 4) * U
+    batch.close()
+
+
+def test_batch_bf16x3_alpha_beta(tcmod):
+    rows = problems(50, 8, 30, seed=6)
+    As, Bs, Cs, host = make(rows, "bf16x3", 60, integer=True)
+    for c in Cs:
+        c.fill_(3.0)
+    batch = tcmod.Batch(SPEC, rows, "bf16x3")
+    batch.set_operands(As, Bs, Cs)
+    batch.execute(alpha=2.0, beta=-0.5)
+    torch.cuda.synchronize()
+    batch.device_status()
+    for ext, (A, B), C in zip(rows, host, Cs):
+        want = 2.0 * oc.contract(SPEC, ext, A, B) - 1.5
+        assert np.array_equal(C.double().cpu().numpy(), want)
+    batch.close()

@@ -297,3 +297,39 @@ def test_precision_workload_meets_fp32_level(tcmod, dist):
     err = float(np.max(np.abs(got[pts[:, 0] + 4096 * pts[:, 1]] - want) / scale))
     assert err <= 1e-6, err
     assert np.isfinite(got).all()
+
+
+# Output layouts of the epilogue: C whose free modes of B do not chain
+# (padded strides: the per-tile column check and the column table), and
+# contractions with no free index in B or in A.
+EPI_CASES = [
+    ("abc=ai,ibc", [130, 40, 9, 24], [1, 133, 133 * 40 + 7, 1, 130, 1, 24, 24 * 40]),
+    ("abc=ai,ibc", [64, 300, 3, 16], [1, 64 * 1, 64 * 300 + 32, 1, 64, 1, 16, 16 * 300]),
+    ("a=ai,i", [200, 48], None),
+    ("b=i,ib", [48, 300], None),
+]
+
+
+@pytest.mark.parametrize("dtype", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("spec,ext,strides", EPI_CASES)
+def test_gett_output_layouts(tcmod, spec, ext, strides, dtype):
+    A, B, _ = synth.uniform_operands(spec, ext, seed=11)
+    nc = oc.required_length(oc.parse_spec(spec)[0], *oc.operand_layout(spec, ext, strides)[0:2])
+    C0 = np.random.default_rng(3).uniform(-1, 1, nc)
+    dA, dB, (Ar, Br) = device_inputs(dtype, A, B)
+    plan = tcmod.Plan(spec, ext, strides=strides, dtype=dtype)
+    plan.select(0)
+    dC = torch.from_numpy(C0).float().to("cuda:0")
+    plan.execute(dA, dB, dC, alpha=0.5, beta=2.0)
+    torch.cuda.synchronize()
+    plan.device_status()
+    plan.close()
+    got = dC.double().cpu().numpy()
+    C0f = C0.astype(np.float32).astype(np.float64)
+    want = oc.contract(spec, ext, Ar, Br, C=C0f.copy(), alpha=0.5, beta=2.0, strides=strides)
+    scale = 0.5 * oc.contract(spec, ext, np.abs(Ar), np.abs(Br), strides=strides,
+                              C=np.zeros(nc)) + 2.0 * np.abs(C0f)
+    K = ksize(spec, ext)
+    bound = (6 * K + 8) * U32 if dtype == "bf16x3" else (K + 3) * U32 / (1 - (K + 3) * U32)
+    err = np.abs(got - want) / np.maximum(scale, 1e-300)
+    assert float(np.max(err)) <= bound, (float(np.max(err)), bound)
