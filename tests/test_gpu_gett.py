@@ -333,3 +333,15 @@ def test_gett_output_layouts(tcmod, spec, ext, strides, dtype):
     bound = (6 * K + 8) * U32 if dtype == "bf16x3" else (K + 3) * U32 / (1 - (K + 3) * U32)
     err = np.abs(got - want) / np.maximum(scale, 1e-300)
     assert float(np.max(err)) <= bound, (float(np.max(err)), bound)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("spec,ext", [
+    ("abc=ai,ibc", [1, 1, 1, 1]),        # every extent one
+    ("abc=ai,ibc", [130, 3, 70, 1]),     # K = 1 (one product per output)
+    ("abc=iaj,jbic", [1, 300, 2, 1, 1]),  # M = 1, K = 1
+])
+def test_gett_degenerate_extents(tcmod, spec, ext, dtype):
+    A, B, _ = synth.integer_operands(spec, ext, seed=14)
+    dA, dB, _ = device_inputs(dtype, A, B)
+    assert np.array_equal(run_gett(tcmod, spec, ext, dtype, dA, dB), oc.contract(spec, ext, A, B))
