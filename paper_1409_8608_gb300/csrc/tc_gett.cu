@@ -346,12 +346,26 @@ struct SmemPlan {
     static constexpr int kTotal = kOpBytes + kStgBytes + kKTab + kRowTab + kColTab + kBars;
 };
 
+// x = q * y + r for non-negative x, y > 0: 32-bit division when both fit
+// (a 64-bit division is a long dependent instruction sequence, and these
+// sit on the per-tile critical path of every role)
+__device__ __forceinline__ int64_t divmod(int64_t x, int64_t y, int64_t &r) {
+    if (((x | y) >> 31) == 0) {
+        const uint32_t q = (uint32_t)x / (uint32_t)y;
+        r = x - (int64_t)q * y;
+        return q;
+    }
+    const int64_t q = x / y;
+    r = x - q * y;
+    return q;
+}
+
 __device__ __forceinline__ void decode(int64_t x, int n, const int64_t *ext, const int64_t *s1,
                                        const int64_t *s2, int64_t &o1, int64_t &o2) {
     // first mode fastest
     for (int m = 0; m < n; ++m) {
-        int64_t v = x % ext[m];
-        x /= ext[m];
+        int64_t v;
+        x = divmod(x, ext[m], v);
         o1 += v * s1[m];
         o2 += v * s2[m];
     }
@@ -481,19 +495,19 @@ __device__ __forceinline__ void produce_any(const typename KindTraits<KIND, BK>:
 // laid out as the box's dimensions) into the core-matrix layout.  Row r of
 // the tile sits at r * srow, K position k at sk[k] (elements); rows past the
 // operand's extent were filled with zeros by the TMA unit.
-template <int KIND, int BK, int ROWS>
+template <int KIND, int BK, int ROWS, int NT = kProducerThreads>
 __device__ __forceinline__ void convert_staged(const char *stg, int srow, const int *sk, int vec4,
                                                char *tile, int slice_stride, int pt) {
     using T = KindTraits<KIND, BK>;
     using In = typename T::In;
     constexpr int KC = T::kKc, CH = T::kChunk;
-    constexpr int NC = ROWS * KC / kProducerThreads;
-    static_assert(NC * kProducerThreads == ROWS * KC, "even split");
+    constexpr int NC = ROWS * KC / NT;  // NT threads share the box
+    static_assert(NC * NT == ROWS * KC, "even split");
     constexpr bool kFloatIn = KIND == GK_BF16X3 || KIND == GK_TF32;
     const In *s = (const In *)stg;
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-        const int c = pt + i * kProducerThreads;
+        const int c = pt + i * NT;
         const int row = c % ROWS, kc = c / ROWS;  // rows across lanes: conflict-free stores
         char *dst = tile + (kc * (ROWS / 8) + row / 8) * 128 + (row % 8) * 16;
         const In *base = s + row * srow;
@@ -606,15 +620,22 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     const int nch = (nkt + cstg - 1) / cstg;
     const bool any_tma = TMA && (d.tma[0] || d.tma[1]);
     const bool any_ldg = !TMA || !d.tma[0] || !d.tma[1];
+    // both operands staged by TMA: the converter warps split into two groups
+    // of four that take alternate stages, so one group's waits and barrier
+    // overlap the other's conversion
+    const bool grouped = TMA && !BATCH && d.tma[0] && d.tma[1];
 
     if (threadIdx.x == 0) {
+        // one arrival per converter warp that converts a stage: all eight,
+        // or the four of one group when the groups take turns
+        const uint32_t conv_warps = grouped ? kProducerThreads / 64 : kProducerThreads / 32;
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], kProducerThreads / 32);  // one arrival per converter warp
+            mbar_init(&full[s], conv_warps);
             mbar_init(&empty[s], 1);
         }
         for (int s = 0; s < SS; ++s) {
             mbar_init(&sfull[s], 1);
-            mbar_init(&sempty[s], kProducerThreads / 32);
+            mbar_init(&sempty[s], conv_warps);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
@@ -636,22 +657,68 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         int64_t g = 0;
         int it = 0;
         bool stop = false;
-        for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x, ++it) {
+        if (grouped) {
+            const int gp = pt >> 7, ptg = pt & 127;  // group of 128 threads, rank within it
+            for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x) {
+                for (int kt = 0; kt < nkt; ++kt, ++g) {
+                    if ((int)(g & 1) != gp) continue;  // the other group's stage
+                    const int s = (int)(g % STAGES);
+                    const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+                    const int ss = (int)(g % SS);
+                    const uint32_t sph = (uint32_t)((g / SS) & 1);
+                    const bool e_ok = g < STAGES || mbar_try_wait(&empty[s], ph ^ 1u);
+                    const bool f_ok = mbar_try_wait(&sfull[ss], sph);
+                    bool bad = false;
+                    if (!e_ok) bad = !mbar_wait(&empty[s], ph ^ 1u);
+                    if (!f_ok && !bad) bad = !mbar_wait(&sfull[ss], sph);
+                    const bool quit = gp == 0 ? role_sync_or<1, 128>(bad || *abort_flag)
+                                              : role_sync_or<3, 128>(bad || *abort_flag);
+                    if (quit) {
+                        if (ptg == 0) {
+                            *abort_flag = 1;
+                            atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
+                        }
+                        stop = true;
+                        break;
+                    }
+                    char *stage = ops + s * SP::kStage;
+                    const char *box = stg + ss * (SP::kStgA + SP::kStgB);
+                    convert_staged<KIND, BK, kBM, 128>(box, d.srow[0], d.sk[0], d.sk_vec4[0], stage, SP::kATile, ptg);
+                    convert_staged<KIND, BK, BN, 128>(box + SP::kStgA, d.srow[1], d.sk[1], d.sk_vec4[1],
+                                                      stage + T::kSlices * SP::kATile, SP::kBTile, ptg);
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive(&full[s]);
+                        mbar_arrive(&sempty[ss]);
+                    }
+                }
+            }
+        }
+        for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop && !grouped;
+             tile += gridDim.x, ++it) {
             const GettDesc &P = tile_desc<BATCH>(d, tile);
             const int64_t lt = BATCH ? tile - P.tile0 : tile;
             const int nkt_t = BATCH ? (int)((P.K + BK - 1) / BK) : nkt;
             const In *__restrict__ Ap = (const In *)P.A;
             const In *__restrict__ Bp = (const In *)P.B;
-            const int64_t m0 = (lt % P.tiles_m) * kBM, n0 = (lt / P.tiles_m) * BN;
+            int64_t mt;
+            const int64_t nt = divmod(lt, P.tiles_m, mt);
+            const int64_t m0 = mt * kBM, n0 = nt * BN;
             int64_t *rA = rowA + (it & 1) * kBM;
             int64_t *rB = rowB + (it & 1) * BN;
             for (int kt = 0; kt < nkt_t; ++kt, ++g) {
                 const int s = (int)(g % STAGES);
                 const uint32_t ph = (uint32_t)((g / STAGES) & 1);
                 const int ss = (int)(g % SS);
+                // both barriers polled back to back (their latencies overlap);
+                // the bounded waits only when one is not complete yet
+                const uint32_t sph = (uint32_t)((g / SS) & 1);
+                const bool e_ok = g < STAGES || mbar_try_wait(&empty[s], ph ^ 1u);
+                const bool f_ok = !any_tma || mbar_try_wait(&sfull[ss], sph);
                 bool bad = false;
-                if (g >= STAGES) bad = !mbar_wait(&empty[s], ph ^ 1u);
-                if (any_tma && !bad) bad = !mbar_wait(&sfull[ss], (uint32_t)((g / SS) & 1));
+                if (!e_ok) bad = !mbar_wait(&empty[s], ph ^ 1u);
+                if (!f_ok && !bad) bad = !mbar_wait(&sfull[ss], sph);
                 if (any_ldg) {
                     if (kt == 0) {
                         for (int i = pt; i < kBM; i += kProducerThreads) {
@@ -735,27 +802,53 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         if (TMA && any_tma && lane == 0) {
             int64_t g = 0;
             bool stop = false;
-            for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x) {
-                const int64_t m0 = (tile % d.tiles_m) * kBM, n0 = (tile / d.tiles_m) * BN;
-                int32_t rc[2][kTmaRank] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
-                {
-                    int64_t r = m0;
-                    for (int m = 0; m < d.nm; ++m) {
-                        const int32_t v = (int32_t)(r % d.m_ext[m]);
+            // box coordinates of a tile's rows, and of one of its K stages
+            auto tile_rc = [&](int64_t tile, int32_t (&rc)[2][kTmaRank]) {
+                int64_t mt;
+                const int64_t nt = divmod(tile, d.tiles_m, mt);
+#pragma unroll
+                for (int o = 0; o < 2; ++o)
+#pragma unroll
+                    for (int x = 0; x < kTmaRank; ++x) rc[o][x] = 0;
+                int64_t r = mt * kBM, v;
+                for (int m = 0; m < d.nm; ++m) {
+                    r = divmod(r, d.m_ext[m], v);
+#pragma unroll
+                    for (int x = 0; x < kTmaRank; ++x)
+                        if (d.row_dim[0][m] == x) rc[0][x] = (int32_t)v;
+                }
+                r = nt * BN;
+                for (int m = 0; m < d.nn; ++m) {
+                    r = divmod(r, d.n_ext[m], v);
+#pragma unroll
+                    for (int x = 0; x < kTmaRank; ++x)
+                        if (d.row_dim[1][m] == x) rc[1][x] = (int32_t)v;
+                }
+            };
+            auto stage_c = [&](const int32_t (&rc)[2][kTmaRank], int kt, int32_t (&c)[2][kTmaRank]) {
+#pragma unroll
+                for (int o = 0; o < 2; ++o)
+#pragma unroll
+                    for (int x = 0; x < kTmaRank; ++x) c[o][x] = rc[o][x];
+                // the host keeps K below 2^31 on this path
+                uint32_t k = (uint32_t)kt * (uint32_t)BK;
+                for (int m = d.nk - 1; m >= 0; --m) {
+                    const uint32_t e = (uint32_t)d.k_ext[m];
+                    const uint32_t v = k % e;
+                    k /= e;
+#pragma unroll
+                    for (int o = 0; o < 2; ++o) {
+                        const int dd = d.k_dim[o][m];
+                        const int32_t add = (int32_t)(v * (uint32_t)d.k_mul[o][m]);
 #pragma unroll
                         for (int x = 0; x < kTmaRank; ++x)
-                            if (d.row_dim[0][m] == x) rc[0][x] = v;
-                        r /= d.m_ext[m];
-                    }
-                    r = n0;
-                    for (int m = 0; m < d.nn; ++m) {
-                        const int32_t v = (int32_t)(r % d.n_ext[m]);
-#pragma unroll
-                        for (int x = 0; x < kTmaRank; ++x)
-                            if (d.row_dim[1][m] == x) rc[1][x] = v;
-                        r /= d.n_ext[m];
+                            if (dd == x) c[o][x] += add;
                     }
                 }
+            };
+            int32_t rc[2][kTmaRank];
+            for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x) {
+                tile_rc(tile, rc);
                 for (int kt = 0; kt < nkt; ++kt, ++g) {
                     const int s = (int)(g % SS);
                     if (g >= SS && (*abort_flag || !mbar_wait(&sempty[s], (uint32_t)(((g / SS) - 1) & 1)))) {
@@ -763,25 +856,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                         break;
                     }
                     int32_t c[2][kTmaRank];
-#pragma unroll
-                    for (int o = 0; o < 2; ++o)
-#pragma unroll
-                        for (int x = 0; x < kTmaRank; ++x) c[o][x] = rc[o][x];
-                    // the host keeps K below 2^31 on this path
-                    uint32_t k = (uint32_t)kt * (uint32_t)BK;
-                    for (int m = d.nk - 1; m >= 0; --m) {
-                        const uint32_t e = (uint32_t)d.k_ext[m];
-                        const uint32_t v = k % e;
-                        k /= e;
-#pragma unroll
-                        for (int o = 0; o < 2; ++o) {
-                            const int dd = d.k_dim[o][m];
-                            const int32_t add = (int32_t)(v * (uint32_t)d.k_mul[o][m]);
-#pragma unroll
-                            for (int x = 0; x < kTmaRank; ++x)
-                                if (dd == x) c[o][x] += add;
-                        }
-                    }
+                    stage_c(rc, kt, c);
                     char *box = stg + s * (SP::kStgA + SP::kStgB);
                     mbar_arrive_expect_tx(&sfull[s], d.tma_bytes);
                     if (d.tma[0]) tma_load_5d(box, &tmA, &sfull[s], c[0]);
@@ -863,7 +938,9 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             const int64_t lt = BATCH ? tile - P.tile0 : tile;
             const int nch_t = BATCH ? 1 : nch;
             float *__restrict__ C = P.C;
-            const int64_t m0 = (lt % P.tiles_m) * kBM, n0 = (lt / P.tiles_m) * BN;
+            int64_t mt;
+            const int64_t nt = divmod(lt, P.tiles_m, mt);
+            const int64_t m0 = mt * kBM, n0 = nt * BN;
             int64_t *cn = cN + (it & 1) * BN;
             // one stride across the tile's columns: no column table
             const int64_t nval = min((int64_t)BN, P.N - n0);
@@ -873,7 +950,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             } else if (P.n_chain) {
                 lin = P.n_sC[0];
                 on0 = n0 * lin;
-            } else if ((n0 % P.n_ext[0]) + BN <= P.n_ext[0]) {
+            } else if ([&] { int64_t rr; divmod(n0, P.n_ext[0], rr); return rr + BN <= P.n_ext[0]; }()) {
                 int64_t ob = 0;
                 decode(n0, P.nn, P.n_ext, P.n_sB, P.n_sC, ob, on0);
                 lin = P.n_sC[0];
