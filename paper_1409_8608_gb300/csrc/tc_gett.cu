@@ -58,6 +58,7 @@ constexpr int kBM = 128;                  // accumulator rows = TMEM lanes
 constexpr int kBK = 32;                   // K elements per stage, global-load path
 constexpr int kBKT = 16;                  // K elements per stage, TMA path
 constexpr int64_t kCompChunkK = 256;      // default K chunk of the compensated split-BF16 form
+constexpr int kConvGroups = 2;            // converter groups taking turns (TMA-staged operands)
 constexpr int kEpiWarps = 4;              // warps 0-3
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kProducerWarps = 8;         // warps 4-11
@@ -628,7 +629,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     if (threadIdx.x == 0) {
         // one arrival per converter warp that converts a stage: all eight,
         // or the four of one group when the groups take turns
-        const uint32_t conv_warps = grouped ? kProducerThreads / 64 : kProducerThreads / 32;
+        const uint32_t conv_warps = grouped ? kProducerThreads / 32 / kConvGroups : kProducerThreads / 32;
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], conv_warps);
             mbar_init(&empty[s], 1);
@@ -658,10 +659,15 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         int it = 0;
         bool stop = false;
         if (grouped) {
-            const int gp = pt >> 7, ptg = pt & 127;  // group of 128 threads, rank within it
+            constexpr int kGT = kProducerThreads / kConvGroups;  // threads per group
+            // a group starts stage g once it has finished g - kConvGroups; the
+            // parity waits on a slot's barriers stay unambiguous only while
+            // both rings have at least kConvGroups slots
+            static_assert(!TMA || (STAGES >= kConvGroups && SSTG >= kConvGroups), "ring depth vs groups");
+            const int gp = pt / kGT, ptg = pt % kGT;
             for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x) {
                 for (int kt = 0; kt < nkt; ++kt, ++g) {
-                    if ((int)(g & 1) != gp) continue;  // the other group's stage
+                    if ((int)(g % kConvGroups) != gp) continue;  // another group's stage
                     const int s = (int)(g % STAGES);
                     const uint32_t ph = (uint32_t)((g / STAGES) & 1);
                     const int ss = (int)(g % SS);
@@ -671,8 +677,12 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                     bool bad = false;
                     if (!e_ok) bad = !mbar_wait(&empty[s], ph ^ 1u);
                     if (!f_ok && !bad) bad = !mbar_wait(&sfull[ss], sph);
-                    const bool quit = gp == 0 ? role_sync_or<1, 128>(bad || *abort_flag)
-                                              : role_sync_or<3, 128>(bad || *abort_flag);
+                    // named barriers 1, 3, 4, 5 (0: the whole CTA, 2: the epilogue)
+                    bool quit;
+                    if (gp == 0) quit = role_sync_or<1, kGT>(bad || *abort_flag);
+                    else if (gp == 1) quit = role_sync_or<3, kGT>(bad || *abort_flag);
+                    else if (gp == 2) quit = role_sync_or<4, kGT>(bad || *abort_flag);
+                    else quit = role_sync_or<5, kGT>(bad || *abort_flag);
                     if (quit) {
                         if (ptg == 0) {
                             *abort_flag = 1;
@@ -683,8 +693,8 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                     }
                     char *stage = ops + s * SP::kStage;
                     const char *box = stg + ss * (SP::kStgA + SP::kStgB);
-                    convert_staged<KIND, BK, kBM, 128>(box, d.srow[0], d.sk[0], d.sk_vec4[0], stage, SP::kATile, ptg);
-                    convert_staged<KIND, BK, BN, 128>(box + SP::kStgA, d.srow[1], d.sk[1], d.sk_vec4[1],
+                    convert_staged<KIND, BK, kBM, kGT>(box, d.srow[0], d.sk[0], d.sk_vec4[0], stage, SP::kATile, ptg);
+                    convert_staged<KIND, BK, BN, kGT>(box + SP::kStgA, d.srow[1], d.sk[1], d.sk_vec4[1],
                                                       stage + T::kSlices * SP::kATile, SP::kBTile, ptg);
                     fence_proxy_async_smem();
                     __syncwarp();
