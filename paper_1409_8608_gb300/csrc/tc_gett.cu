@@ -57,6 +57,8 @@ enum GettKind { GK_BF16X3 = 0, GK_BF16 = 1, GK_F16 = 2, GK_TF32 = 3 };
 constexpr int kBM = 128;                  // accumulator rows = TMEM lanes
 constexpr int kBK = 32;                   // K elements per stage, global-load path
 constexpr int kBKT = 16;                  // K elements per stage, TMA path
+constexpr int kBoxK = 32;                 // most K positions one TMA box covers (two stages)
+constexpr int64_t kTwoStageBoxMinK = 128; // shorter K keeps one-stage boxes (finer refill of the ring)
 constexpr int64_t kCompChunkK = 256;      // default K chunk of the compensated split-BF16 form
 constexpr int kConvGroups = 2;            // converter groups taking turns (TMA-staged operands)
 constexpr int kEpiWarps = 4;              // warps 0-3
@@ -96,9 +98,10 @@ struct GettDesc {
     int k_dim[2][kMaxModes];
     int64_t k_mul[2][kMaxModes];
     int srow[2];
-    int sk[2][kBKT];
+    int sk[2][kBoxK];
     int sk_vec4[2];
-    uint32_t tma_bytes;  // staged bytes per stage (both operands)
+    uint32_t tma_bytes;  // staged bytes per box (both operands)
+    int spb;             // K stages per TMA box: 1 (16 K positions) or 2 (32)
     double tile_frac;    // micro-benchmark: run this fraction of the tiles
     int chunk_stages;    // compensated form: K stages per TMEM chunk
     // batched form: per-problem descriptors (num_tiles, status, nprod,
@@ -331,19 +334,21 @@ struct KindTraits {
 template <int KIND, int BN, int STAGES, int BK, int SSTG>
 struct SmemPlan {
     static constexpr bool TMA = SSTG > 0;
-    static constexpr int kSstg = SSTG > 0 ? SSTG : 1;         // barrier slots
+    static constexpr int kSstg = SSTG > 0 ? SSTG : 1;         // slots of two-stage boxes
     using T = KindTraits<KIND, BK>;
     static constexpr int kATile = kBM * BK * T::kElemBytes;    // one slice
     static constexpr int kBTile = BN * BK * T::kElemBytes;
     static constexpr int kStage = T::kSlices * (kATile + kBTile);
     static constexpr int kOpBytes = STAGES * kStage;
-    static constexpr int kStgA = TMA ? kBM * BK * T::kInBytes : 0;  // staged input box
-    static constexpr int kStgB = TMA ? BN * BK * T::kInBytes : 0;
+    // staged input boxes cover up to kBoxK K positions (two stages)
+    static constexpr int kStgA = TMA ? kBM * kBoxK * T::kInBytes : 0;
+    static constexpr int kStgB = TMA ? BN * kBoxK * T::kInBytes : 0;
     static constexpr int kStgBytes = SSTG * (kStgA + kStgB);
     static constexpr int kKTab = STAGES * BK * 8 * 2;
     static constexpr int kRowTab = 2 * (kBM + BN) * 8;          // converters, double-buffered
     static constexpr int kColTab = 2 * BN * 8;                  // epilogue, double-buffered
-    static constexpr int kBars = (2 * STAGES + 2 * kSstg + 5) * 8 + 16;
+    // with one-stage boxes the staging ring holds twice as many slots
+    static constexpr int kBars = (2 * STAGES + 4 * kSstg + 5) * 8 + 16;
     static constexpr int kTotal = kOpBytes + kStgBytes + kKTab + kRowTab + kColTab + kBars;
 };
 
@@ -605,8 +610,8 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     uint64_t *full = (uint64_t *)(cN + 2 * BN);               // operand stage filled
     uint64_t *empty = full + STAGES;                          // operand stage consumed
     uint64_t *sfull = empty + STAGES;                         // staged box landed
-    uint64_t *sempty = sfull + SS;                            // staged box converted
-    uint64_t *tfull = sempty + SS;                            // [2]
+    uint64_t *sempty = sfull + 2 * SS;                        // staged box converted
+    uint64_t *tfull = sempty + 2 * SS;                        // [2]
     uint64_t *tempty = tfull + 2;                             // [2]
     uint64_t *drain = tempty + 2;
     uint32_t *tmem_slot = (uint32_t *)(drain + 1);
@@ -625,6 +630,11 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     // of four that take alternate stages, so one group's waits and barrier
     // overlap the other's conversion
     const bool grouped = TMA && !BATCH && d.tma[0] && d.tma[1];
+    // staging ring geometry: SS slots of two-stage boxes, or 2 * SS slots of
+    // one-stage boxes (the same bytes)
+    const int spb_r = d.spb > 1 ? d.spb : 1;
+    const int NSL = spb_r == 1 ? 2 * SS : SS;
+    const int boxA = spb_r == 1 ? SP::kStgA / 2 : SP::kStgA, boxB = spb_r == 1 ? SP::kStgB / 2 : SP::kStgB;
 
     if (threadIdx.x == 0) {
         // one arrival per converter warp that converts a stage: all eight,
@@ -634,9 +644,11 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             mbar_init(&full[s], conv_warps);
             mbar_init(&empty[s], 1);
         }
-        for (int s = 0; s < SS; ++s) {
+        // a staging slot is free again once every stage of its box is converted
+        const int spb = d.spb > 1 ? d.spb : 1;
+        for (int s = 0; s < NSL; ++s) {
             mbar_init(&sfull[s], 1);
-            mbar_init(&sempty[s], conv_warps);
+            mbar_init(&sempty[s], conv_warps * spb);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
@@ -658,6 +670,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         int64_t g = 0;
         int it = 0;
         bool stop = false;
+        const int spb_c = d.spb > 1 ? d.spb : 1;  // stages per staged box
         if (grouped) {
             constexpr int kGT = kProducerThreads / kConvGroups;  // threads per group
             // a group starts stage g once it has finished g - kConvGroups; the
@@ -670,8 +683,10 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                     if ((int)(g % kConvGroups) != gp) continue;  // another group's stage
                     const int s = (int)(g % STAGES);
                     const uint32_t ph = (uint32_t)((g / STAGES) & 1);
-                    const int ss = (int)(g % SS);
-                    const uint32_t sph = (uint32_t)((g / SS) & 1);
+                    const int64_t gb = g / spb_c;  // the TMA box of this stage
+                    const int half = (int)(g - gb * spb_c);
+                    const int ss = (int)(gb % NSL);
+                    const uint32_t sph = (uint32_t)((gb / NSL) & 1);
                     const bool e_ok = g < STAGES || mbar_try_wait(&empty[s], ph ^ 1u);
                     const bool f_ok = mbar_try_wait(&sfull[ss], sph);
                     bool bad = false;
@@ -692,9 +707,10 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                         break;
                     }
                     char *stage = ops + s * SP::kStage;
-                    const char *box = stg + ss * (SP::kStgA + SP::kStgB);
-                    convert_staged<KIND, BK, kBM, kGT>(box, d.srow[0], d.sk[0], d.sk_vec4[0], stage, SP::kATile, ptg);
-                    convert_staged<KIND, BK, BN, kGT>(box + SP::kStgA, d.srow[1], d.sk[1], d.sk_vec4[1],
+                    const char *box = stg + ss * (boxA + boxB);
+                    convert_staged<KIND, BK, kBM, kGT>(box, d.srow[0], d.sk[0] + half * BK, d.sk_vec4[0], stage,
+                                                       SP::kATile, ptg);
+                    convert_staged<KIND, BK, BN, kGT>(box + boxA, d.srow[1], d.sk[1] + half * BK, d.sk_vec4[1],
                                                       stage + T::kSlices * SP::kATile, SP::kBTile, ptg);
                     fence_proxy_async_smem();
                     __syncwarp();
@@ -720,10 +736,12 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             for (int kt = 0; kt < nkt_t; ++kt, ++g) {
                 const int s = (int)(g % STAGES);
                 const uint32_t ph = (uint32_t)((g / STAGES) & 1);
-                const int ss = (int)(g % SS);
+                const int64_t gb = g / spb_c;  // the TMA box of this stage
+                const int half = (int)(g - gb * spb_c);
+                const int ss = (int)(gb % NSL);
                 // both barriers polled back to back (their latencies overlap);
                 // the bounded waits only when one is not complete yet
-                const uint32_t sph = (uint32_t)((g / SS) & 1);
+                const uint32_t sph = (uint32_t)((gb / NSL) & 1);
                 const bool e_ok = g < STAGES || mbar_try_wait(&empty[s], ph ^ 1u);
                 const bool f_ok = !any_tma || mbar_try_wait(&sfull[ss], sph);
                 bool bad = false;
@@ -786,14 +804,14 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                 char *stage = ops + s * SP::kStage;
                 char *bstage = stage + T::kSlices * SP::kATile;
                 if (TMA && d.tma[0]) {
-                    convert_staged<KIND, BK, kBM>(stg + ss * (SP::kStgA + SP::kStgB), d.srow[0], d.sk[0],
+                    convert_staged<KIND, BK, kBM>(stg + ss * (boxA + boxB), d.srow[0], d.sk[0] + half * BK,
                                                   d.sk_vec4[0], stage, SP::kATile, pt);
                 } else {
                     produce_any<KIND, BK, kBM>(Ap, rA, kA + s * BK, stage, SP::kATile, P.a_map, pt);
                 }
                 if (TMA && d.tma[1]) {
-                    convert_staged<KIND, BK, BN>(stg + ss * (SP::kStgA + SP::kStgB) + SP::kStgA, d.srow[1],
-                                                 d.sk[1], d.sk_vec4[1], bstage, SP::kBTile, pt);
+                    convert_staged<KIND, BK, BN>(stg + ss * (boxA + boxB) + boxA, d.srow[1],
+                                                 d.sk[1] + half * BK, d.sk_vec4[1], bstage, SP::kBTile, pt);
                 } else {
                     produce_any<KIND, BK, BN>(Bp, rB, kB + s * BK, bstage, SP::kBTile, P.b_map, pt);
                 }
@@ -857,20 +875,21 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                 }
             };
             int32_t rc[2][kTmaRank];
+            const int spb = d.spb > 1 ? d.spb : 1;  // g counts boxes here
             for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x) {
                 tile_rc(tile, rc);
-                for (int kt = 0; kt < nkt; ++kt, ++g) {
-                    const int s = (int)(g % SS);
-                    if (g >= SS && (*abort_flag || !mbar_wait(&sempty[s], (uint32_t)(((g / SS) - 1) & 1)))) {
+                for (int kt = 0; kt < nkt; kt += spb, ++g) {
+                    const int s = (int)(g % NSL);
+                    if (g >= NSL && (*abort_flag || !mbar_wait(&sempty[s], (uint32_t)(((g / NSL) - 1) & 1)))) {
                         stop = true;
                         break;
                     }
                     int32_t c[2][kTmaRank];
                     stage_c(rc, kt, c);
-                    char *box = stg + s * (SP::kStgA + SP::kStgB);
+                    char *box = stg + s * (boxA + boxB);
                     mbar_arrive_expect_tx(&sfull[s], d.tma_bytes);
                     if (d.tma[0]) tma_load_5d(box, &tmA, &sfull[s], c[0]);
-                    if (d.tma[1]) tma_load_5d(box + SP::kStgA, &tmB, &sfull[s], c[1]);
+                    if (d.tma[1]) tma_load_5d(box + boxA, &tmB, &sfull[s], c[1]);
                 }
             }
             if (stop) {
@@ -1100,22 +1119,22 @@ tc_status launch_kind(GettDesc &d, int bn, bool tma, bool comp, const CUtensorMa
     d.tiles_n = (d.N + bn - 1) / bn;
     d.num_tiles = d.tiles_m * d.tiles_n;
     if (d.tile_frac < 1.0) d.num_tiles = std::max<int64_t>(1, (int64_t)(d.num_tiles * d.tile_frac));
-    // <KIND, BN, operand stages, BK, staging stages (0 = no TMA)>
+    // <KIND, BN, operand stages, BK, staging slots (boxes of up to two stages; 0 = no TMA)>
     if constexpr (KIND == GK_BF16X3) {
         if (comp) {  // 128 x 128 tiles: two chunk accumulators and (hi, lo) fill the tensor memory
-            if (tma) return launch_gett<KIND, 128, 3, kBKT, 6, true>(d, ta, tb, st);
+            if (tma) return launch_gett<KIND, 128, 3, kBKT, 3, true>(d, ta, tb, st);
             return launch_gett<KIND, 128, 4, kBK, 0, true>(d, ta, tb, st);
         }
     }
     if (tma) {  // 16-K stages, staged input boxes
         if (bn == 128) {
-            if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 128, 3, kBKT, 6>(d, ta, tb, st);
-            else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 128, 4, kBKT, 8>(d, ta, tb, st);
-            else return launch_gett<KIND, 128, 6, kBKT, 12>(d, ta, tb, st);
+            if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 128, 3, kBKT, 3>(d, ta, tb, st);
+            else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 128, 4, kBKT, 4>(d, ta, tb, st);
+            else return launch_gett<KIND, 128, 6, kBKT, 8>(d, ta, tb, st);
         }
-        if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 256, 3, kBKT, 4>(d, ta, tb, st);
-        else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 256, 3, kBKT, 5>(d, ta, tb, st);
-        else return launch_gett<KIND, 256, 4, kBKT, 10>(d, ta, tb, st);
+        if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 256, 3, kBKT, 2>(d, ta, tb, st);
+        else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 256, 3, kBKT, 2>(d, ta, tb, st);
+        else return launch_gett<KIND, 256, 4, kBKT, 4>(d, ta, tb, st);
     }
     if (bn == 256) {
         if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 256, 2, kBK, 0>(d, ta, tb, st);
@@ -1191,7 +1210,7 @@ bool encoder() {
 // mode fastest; K modes as in the descriptor (outermost first).
 bool plan_tma_operand(const Plan &p, int opnd, const void *base, int in_bytes, int rows, int nrow,
                       const int64_t *row_ext, const int64_t *row_s, int nk, const int64_t *k_ext,
-                      const int64_t *k_s, GettDesc &d, CUtensorMap &map) {
+                      const int64_t *k_s, GettDesc &d, CUtensorMap &map, int kpb) {
     const int o = opnd == OP_A ? 0 : 1;
     if (((uintptr_t)base & 15) != 0 || nrow < 1) return false;
     if (row_ext[0] % rows != 0) return false;  // tiles must be boxes of the first row mode
@@ -1199,19 +1218,19 @@ bool plan_tma_operand(const Plan &p, int opnd, const void *base, int in_bytes, i
     int64_t cover = 1;
     std::vector<int64_t> kbox(nk, 1);
     int m = nk - 1;
-    for (; m >= 0 && cover < kBKT; --m) {
-        if (cover * k_ext[m] <= kBKT) {
+    for (; m >= 0 && cover < kpb; --m) {
+        if (cover * k_ext[m] <= kpb) {
             kbox[m] = k_ext[m];
             cover *= k_ext[m];
         } else {
-            if (k_ext[m] % (kBKT / cover) != 0 || kBKT % cover != 0) return false;
-            kbox[m] = kBKT / cover;
-            cover = kBKT;
+            if (k_ext[m] % (kpb / cover) != 0 || kpb % cover != 0) return false;
+            kbox[m] = kpb / cover;
+            cover = kpb;
         }
     }
     int64_t K = 1;
     for (int x = 0; x < nk; ++x) K *= k_ext[x];
-    if (cover != kBKT && cover != K) return false;
+    if (cover != kpb && cover != K) return false;
     // tensor dimensions: the operand's own modes (split K modes share one),
     // the stride-1 mode first
     struct Dim { int64_t ext, stride; int64_t box; };
@@ -1259,10 +1278,10 @@ bool plan_tma_operand(const Plan &p, int opnd, const void *base, int in_bytes, i
     std::vector<int64_t> bstride(dims.size(), 1);
     for (size_t x = 1; x < dims.size(); ++x) bstride[x] = bstride[x - 1] * dims[x - 1].box;
     int64_t box_elems = bstride.back() * dims.back().box;
-    if (box_elems != (int64_t)rows * kBKT && box_elems != (int64_t)rows * K) return false;
+    if (box_elems != (int64_t)rows * kpb && box_elems != (int64_t)rows * K) return false;
     d.srow[o] = (int)bstride[d.row_dim[o][0]];
     bool v4 = true;
-    for (int k = 0; k < kBKT; ++k) {
+    for (int k = 0; k < kpb; ++k) {
         int64_t kk = k, off = 0;
         bool valid = k < K;
         for (int x = nk - 1; x >= 0; --x) {
@@ -1276,7 +1295,7 @@ bool plan_tma_operand(const Plan &p, int opnd, const void *base, int in_bytes, i
     }
     if (d.srow[o] % 4 != 0 || in_bytes != 4) v4 = false;
     d.sk_vec4[o] = v4 ? 1 : 0;
-    if (K < kBKT) return false;  // zero-padded K positions would read staged data
+    if (K < kpb || K % kpb != 0) return false;  // every box covers kpb valid K positions
     // encode (rank 5: unused dimensions have extent 1)
     if (!encoder()) return false;
     cuuint64_t gdim[kTmaRank], gstride[kTmaRank - 1];
@@ -1405,11 +1424,34 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     std::memset(&tmA, 0, sizeof(tmA));
     std::memset(&tmB, 0, sizeof(tmB));
     bool tma = false;
+    d.spb = 1;
     if (p.gett_tma && d.K < (int64_t(1) << 31)) {  // 32-bit K positions in the TMA warp
-        d.tma[0] = plan_tma_operand(p, OP_A, A, in_bytes, kBM, d.nm, d.m_ext, d.m_sA, d.nk, d.k_ext, d.k_sA, d, tmA);
-        d.tma[1] = plan_tma_operand(p, OP_B, B, in_bytes, bn, d.nn, d.n_ext, d.n_sB, d.nk, d.k_ext, d.k_sB, d, tmB);
+        d.tma[0] = plan_tma_operand(p, OP_A, A, in_bytes, kBM, d.nm, d.m_ext, d.m_sA, d.nk, d.k_ext, d.k_sA, d, tmA,
+                                    kBKT);
+        d.tma[1] = plan_tma_operand(p, OP_B, B, in_bytes, bn, d.nn, d.n_ext, d.n_sB, d.nk, d.k_ext, d.k_sB, d, tmB,
+                                    kBKT);
         tma = d.tma[0] || d.tma[1];
-        d.tma_bytes = (uint32_t)((d.tma[0] ? kBM * kBKT * in_bytes : 0) + (d.tma[1] ? bn * kBKT * in_bytes : 0));
+        // boxes of two stages where the K modes allow them for the same
+        // operands: each TMA box costs a fixed few hundred cycles on top of
+        // its bytes, so fewer, larger boxes move more data per SM
+        if (tma && d.K % kBoxK == 0 && d.K >= kTwoStageBoxMinK) {
+            GettDesc d2 = d;
+            CUtensorMap a2, b2;
+            std::memset(&a2, 0, sizeof(a2));
+            std::memset(&b2, 0, sizeof(b2));
+            const bool ta = d.tma[0] && plan_tma_operand(p, OP_A, A, in_bytes, kBM, d.nm, d.m_ext, d.m_sA, d.nk,
+                                                         d.k_ext, d.k_sA, d2, a2, kBoxK);
+            const bool tb = d.tma[1] && plan_tma_operand(p, OP_B, B, in_bytes, bn, d.nn, d.n_ext, d.n_sB, d.nk,
+                                                         d.k_ext, d.k_sB, d2, b2, kBoxK);
+            if (ta == (bool)d.tma[0] && tb == (bool)d.tma[1]) {
+                d = d2;
+                tmA = a2;
+                tmB = b2;
+                d.spb = kBoxK / kBKT;
+            }
+        }
+        const int kpb = d.spb * kBKT;
+        d.tma_bytes = (uint32_t)((d.tma[0] ? kBM * kpb * in_bytes : 0) + (d.tma[1] ? bn * kpb * in_bytes : 0));
     }
     if (comp) d.chunk_stages = (int)(comp_k / (tma ? kBKT : kBK));
     // global-load mappings (used by operands without TMA staging)
