@@ -28,7 +28,8 @@
 //                        fills the other accumulator.
 //
 // Split-BF16 ("BF16X3"): each FP32 input x is split into three BF16 slices
-// x = h0 + h1 + h2 (h0 = rn(x), h1 = rn(x - h0), h2 = rn(x - h0 - h1)); the
+// x = h0 + h1 + h2 exactly (h0 = rn(x); h1 = x - h0 truncated to BF16;
+// h2 = the rest, itself a BF16 value: see split3x2); the
 // kept slice products are ordered by weight: 3 products keep (0,0) (0,1)
 // (1,0); 6 add (0,2) (1,1) (2,0); 9 add (1,2) (2,1) (2,2).
 //
@@ -377,18 +378,21 @@ __device__ __forceinline__ void decode(int64_t x, int n, const int64_t *ext, con
     }
 }
 
-// x = h0 + h1 + h2 for two values at once: cvt.rn.bf16x2 rounds a pair,
-// the widening back to FP32 is exact, so the remainders are exact.
+// x = h0 + h1 + h2 exactly, for two values at once.  h0 = RN_bf16(x) (one
+// cvt.rn.bf16x2 for the pair); the remainder r = x - h0 is exact and has at
+// most 16 significant bits (|r| <= 2^-9 |x|); h1 = r with its low 16 bits
+// cleared (truncation to BF16); r - h1 is exact with at most 8 significant
+// bits, so it is a BF16 value: h2.  The dropped slice products then stay
+// below about 2^-24 |a||b| per term.
 __device__ __forceinline__ void split3x2(float x0, float x1, uint32_t &w0, uint32_t &w1, uint32_t &w2) {
     __nv_bfloat162 h0 = __floats2bfloat162_rn(x0, x1);
-    float2 f0 = __bfloat1622float2(h0);
-    const float r0 = x0 - f0.x, r1 = x1 - f0.y;
-    __nv_bfloat162 h1 = __floats2bfloat162_rn(r0, r1);
-    float2 f1 = __bfloat1622float2(h1);
-    __nv_bfloat162 h2 = __floats2bfloat162_rn(r0 - f1.x, r1 - f1.y);
-    w0 = *(uint32_t *)&h0;
-    w1 = *(uint32_t *)&h1;
-    w2 = *(uint32_t *)&h2;
+    const uint32_t u0 = *(uint32_t *)&h0;  // x0 in the low half, x1 in the high half
+    const float r0 = x0 - __uint_as_float(u0 << 16), r1 = x1 - __uint_as_float(u0 & 0xFFFF0000u);
+    const uint32_t t0 = __float_as_uint(r0) & 0xFFFF0000u, t1 = __float_as_uint(r1) & 0xFFFF0000u;
+    const float q0 = r0 - __uint_as_float(t0), q1 = r1 - __uint_as_float(t1);
+    w0 = u0;
+    w1 = __byte_perm(t0, t1, 0x7632);  // the high halves of the two words
+    w2 = __byte_perm(__float_as_uint(q0), __float_as_uint(q1), 0x7632);
 }
 
 // Converts N (4 or 8) FP32 values into the 16-bit slices or TF32 words
