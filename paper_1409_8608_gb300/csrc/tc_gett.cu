@@ -7,17 +7,19 @@
 // The kernel is persistent (one CTA per SM walks the tile list, M tiles
 // fastest so that CTAs sharing a B tile run together) and warp-specialised:
 //
-//   TMA warp 13          streams each operand's stage box (tile rows x 16 K
-//                        positions, any permutation of the operand's modes,
-//                        described by a CUtensorMap over its own strides: no
-//                        transpose pass) into a staging ring with
-//                        cp.async.bulk.tensor and mbarrier transaction counts;
+//   TMA warp 13          streams each operand's box (tile rows x 16 or 32 K
+//                        positions, one or two K stages, any permutation of
+//                        the operand's modes, described by a CUtensorMap over
+//                        its own strides: no transpose pass) into a staging
+//                        ring with cp.async.bulk.tensor and mbarrier
+//                        transaction counts;
 //   converter warps 4-11 convert or split the staged inputs (or, for an
 //                        operand TMA cannot describe, load it straight from
 //                        global memory through its strides) and store the
 //                        canonical no-swizzle K-major core-matrix layout
 //                        (8 rows x 16 bytes per core matrix) in a ring of
-//                        operand stages;
+//                        16-K operand stages; with both operands staged they
+//                        work as two groups of four taking alternate stages;
 //   MMA warp 12          one elected thread issues tcgen05.mma (kind::f16 for
 //                        BF16/FP16 and the split-BF16 slices, kind::tf32) into
 //                        one of two FP32 accumulators in tensor memory, and
