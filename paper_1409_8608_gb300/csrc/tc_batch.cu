@@ -446,8 +446,12 @@ tc_status tc_batch_execute(tc_batch batch, const void *alpha, const void *beta, 
     b.last_stream = stream;
     if (b.dtype == TC_BF16X3) {
         const float a = *(const float *)alpha, be = *(const float *)beta;
+        int one_stage = 1;
+        for (const auto &P : b.probs)
+            if (P.K > 32) one_stage = 0;
         auto run = [&](int64_t t0, int64_t t1) {
-            return gett_launch_batch(b.ddescs, b.dtile_prob, t0, t1, b.bn, a, be, b.nprod, b.dstatus, stream);
+            return gett_launch_batch(b.ddescs, b.dtile_prob, t0, t1, b.bn, a, be, b.nprod, b.dstatus, one_stage,
+                                     stream);
         };
         if (one_launch_per_problem) {
             for (int slot = 0; slot < b.count; ++slot) {

@@ -114,6 +114,7 @@ struct GettDesc {
     const int32_t *tile_prob;
     int64_t tile0;
     int64_t tile_begin;  // first tile of this launch (batched form; else 0)
+    int one_stage;       // batched form: every problem's K fits one stage
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -334,7 +335,7 @@ struct KindTraits {
 // STAGES: depth of the operand ring (converted tiles the MMA reads);
 // SSTG: depth of the TMA staging ring (0 = no TMA staging).  The staging
 // ring is the deeper one: it covers the load latency.
-template <int KIND, int BN, int STAGES, int BK, int SSTG>
+template <int KIND, int BN, int STAGES, int BK, int SSTG, bool BATCH = false>
 struct SmemPlan {
     static constexpr bool TMA = SSTG > 0;
     static constexpr int kSstg = SSTG > 0 ? SSTG : 1;         // slots of two-stage boxes
@@ -347,12 +348,18 @@ struct SmemPlan {
     static constexpr int kStgA = TMA ? kBM * kBoxK * T::kInBytes : 0;
     static constexpr int kStgB = TMA ? BN * kBoxK * T::kInBytes : 0;
     static constexpr int kStgBytes = SSTG * (kStgA + kStgB);
-    static constexpr int kKTab = STAGES * BK * 8 * 2;
-    static constexpr int kRowTab = 2 * (kBM + BN) * 8;          // converters, double-buffered
+    // K-offset and row-offset tables of the global-load path: per stage slot
+    // (or, in the batched form, per converter group and double-buffered)
+    static constexpr int kKSlots = BATCH ? (STAGES > 4 ? STAGES : 4) : STAGES;
+    static constexpr int kRowBufs = BATCH ? 4 : 2;
+    static constexpr int kKTab = kKSlots * BK * 8 * 2;
+    static constexpr int kRowTab = kRowBufs * (kBM + BN) * 8;
+    // batched form: per-tile records the converters leave for the epilogue
+    static constexpr int kRecs = BATCH ? 8 : 0;
     static constexpr int kColTab = 2 * BN * 8;                  // epilogue, double-buffered
     // with one-stage boxes the staging ring holds twice as many slots
     static constexpr int kBars = (2 * STAGES + 4 * kSstg + 5) * 8 + 16;
-    static constexpr int kTotal = kOpBytes + kStgBytes + kKTab + kRowTab + kColTab + kBars;
+    static constexpr int kTotal = kOpBytes + kStgBytes + kKTab + kRowTab + kColTab + kRecs * 64 + kRecs * 16 + kBars;
 };
 
 // x = q * y + r for non-negative x, y > 0: 32-bit division when both fit
@@ -425,7 +432,7 @@ __device__ __forceinline__ void store_converted(const float (&x)[N], char *dst, 
 // MAP 2: 16-byte vector loads along K (contiguity and alignment checked on
 // the host); MAP 1: K chunks across lanes; MAP 0: rows across lanes.  Maps 0
 // and 1 load through the offset tables one element at a time (any strides).
-template <int KIND, int BK, int ROWS, int MAP>
+template <int KIND, int BK, int ROWS, int MAP, int NT = kProducerThreads>
 __device__ __forceinline__ void produce_operand(const typename KindTraits<KIND, BK>::In *__restrict__ src,
                                                 const int64_t *rowoff, const int64_t *koff, char *tile,
                                                 int slice_stride, int pt) {
@@ -434,19 +441,19 @@ __device__ __forceinline__ void produce_operand(const typename KindTraits<KIND, 
     constexpr bool kFloatIn = KIND == GK_BF16X3 || KIND == GK_TF32;
     if constexpr (MAP == 2) {
         constexpr int UPR = BK / T::kVec;  // 16-byte loads per row per stage
-        constexpr int NU = ROWS * UPR / kProducerThreads;
-        static_assert(NU * kProducerThreads == ROWS * UPR, "even split");
+        constexpr int NU = ROWS * UPR / NT;
+        static_assert(NU * NT == ROWS * UPR, "even split");
         uint4 v[NU];
 #pragma unroll
         for (int i = 0; i < NU; ++i) {
-            const int u = pt + i * kProducerThreads;
+            const int u = pt + i * NT;
             const int row = u / UPR, k = (u % UPR) * T::kVec;
             const int64_t ro = rowoff[row], ko = koff[k];
             v[i] = (ro >= 0 && ko >= 0) ? __ldg((const uint4 *)(src + ro + ko)) : make_uint4(0u, 0u, 0u, 0u);
         }
 #pragma unroll
         for (int i = 0; i < NU; ++i) {
-            const int u = pt + i * kProducerThreads;
+            const int u = pt + i * NT;
             const int row = u / UPR, k = (u % UPR) * T::kVec;
             const int kc = k / CH, byte = (k % CH) * T::kElemBytes;
             char *dst = tile + (kc * (ROWS / 8) + row / 8) * 128 + (row % 8) * 16 + byte;
@@ -459,14 +466,14 @@ __device__ __forceinline__ void produce_operand(const typename KindTraits<KIND, 
             }
         }
     } else {
-        constexpr int NC = ROWS * KC / kProducerThreads;
-        static_assert(NC * kProducerThreads == ROWS * KC, "even split");
+        constexpr int NC = ROWS * KC / NT;
+        static_assert(NC * NT == ROWS * KC, "even split");
         using L = typename std::conditional<kFloatIn, float, unsigned short>::type;
         const L *s = (const L *)src;
         L x[NC][CH];
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-            const int c = pt + i * kProducerThreads;
+            const int c = pt + i * NT;
             const int row = MAP == 1 ? c / KC : c % ROWS;
             const int kc = MAP == 1 ? c % KC : c / ROWS;
             const int64_t ro = rowoff[row];
@@ -478,7 +485,7 @@ __device__ __forceinline__ void produce_operand(const typename KindTraits<KIND, 
         }
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-            const int c = pt + i * kProducerThreads;
+            const int c = pt + i * NT;
             const int row = MAP == 1 ? c / KC : c % ROWS;
             const int kc = MAP == 1 ? c % KC : c / ROWS;
             char *dst = tile + (kc * (ROWS / 8) + row / 8) * 128 + (row % 8) * 16;
@@ -494,13 +501,13 @@ __device__ __forceinline__ void produce_operand(const typename KindTraits<KIND, 
     }
 }
 
-template <int KIND, int BK, int ROWS>
+template <int KIND, int BK, int ROWS, int NT = kProducerThreads>
 __device__ __forceinline__ void produce_any(const typename KindTraits<KIND, BK>::In *__restrict__ src,
                                             const int64_t *rowoff, const int64_t *koff, char *tile,
                                             int slice_stride, int map, int pt) {
-    if (map == 2) produce_operand<KIND, BK, ROWS, 2>(src, rowoff, koff, tile, slice_stride, pt);
-    else if (map == 1) produce_operand<KIND, BK, ROWS, 1>(src, rowoff, koff, tile, slice_stride, pt);
-    else produce_operand<KIND, BK, ROWS, 0>(src, rowoff, koff, tile, slice_stride, pt);
+    if (map == 2) produce_operand<KIND, BK, ROWS, 2, NT>(src, rowoff, koff, tile, slice_stride, pt);
+    else if (map == 1) produce_operand<KIND, BK, ROWS, 1, NT>(src, rowoff, koff, tile, slice_stride, pt);
+    else produce_operand<KIND, BK, ROWS, 0, NT>(src, rowoff, koff, tile, slice_stride, pt);
 }
 
 // TMA path: converts one operand's staged box (ROWS rows x BK K positions,
@@ -601,7 +608,7 @@ template <int KIND, int BN, int STAGES, int BK, int SSTG, bool COMP, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1)
 gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
     using T = KindTraits<KIND, BK>;
-    using SP = SmemPlan<KIND, BN, STAGES, BK, SSTG>;
+    using SP = SmemPlan<KIND, BN, STAGES, BK, SSTG, BATCH>;
     constexpr bool TMA = SP::TMA;
     constexpr int SS = SP::kSstg;
     using In = typename T::In;
@@ -609,11 +616,14 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     char *ops = smem;
     char *stg = smem + SP::kOpBytes;                          // [SSTG][A box | B box]
     int64_t *kA = (int64_t *)(stg + SP::kStgBytes);           // [STAGES][BK]
-    int64_t *kB = kA + STAGES * BK;
-    int64_t *rowA = kB + STAGES * BK;                         // [2][kBM]
-    int64_t *rowB = rowA + 2 * kBM;                           // [2][BN]
-    int64_t *cN = rowB + 2 * BN;                              // [2][BN]
-    uint64_t *full = (uint64_t *)(cN + 2 * BN);               // operand stage filled
+    int64_t *kB = kA + SP::kKSlots * BK;
+    int64_t *rowA = kB + SP::kKSlots * BK;                    // [kRowBufs][kBM]
+    int64_t *rowB = rowA + SP::kRowBufs * kBM;                // [kRowBufs][BN]
+    int64_t *cN = rowB + SP::kRowBufs * BN;                   // [2][BN]
+    int64_t *trec = cN + 2 * BN;                              // [kRecs][8] batched tile records
+    uint64_t *rfull = (uint64_t *)(trec + SP::kRecs * 8);     // [kRecs] record written
+    uint64_t *rempty = rfull + SP::kRecs;                     // [kRecs] record read
+    uint64_t *full = rempty + SP::kRecs;                      // operand stage filled
     uint64_t *empty = full + STAGES;                          // operand stage consumed
     uint64_t *sfull = empty + STAGES;                         // staged box landed
     uint64_t *sempty = sfull + 2 * SS;                        // staged box converted
@@ -635,7 +645,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     // both operands staged by TMA: the converter warps split into two groups
     // of four that take alternate stages, so one group's waits and barrier
     // overlap the other's conversion
-    const bool grouped = TMA && !BATCH && d.tma[0] && d.tma[1];
+    const bool grouped = (TMA && !BATCH && d.tma[0] && d.tma[1]) || (BATCH && d.one_stage);
     // staging ring geometry: SS slots of two-stage boxes, or 2 * SS slots of
     // one-stage boxes (the same bytes)
     const int spb_r = d.spb > 1 ? d.spb : 1;
@@ -660,6 +670,10 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], kEpiThreads / 32);  // one arrival per epilogue warp
         }
+        for (int r = 0; r < SP::kRecs; ++r) {
+            mbar_init(&rfull[r], 1);
+            mbar_init(&rempty[r], 1);
+        }
         mbar_init(drain, 1);
         *abort_flag = 0;
         fence_mbar_init();
@@ -677,7 +691,96 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         int it = 0;
         bool stop = false;
         const int spb_c = d.spb > 1 ? d.spb : 1;  // stages per staged box
-        if (grouped) {
+        if (BATCH && grouped) {
+            // batched form, one K stage per tile: the groups take alternate
+            // tiles, each with its own double-buffered offset tables, so one
+            // group's global-load latency overlaps the other's conversion
+            constexpr int kGT = kProducerThreads / kConvGroups;
+            static_assert(kConvGroups == 2, "table buffers per group");
+            const int gp = pt / kGT, ptg = pt % kGT;
+            int gi = 0;  // this group's tile count
+            for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x, ++g) {
+                if ((int)(g % kConvGroups) != gp) continue;
+                const GettDesc &P = tile_desc<BATCH>(d, tile);
+                const int64_t lt = tile - P.tile0;
+                int64_t mt;
+                const int64_t nt = divmod(lt, P.tiles_m, mt);
+                const int64_t m0 = mt * kBM, n0 = nt * BN;
+                const int s = (int)(g % STAGES);
+                const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+                const int bix = gp * 2 + (gi & 1);
+                ++gi;
+                int64_t *rA = rowA + bix * kBM, *rB = rowB + bix * BN;
+                int64_t *tA = kA + bix * BK, *tB = kB + bix * BK;
+                bool bad = g >= STAGES && !mbar_wait(&empty[s], ph ^ 1u);
+                for (int i = ptg; i < kBM; i += kGT) {
+                    int64_t mm = m0 + i, oa = -1, oc = 0;
+                    if (mm < P.M) {
+                        oa = 0;
+                        decode(mm, P.nm, P.m_ext, P.m_sA, P.m_sC, oa, oc);
+                    }
+                    rA[i] = oa;
+                }
+                for (int j = ptg; j < BN; j += kGT) {
+                    int64_t nn = n0 + j, ob = -1, oc = 0;
+                    if (nn < P.N) {
+                        ob = 0;
+                        decode(nn, P.nn, P.n_ext, P.n_sB, P.n_sC, ob, oc);
+                    }
+                    rB[j] = ob;
+                }
+                if (ptg < BK) {
+                    int64_t oa = -1, ob = -1;
+                    if (ptg < P.K) {  // one stage: the K position is the thread's
+                        oa = 0;
+                        ob = 0;
+                        int64_t k = ptg, v;
+                        for (int m = P.nk - 1; m >= 0; --m) {
+                            k = divmod(k, P.k_ext[m], v);
+                            oa += v * P.k_sA[m];
+                            ob += v * P.k_sB[m];
+                        }
+                    }
+                    tA[ptg] = oa;
+                    tB[ptg] = ob;
+                }
+                const bool quit = gp == 0 ? role_sync_or<1, kGT>(bad || *abort_flag)
+                                          : role_sync_or<3, kGT>(bad || *abort_flag);
+                if (quit) {
+                    if (ptg == 0) {
+                        *abort_flag = 1;
+                        atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
+                    }
+                    stop = true;
+                    break;
+                }
+                if (ptg == 0 && !stop) {
+                    // what the epilogue needs of this tile, so that it reads no
+                    // problem descriptor from global memory: a ring of records
+                    // with its own barriers (written here, read there)
+                    const int r = (int)(g % SP::kRecs);
+                    if (g >= SP::kRecs && !mbar_wait(&rempty[r], (uint32_t)(((g / SP::kRecs) - 1) & 1))) {
+                        *abort_flag = 1;
+                        atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
+                    }
+                    int64_t *rec = trec + r * 8;
+                    rec[0] = (int64_t)P.C;
+                    rec[1] = P.M - m0;                   // valid rows of the tile
+                    rec[2] = P.m_sC[0];
+                    rec[3] = P.n_sC[0];
+                    rec[4] = m0 * P.m_sC[0] + n0 * P.n_sC[0];
+                    rec[5] = min((int64_t)BN, P.N - n0);  // valid columns
+                    mbar_arrive(&rfull[r]);
+                }
+                char *stage = ops + s * SP::kStage;
+                produce_any<KIND, BK, kBM, kGT>((const In *)P.A, rA, tA, stage, SP::kATile, P.a_map, ptg);
+                produce_any<KIND, BK, BN, kGT>((const In *)P.B, rB, tB, stage + T::kSlices * SP::kATile,
+                                               SP::kBTile, P.b_map, ptg);
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[s]);
+            }
+        } else if (grouped) {
             constexpr int kGT = kProducerThreads / kConvGroups;  // threads per group
             // a group starts stage g once it has finished g - kConvGroups; the
             // parity waits on a slot's barriers stay unambiguous only while
@@ -969,46 +1072,63 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         int it = 0;
         int64_t u = 0;
         for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles; tile += gridDim.x, ++it) {
-            const GettDesc &P = tile_desc<BATCH>(d, tile);
-            const int64_t lt = BATCH ? tile - P.tile0 : tile;
             const int nch_t = BATCH ? 1 : nch;
-            float *__restrict__ C = P.C;
-            int64_t mt;
-            const int64_t nt = divmod(lt, P.tiles_m, mt);
-            const int64_t m0 = mt * kBM, n0 = nt * BN;
+            float *__restrict__ C;
             int64_t *cn = cN + (it & 1) * BN;
-            // one stride across the tile's columns: no column table
-            const int64_t nval = min((int64_t)BN, P.N - n0);
-            int64_t lin = 0, on0 = 0;
-            if (P.nn == 0) {
-                lin = 0;  // a single column: the table
-            } else if (P.n_chain) {
-                lin = P.n_sC[0];
-                on0 = n0 * lin;
-            } else if ([&] { int64_t rr; divmod(n0, P.n_ext[0], rr); return rr + BN <= P.n_ext[0]; }()) {
-                int64_t ob = 0;
-                decode(n0, P.nn, P.n_ext, P.n_sB, P.n_sC, ob, on0);
-                lin = P.n_sC[0];
-            }
-            if (lin == 0) {
-                for (int j = et; j < BN; j += kEpiThreads) {
-                    int64_t nn = n0 + j, ob = 0, oc = -1;
-                    if (nn < P.N) {
-                        oc = 0;
-                        decode(nn, P.nn, P.n_ext, P.n_sB, P.n_sC, ob, oc);
+            int64_t nval, lin = 0, on0 = 0, om = -1;
+            bool rec_ok = true;
+            if (BATCH && grouped) {
+                // the tile's record, left by the converters
+                const int r = it % SP::kRecs;
+                rec_ok = mbar_wait(&rfull[r], (uint32_t)((it / SP::kRecs) & 1));
+                const int64_t *rec = trec + r * 8;
+                C = (float *)rec[0];
+                nval = rec[5];
+                lin = rec[3];
+                om = et < rec[1] ? rec[4] + (int64_t)et * rec[2] : -1;
+            } else {
+                const GettDesc &P = tile_desc<BATCH>(d, tile);
+                const int64_t lt = BATCH ? tile - P.tile0 : tile;
+                C = P.C;
+                int64_t mt;
+                const int64_t nt = divmod(lt, P.tiles_m, mt);
+                const int64_t m0 = mt * kBM, n0 = nt * BN;
+                // one stride across the tile's columns: no column table
+                nval = min((int64_t)BN, P.N - n0);
+                if (P.nn == 0) {
+                    lin = 0;  // a single column: the table
+                } else if (P.n_chain) {
+                    lin = P.n_sC[0];
+                    on0 = n0 * lin;
+                } else if ([&] { int64_t rr; divmod(n0, P.n_ext[0], rr); return rr + BN <= P.n_ext[0]; }()) {
+                    int64_t ob = 0;
+                    decode(n0, P.nn, P.n_ext, P.n_sB, P.n_sC, ob, on0);
+                    lin = P.n_sC[0];
+                }
+                if (lin == 0) {
+                    for (int j = et; j < BN; j += kEpiThreads) {
+                        int64_t nn = n0 + j, ob = 0, oc = -1;
+                        if (nn < P.N) {
+                            oc = 0;
+                            decode(nn, P.nn, P.n_ext, P.n_sB, P.n_sC, ob, oc);
+                        }
+                        cn[j] = oc;
                     }
-                    cn[j] = oc;
+                }
+                {
+                    int64_t mm = m0 + et, oa = 0;
+                    if (mm < P.M) {
+                        om = 0;
+                        decode(mm, P.nm, P.m_ext, P.m_sA, P.m_sC, oa, om);
+                    }
                 }
             }
-            int64_t om = -1;
-            {
-                int64_t mm = m0 + et, oa = 0;
-                if (mm < P.M) {
-                    om = 0;
-                    decode(mm, P.nm, P.m_ext, P.m_sA, P.m_sC, oa, om);
-                }
+            if (!rec_ok) {
+                *abort_flag = 1;
+                atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
             }
             if (role_sync_or<2, kEpiThreads>(*abort_flag)) break;
+            if (BATCH && grouped && et == 0) mbar_arrive(&rempty[it % SP::kRecs]);  // record read by all
             const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
             bool aborted = false;
             for (int c = 0; c < nch_t; ++c, ++u) {
@@ -1099,7 +1219,7 @@ int g_gett_sms = 0;
 
 template <int KIND, int BN, int STAGES, int BK, int SSTG, bool COMP = false, bool BATCH = false>
 tc_status launch_gett(const GettDesc &d, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
-    using SP = SmemPlan<KIND, BN, STAGES, BK, SSTG>;
+    using SP = SmemPlan<KIND, BN, STAGES, BK, SSTG, BATCH>;
     static_assert(SP::kTotal <= 227 * 1024, "shared memory budget");
     // at least 116 KB so that one CTA (and one tensor-memory allocation of
     // up to 512 columns) occupies each SM
@@ -1528,7 +1648,7 @@ void gett_fill_batch_desc(const BatchProblem &P, int bn, void *out) {
 }
 
 tc_status gett_launch_batch(const void *ddescs, const int32_t *dtile_prob, int64_t t_begin, int64_t t_end, int bn,
-                            float alpha, float beta, int nprod, int *dstatus, void *stream) {
+                            float alpha, float beta, int nprod, int *dstatus, int one_stage, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     GettDesc d;
     std::memset(&d, 0, sizeof(d));
@@ -1542,6 +1662,7 @@ tc_status gett_launch_batch(const void *ddescs, const int32_t *dtile_prob, int64
     d.nprod = nprod;
     d.status = dstatus;
     d.tile_frac = 1.0;
+    d.one_stage = one_stage;
     CUtensorMap none;
     std::memset(&none, 0, sizeof(none));
     if (bn == 128) return launch_gett<GK_BF16X3, 128, 4, kBK, 0, false, true>(d, none, none, st);

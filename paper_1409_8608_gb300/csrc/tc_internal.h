@@ -123,8 +123,10 @@ struct BatchProblem {
 // 128 x bn tiles), then one launch over tiles [t_begin, t_end).
 size_t gett_desc_bytes();
 void gett_fill_batch_desc(const BatchProblem &P, int bn, void *out);
+// one_stage: every problem's K fits one 32-element stage (the converter
+// groups then take alternate tiles).
 tc_status gett_launch_batch(const void *ddescs, const int32_t *dtile_prob, int64_t t_begin, int64_t t_end, int bn,
-                            float alpha, float beta, int nprod, int *dstatus, void *stream);
+                            float alpha, float beta, int nprod, int *dstatus, int one_stage, void *stream);
 
 }  // namespace tc
 
