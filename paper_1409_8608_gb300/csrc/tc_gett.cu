@@ -699,12 +699,27 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             static_assert(kConvGroups == 2, "table buffers per group");
             const int gp = pt / kGT, ptg = pt % kGT;
             int gi = 0;  // this group's tile count
-            for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x, ++g) {
-                if ((int)(g % kConvGroups) != gp) continue;
-                const GettDesc &P = tile_desc<BATCH>(d, tile);
-                const int64_t lt = tile - P.tile0;
+            // every batched problem is a strided GEMM (one M, N and K mode):
+            // its fields are read with independent loads, and the problem
+            // index of the group's next tile is fetched one tile ahead
+            int64_t tile = d.tile_begin + blockIdx.x;
+            for (int k = 0; k < gp; ++k) tile += gridDim.x;  // this group's first tile
+            g = gp;
+            int32_t q = tile < d.num_tiles ? d.tile_prob[tile] : 0;
+            for (; tile < d.num_tiles && !stop; tile += (int64_t)kConvGroups * gridDim.x, g += kConvGroups) {
+                const int64_t next = tile + (int64_t)kConvGroups * gridDim.x;
+                const int32_t q_next = next < d.num_tiles ? d.tile_prob[next] : 0;
+                const GettDesc &P = d.probs[q];
+                const int64_t pM = P.M, pN = P.N, pK = P.K, ptm = P.tiles_m, pt0 = P.tile0;
+                const int64_t sAm = P.m_sA[0], sCm = P.m_sC[0], sBn = P.n_sB[0], sCn = P.n_sC[0];
+                const int64_t sAk = P.k_sA[0], sBk = P.k_sB[0];
+                const In *__restrict__ Ap = (const In *)P.A;
+                const In *__restrict__ Bp = (const In *)P.B;
+                float *const Cp = P.C;
+                const int amap = P.a_map, bmap = P.b_map;
+                q = q_next;
                 int64_t mt;
-                const int64_t nt = divmod(lt, P.tiles_m, mt);
+                const int64_t nt = divmod(tile - pt0, ptm, mt);
                 const int64_t m0 = mt * kBM, n0 = nt * BN;
                 const int s = (int)(g % STAGES);
                 const uint32_t ph = (uint32_t)((g / STAGES) & 1);
@@ -713,36 +728,11 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                 int64_t *rA = rowA + bix * kBM, *rB = rowB + bix * BN;
                 int64_t *tA = kA + bix * BK, *tB = kB + bix * BK;
                 bool bad = g >= STAGES && !mbar_wait(&empty[s], ph ^ 1u);
-                for (int i = ptg; i < kBM; i += kGT) {
-                    int64_t mm = m0 + i, oa = -1, oc = 0;
-                    if (mm < P.M) {
-                        oa = 0;
-                        decode(mm, P.nm, P.m_ext, P.m_sA, P.m_sC, oa, oc);
-                    }
-                    rA[i] = oa;
-                }
-                for (int j = ptg; j < BN; j += kGT) {
-                    int64_t nn = n0 + j, ob = -1, oc = 0;
-                    if (nn < P.N) {
-                        ob = 0;
-                        decode(nn, P.nn, P.n_ext, P.n_sB, P.n_sC, ob, oc);
-                    }
-                    rB[j] = ob;
-                }
-                if (ptg < BK) {
-                    int64_t oa = -1, ob = -1;
-                    if (ptg < P.K) {  // one stage: the K position is the thread's
-                        oa = 0;
-                        ob = 0;
-                        int64_t k = ptg, v;
-                        for (int m = P.nk - 1; m >= 0; --m) {
-                            k = divmod(k, P.k_ext[m], v);
-                            oa += v * P.k_sA[m];
-                            ob += v * P.k_sB[m];
-                        }
-                    }
-                    tA[ptg] = oa;
-                    tB[ptg] = ob;
+                for (int i = ptg; i < kBM; i += kGT) rA[i] = m0 + i < pM ? (m0 + i) * sAm : -1;
+                for (int j = ptg; j < BN; j += kGT) rB[j] = n0 + j < pN ? (n0 + j) * sBn : -1;
+                if (ptg < BK) {  // one stage: the K position is the thread's
+                    tA[ptg] = ptg < pK ? ptg * sAk : -1;
+                    tB[ptg] = ptg < pK ? ptg * sBk : -1;
                 }
                 const bool quit = gp == 0 ? role_sync_or<1, kGT>(bad || *abort_flag)
                                           : role_sync_or<3, kGT>(bad || *abort_flag);
@@ -764,18 +754,17 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                         atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
                     }
                     int64_t *rec = trec + r * 8;
-                    rec[0] = (int64_t)P.C;
-                    rec[1] = P.M - m0;                   // valid rows of the tile
-                    rec[2] = P.m_sC[0];
-                    rec[3] = P.n_sC[0];
-                    rec[4] = m0 * P.m_sC[0] + n0 * P.n_sC[0];
-                    rec[5] = min((int64_t)BN, P.N - n0);  // valid columns
+                    rec[0] = (int64_t)Cp;
+                    rec[1] = pM - m0;                   // valid rows of the tile
+                    rec[2] = sCm;
+                    rec[3] = sCn;
+                    rec[4] = m0 * sCm + n0 * sCn;
+                    rec[5] = min((int64_t)BN, pN - n0);  // valid columns
                     mbar_arrive(&rfull[r]);
                 }
                 char *stage = ops + s * SP::kStage;
-                produce_any<KIND, BK, kBM, kGT>((const In *)P.A, rA, tA, stage, SP::kATile, P.a_map, ptg);
-                produce_any<KIND, BK, BN, kGT>((const In *)P.B, rB, tB, stage + T::kSlices * SP::kATile,
-                                               SP::kBTile, P.b_map, ptg);
+                produce_any<KIND, BK, kBM, kGT>(Ap, rA, tA, stage, SP::kATile, amap, ptg);
+                produce_any<KIND, BK, BN, kGT>(Bp, rB, tB, stage + T::kSlices * SP::kATile, SP::kBTile, bmap, ptg);
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&full[s]);
