@@ -1486,16 +1486,28 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
         for (int id : ki)
             if (id != inner && p.op[small].stride_of(id) == 1) other = id;
         const int64_t ein = p.ext[inner];
-        if (other >= 0 && p.op[big].stride_of(inner) == 1 && ein % vec == 0 && ein > vec &&
+        // Where K allows two-stage (32-position) TMA boxes, the larger input
+        // keeps 32-byte runs (8 FP32 values) and the other input 16-byte runs
+        // of its own index: that costs the fewest box rows per K position.
+        // (The K order does not depend on the input path, so every path sums
+        // in the same order.)
+        int64_t ktot = 1;
+        for (int id : ki) ktot *= p.ext[id];
+        const int vsplit = (other >= 0 && in_bytes == 4 && ktot % kBoxK == 0 &&
+                            ktot >= kTwoStageBoxMinK && ein % (2 * vec) == 0 && ein > 2 * vec &&
+                            p.ext[other] % vec == 0)
+                               ? 2 * vec
+                               : vec;
+        if (other >= 0 && p.op[big].stride_of(inner) == 1 && ein % vsplit == 0 && ein > vsplit &&
             p.op[small].stride_of(inner) != 1) {
             std::vector<KMode> km;
             for (int id : ki)
                 if (id != inner && id != other)
                     km.push_back({p.ext[id], p.op[OP_A].stride_of(id), p.op[OP_B].stride_of(id)});
             const int64_t sAi = p.op[OP_A].stride_of(inner), sBi = p.op[OP_B].stride_of(inner);
-            km.push_back({ein / vec, sAi * vec, sBi * vec});
+            km.push_back({ein / vsplit, sAi * vsplit, sBi * vsplit});
             km.push_back({p.ext[other], p.op[OP_A].stride_of(other), p.op[OP_B].stride_of(other)});
-            km.push_back({(int64_t)vec, sAi, sBi});
+            km.push_back({(int64_t)vsplit, sAi, sBi});
             kmodes = km;
         }
     }
@@ -1546,23 +1558,26 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
         d.tma[1] = plan_tma_operand(p, OP_B, B, in_bytes, bn, d.nn, d.n_ext, d.n_sB, d.nk, d.k_ext, d.k_sB, d, tmB,
                                     kBKT);
         tma = d.tma[0] || d.tma[1];
-        // boxes of two stages where the K modes allow them for the same
-        // operands: each TMA box costs a fixed few hundred cycles on top of
-        // its bytes, so fewer, larger boxes move more data per SM
-        if (tma && d.K % kBoxK == 0 && d.K >= kTwoStageBoxMinK) {
+        // boxes of two stages where the K modes allow them for at least as
+        // many operands: each TMA box costs a fixed few hundred cycles on top
+        // of its bytes, so fewer, larger boxes move more data per SM
+        if (d.K % kBoxK == 0 && d.K >= kTwoStageBoxMinK) {
             GettDesc d2 = d;
             CUtensorMap a2, b2;
             std::memset(&a2, 0, sizeof(a2));
             std::memset(&b2, 0, sizeof(b2));
-            const bool ta = d.tma[0] && plan_tma_operand(p, OP_A, A, in_bytes, kBM, d.nm, d.m_ext, d.m_sA, d.nk,
-                                                         d.k_ext, d.k_sA, d2, a2, kBoxK);
-            const bool tb = d.tma[1] && plan_tma_operand(p, OP_B, B, in_bytes, bn, d.nn, d.n_ext, d.n_sB, d.nk,
-                                                         d.k_ext, d.k_sB, d2, b2, kBoxK);
-            if (ta == (bool)d.tma[0] && tb == (bool)d.tma[1]) {
+            const bool ta = plan_tma_operand(p, OP_A, A, in_bytes, kBM, d.nm, d.m_ext, d.m_sA, d.nk, d.k_ext,
+                                             d.k_sA, d2, a2, kBoxK);
+            const bool tb = plan_tma_operand(p, OP_B, B, in_bytes, bn, d.nn, d.n_ext, d.n_sB, d.nk, d.k_ext,
+                                             d.k_sB, d2, b2, kBoxK);
+            if ((ta || tb) && (int)ta + (int)tb >= (int)(bool)d.tma[0] + (int)(bool)d.tma[1]) {
                 d = d2;
+                d.tma[0] = ta;
+                d.tma[1] = tb;
                 tmA = a2;
                 tmB = b2;
                 d.spb = kBoxK / kBKT;
+                tma = true;
             }
         }
         const int kpb = d.spb * kBKT;
