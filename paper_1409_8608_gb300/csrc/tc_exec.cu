@@ -162,10 +162,20 @@ template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 tile_kernel(const TileDesc d) {
     constexpr int TX = BN / TN, TY = BM / TM, NT = TX * TY;
-    __shared__ T As[BK][BM];
-    __shared__ T Bs[BK][BN];
+    // A thread owns rows ty*V + r + g*TY*V (r < V, g < TM/V) and likewise
+    // columns: with V = 4 for FP32 each group is one 16-byte shared-memory
+    // read, so a K step issues TM/4 + TN/4 loads for TM*TN FMAs instead of
+    // TM + TN; FP64 (V = 1) is bound by the DFMA rate either way.
+    constexpr int V = (sizeof(T) == 4 && TM % 4 == 0 && TN % 4 == 0) ? 4 : 1;
+    auto row_of = [](int ty_, int i) { return (i / V) * (TY * V) + ty_ * V + i % V; };
+    auto col_of = [](int tx_, int j) { return (j / V) * (TX * V) + tx_ * V + j % V; };
+    // two stage buffers; rows padded by 4 elements so that the K-contiguous
+    // store mapping below spreads a warp over all 32 banks
+    constexpr int PAD = 4;
+    __shared__ __align__(16) T As[2][BK][BM + PAD];
+    __shared__ __align__(16) T Bs[2][BK][BN + PAD];
     __shared__ int64_t offAm[BM], offCm[BM], offBn[BN], offCn[BN];
-    __shared__ int64_t kA[BK], kB[BK];
+    __shared__ int64_t kA[2][BK], kB[2][BK];
     const T *__restrict__ A = (const T *)d.A;
     const T *__restrict__ B = (const T *)d.B;
     T *__restrict__ C = (T *)d.C;
@@ -223,10 +233,10 @@ tile_kernel(const TileDesc d) {
     T acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-        const int64_t om = offCm[ty + i * TY];
+        const int64_t om = offCm[row_of(ty, i)];
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
-            const int64_t on = offCn[tx + j * TX];
+            const int64_t on = offCn[col_of(tx, j)];
             T v = T(0);
             if (d.init != 2 && om >= 0 && on >= 0) {
                 v = C[om + on];
@@ -236,7 +246,8 @@ tile_kernel(const TileDesc d) {
         }
     }
 
-    for (int64_t k0 = 0; k0 < d.K; k0 += BK) {
+    // K offsets of a stage into table buffer b (threads kk < BK)
+    auto k_tables = [&](int64_t k0, int b) {
         for (int kk = tid; kk < BK; kk += NT) {
             int64_t k = k0 + kk;
             int64_t oa = -1, ob = -1;
@@ -250,51 +261,122 @@ tile_kernel(const TileDesc d) {
                     ob += x * d.red.sB[m];
                 }
             }
-            kA[kk] = oa;
-            kB[kk] = ob;
+            kA[b][kk] = oa;
+            kB[b][kk] = ob;
         }
-        __syncthreads();
-        for (int e = tid; e < BM * BK; e += NT) {
+    };
+    // Element e of a stage's R x BK operand tile: with M (N) contiguous in
+    // memory, consecutive threads take consecutive rows; otherwise groups
+    // of 8 threads take 8 consecutive K positions of one row (32-byte runs
+    // in memory; with the padded rows a warp's stores hit 32 distinct banks).
+    static_assert(BK % 8 == 0, "K stage is a multiple of 8");
+    auto place = [](int e, bool rfast, int R, int &r, int &kk) {
+        if (rfast) {
+            r = e % R;
+            kk = e / R;
+        } else {
+            r = (e / 8) % R;
+            kk = (e / (8 * R)) * 8 + e % 8;
+        }
+    };
+    // a stage's A and B elements of this thread, into registers
+    constexpr int LA = BM * BK / NT, LB = BN * BK / NT;
+    static_assert(LA * NT == BM * BK && LB * NT == BN * BK, "even split");
+    T ra[LA], rb[LB];
+    auto load_stage = [&](int b) {
+#pragma unroll
+        for (int l = 0; l < LA; ++l) {
             int i, kk;
-            if (d.a_m_fast) { i = e % BM; kk = e / BM; }
-            else { kk = e % BK; i = e / BK; }
-            const int64_t om = offAm[i], ok = kA[kk];
+            place(tid + l * NT, d.a_m_fast, BM, i, kk);
+            const int64_t om = offAm[i], ok = kA[b][kk];
             T v = T(0);
             if (om >= 0 && ok >= 0) {
                 v = A[om + ok];
                 if (!d.alpha_one) v = alpha * v;
             }
-            As[kk][i] = v;
+            ra[l] = v;
         }
-        for (int e = tid; e < BN * BK; e += NT) {
+#pragma unroll
+        for (int l = 0; l < LB; ++l) {
             int j, kk;
-            if (d.b_n_fast) { j = e % BN; kk = e / BN; }
-            else { kk = e % BK; j = e / BK; }
-            const int64_t on = offBn[j], ok = kB[kk];
-            Bs[kk][j] = (on >= 0 && ok >= 0) ? B[on + ok] : T(0);
+            place(tid + l * NT, d.b_n_fast, BN, j, kk);
+            const int64_t on = offBn[j], ok = kB[b][kk];
+            rb[l] = (on >= 0 && ok >= 0) ? B[on + ok] : T(0);
         }
-        __syncthreads();
+    };
+    auto store_stage = [&](int sb) {
+#pragma unroll
+        for (int l = 0; l < LA; ++l) {
+            int i, kk;
+            place(tid + l * NT, d.a_m_fast, BM, i, kk);
+            As[sb][kk][i] = ra[l];
+        }
+#pragma unroll
+        for (int l = 0; l < LB; ++l) {
+            int j, kk;
+            place(tid + l * NT, d.b_n_fast, BN, j, kk);
+            Bs[sb][kk][j] = rb[l];
+        }
+    };
+    // Stage s sits in buffer s & 1 (shared memory and K tables alike).
+    // While stage s is multiplied, stage s + 1's global loads are in flight
+    // and then stored to the other buffer, whose last reader (stage s - 1)
+    // finished before the barrier that ended the previous iteration; one
+    // barrier per stage.
+    k_tables(0, 0);
+    __syncthreads();
+    load_stage(0);
+    store_stage(0);
+    if (BK < d.K) k_tables(BK, 1);
+    __syncthreads();
+    int sb = 0;
+    for (int64_t k0 = 0; k0 < d.K; k0 += BK, sb ^= 1) {
+        const bool more = k0 + BK < d.K;
+        if (more) load_stage(sb ^ 1);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
             T a[TM], b[TN];
+            if constexpr (V == 4) {
 #pragma unroll
-            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * TY];
+                for (int g = 0; g < TM / 4; ++g) {
+                    const float4 v = *reinterpret_cast<const float4 *>(&As[sb][kk][row_of(ty, 4 * g)]);
+                    a[4 * g] = v.x;
+                    a[4 * g + 1] = v.y;
+                    a[4 * g + 2] = v.z;
+                    a[4 * g + 3] = v.w;
+                }
 #pragma unroll
-            for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + j * TX];
+                for (int g = 0; g < TN / 4; ++g) {
+                    const float4 v = *reinterpret_cast<const float4 *>(&Bs[sb][kk][col_of(tx, 4 * g)]);
+                    b[4 * g] = v.x;
+                    b[4 * g + 1] = v.y;
+                    b[4 * g + 2] = v.z;
+                    b[4 * g + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < TM; ++i) a[i] = As[sb][kk][row_of(ty, i)];
+#pragma unroll
+                for (int j = 0; j < TN; ++j) b[j] = Bs[sb][kk][col_of(tx, j)];
+            }
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
                 for (int j = 0; j < TN; ++j) acc[i][j] = fma_t<T>(a[i], b[j], acc[i][j]);
+        }
+        if (more) {
+            store_stage(sb ^ 1);
+            if (k0 + 2 * BK < d.K) k_tables(k0 + 2 * BK, sb);
         }
         __syncthreads();
     }
 
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-        const int64_t om = offCm[ty + i * TY];
+        const int64_t om = offCm[row_of(ty, i)];
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
-            const int64_t on = offCn[tx + j * TX];
+            const int64_t on = offCn[col_of(tx, j)];
             if (om >= 0 && on >= 0) C[om + on] = acc[i][j];
         }
     }
@@ -560,7 +642,7 @@ tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *
             td.B = Beff;
             td.C = Cptr;
             td.init = init;
-            if (sizeof(T) == 8) {
+            if constexpr (sizeof(T) == 8) {
                 constexpr int BM = 64, BN = 64;
                 td.tiles_m = (td.M + BM - 1) / BM;
                 td.tiles_n = (td.N + BN - 1) / BN;
@@ -571,7 +653,7 @@ tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *
                 td.tiles_m = (td.M + BM - 1) / BM;
                 td.tiles_n = (td.N + BN - 1) / BN;
                 int64_t grid = cut(td.tiles_m * td.tiles_n * ntasks);
-                tile_kernel<T, 128, 128, 8, 8, 8><<<(unsigned)grid, 256, 0, st>>>(td);
+                tile_kernel<T, 128, 128, 16, 8, 8><<<(unsigned)grid, 256, 0, st>>>(td);
             }
         } else {
             PhaseDesc q = pd;
@@ -667,14 +749,14 @@ tc_status run_gett_simt(Plan &p, T alpha, const T *A, const T *B, T beta, T *C,
     auto cut = [&](int64_t n) {
         return !probe || probe->fraction >= 1.0 ? n : std::max<int64_t>(1, (int64_t)(n * probe->fraction));
     };
-    if (sizeof(T) == 8) {
+    if constexpr (sizeof(T) == 8) {
         td.tiles_m = (td.M + 63) / 64;
         td.tiles_n = (td.N + 63) / 64;
         tile_kernel<T, 64, 64, 16, 4, 4><<<(unsigned)cut(td.tiles_m * td.tiles_n), 256, 0, st>>>(td);
     } else {
         td.tiles_m = (td.M + 127) / 128;
         td.tiles_n = (td.N + 127) / 128;
-        tile_kernel<T, 128, 128, 8, 8, 8><<<(unsigned)cut(td.tiles_m * td.tiles_n), 256, 0, st>>>(td);
+        tile_kernel<T, 128, 128, 16, 8, 8><<<(unsigned)cut(td.tiles_m * td.tiles_n), 256, 0, st>>>(td);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? TC_SUCCESS
