@@ -141,9 +141,13 @@ tc_status tc_plan_select(tc_plan plan, int32_t alg_id);
 /* The currently selected algorithm id. */
 tc_status tc_plan_selected(tc_plan plan, int32_t *alg_id);
 
-/* Bytes of device workspace the algorithm needs (copy buffers).  The plan
- * allocates it on the first tc_execute of that algorithm and keeps it until
- * tc_plan_destroy; call tc_execute once before capturing a CUDA graph. */
+/* Bytes of device workspace the algorithm needs (copy buffers; for GETT,
+ * id 0, the pre-converted input of tc_plan_set_gett_pack, else 0).  The
+ * plan allocates it on the first tc_execute of that algorithm and keeps it
+ * until tc_plan_destroy; call tc_execute once before capturing a CUDA
+ * graph.  Executes of one plan whose work overlaps on the GPU (several
+ * streams) share this workspace and race on it: give each stream its own
+ * plan. */
 tc_status tc_algorithm_workspace(tc_plan plan, int32_t alg_id, size_t *bytes);
 
 /* C = alpha * A.B + beta * C with the selected algorithm, enqueued on
@@ -190,6 +194,22 @@ tc_status tc_plan_set_gett_tile(tc_plan plan, int32_t width);
  * ring; 0 loads every operand with ordinary global loads.  Results are the
  * same either way. */
 tc_status tc_plan_set_gett_tma(tc_plan plan, int32_t enable);
+
+/* Tensor-core GETT, FP32 inputs (TC_BF16X3, TC_TF32): pre-conversion of the
+ * smaller input.  With it, a pre-pass kernel writes that input once into
+ * the plan's workspace as the converted shared-memory images of its tiles
+ * (split-BF16 slices or TF32 words in the MMA's core-matrix layout, zeros
+ * past the extents), and the GETT copies them with 16-byte asynchronous
+ * copies instead of loading and converting the input per tile; the K order
+ * then follows the larger input alone.  mode 0: never; 1 (default): when
+ * the smaller input has at most 1/8 of the larger one's elements and its
+ * images fit in 64 MiB; 2: whenever its images fit in 64 MiB.  Other values
+ * give TC_ERROR_INVALID_ARGUMENT.  The workspace is allocated by the first
+ * execute that needs it (tc_algorithm_workspace(plan, 0) bounds it).  The
+ * K order, and so the rounding of the sums, depends on this setting but not
+ * on tc_plan_set_gett_tma: both input paths give the same bits.  With
+ * pre-conversion an execute launches two kernels (pre-pass, GETT). */
+tc_status tc_plan_set_gett_pack(tc_plan plan, int32_t mode);
 
 /* Failure-detection self-test (no paper counterpart).  Launches one CTA on
  * `stream` whose thread 0 waits on an mbarrier with the bounded wait every

@@ -64,6 +64,8 @@ constexpr int kBoxK = 32;                 // most K positions one TMA box covers
 constexpr int64_t kTwoStageBoxMinK = 128; // shorter K keeps one-stage boxes (finer refill of the ring)
 constexpr int64_t kCompChunkK = 256;      // default K chunk of the compensated split-BF16 form
 constexpr int kConvGroups = 2;            // converter groups taking turns (TMA-staged operands)
+constexpr int64_t kPackMaxBytes = int64_t(64) << 20;  // largest pre-converted input
+constexpr int kPackRatio = 8;             // auto: the smaller input has <= 1/8 the elements
 constexpr int kEpiWarps = 4;              // warps 0-3
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kProducerWarps = 8;         // warps 4-11
@@ -115,6 +117,12 @@ struct GettDesc {
     int64_t tile0;
     int64_t tile_begin;  // first tile of this launch (batched form; else 0)
     int one_stage;       // batched form: every problem's K fits one stage
+    // pre-converted input (0 none, 1 A, 2 B): its stage images, laid out
+    // [row tile][K stage][slice][core-matrix image] as the converters would
+    // write them to shared memory
+    int pk;
+    const char *pk_base;
+    int64_t pk_tile_bytes;  // one row tile's images (every K stage)
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -184,6 +192,13 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, u
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+
+// 16-byte asynchronous global -> shared copy (completes at cp_async_wait_all)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -557,6 +572,19 @@ __device__ __forceinline__ void convert_staged(const char *stg, int srow, const 
     }
 }
 
+// Pre-converted input: one stage image (BYTES, contiguous) copied to the
+// stage with 16-byte asynchronous copies shared by NT threads; the caller
+// waits with cp_async_wait_all before publishing the stage.
+template <int BYTES, int NT>
+__device__ __forceinline__ void copy_packed(const char *src, char *dst, int pt) {
+    static_assert(BYTES % (16 * NT) == 0, "even split");
+#pragma unroll
+    for (int i = 0; i < BYTES / (16 * NT); ++i) {
+        const int u = (pt + i * NT) * 16;
+        cp_async16(dst + u, src + u);
+    }
+}
+
 // The descriptor of a tile's problem: the launch's own, or in the batched
 // form the one its tile-to-problem table names.
 template <bool BATCH>
@@ -642,15 +670,22 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     const int nch = (nkt + cstg - 1) / cstg;
     const bool any_tma = TMA && (d.tma[0] || d.tma[1]);
     const bool any_ldg = !TMA || !d.tma[0] || !d.tma[1];
-    // both operands staged by TMA: the converter warps split into two groups
-    // of four that take alternate stages, so one group's waits and barrier
-    // overlap the other's conversion
-    const bool grouped = (TMA && !BATCH && d.tma[0] && d.tma[1]) || (BATCH && d.one_stage);
+    // both operands staged by TMA (or one staged and the other
+    // pre-converted): the converter warps split into two groups of four that
+    // take alternate stages, so one group's waits and barrier overlap the
+    // other's conversion
+    const bool grouped = (TMA && !BATCH && any_tma && (d.tma[0] || d.pk == 1) && (d.tma[1] || d.pk == 2)) ||
+                         (BATCH && d.one_stage);
+    constexpr int kPkA = T::kSlices * SP::kATile, kPkB = T::kSlices * SP::kBTile;  // stage image bytes
     // staging ring geometry: SS slots of two-stage boxes, or 2 * SS slots of
     // one-stage boxes (the same bytes)
+    // A pre-converted input has no staged box: its share of the staging
+    // bytes holds further slots of the other input's boxes (up to the
+    // 2 * SS slots the barriers are laid out for).
     const int spb_r = d.spb > 1 ? d.spb : 1;
-    const int NSL = spb_r == 1 ? 2 * SS : SS;
-    const int boxA = spb_r == 1 ? SP::kStgA / 2 : SP::kStgA, boxB = spb_r == 1 ? SP::kStgB / 2 : SP::kStgB;
+    const int boxA = d.pk == 1 ? 0 : (spb_r == 1 ? SP::kStgA / 2 : SP::kStgA);
+    const int boxB = d.pk == 2 ? 0 : (spb_r == 1 ? SP::kStgB / 2 : SP::kStgB);
+    const int NSL = !TMA ? 2 * SS : min(2 * SS, SP::kStgBytes / (boxA + boxB));
 
     if (threadIdx.x == 0) {
         // one arrival per converter warp that converts a stage: all eight,
@@ -777,6 +812,12 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             static_assert(!TMA || (STAGES >= kConvGroups && SSTG >= kConvGroups), "ring depth vs groups");
             const int gp = pt / kGT, ptg = pt % kGT;
             for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x) {
+                const char *pkt = nullptr;  // this tile's pre-converted images
+                if (d.pk) {
+                    int64_t mt;
+                    const int64_t nt = divmod(tile, d.tiles_m, mt);
+                    pkt = d.pk_base + (d.pk == 1 ? mt : nt) * d.pk_tile_bytes;
+                }
                 for (int kt = 0; kt < nkt; ++kt, ++g) {
                     if ((int)(g % kConvGroups) != gp) continue;  // another group's stage
                     const int s = (int)(g % STAGES);
@@ -806,10 +847,17 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                     }
                     char *stage = ops + s * SP::kStage;
                     const char *box = stg + ss * (boxA + boxB);
-                    convert_staged<KIND, BK, kBM, kGT>(box, d.srow[0], d.sk[0] + half * BK, d.sk_vec4[0], stage,
-                                                       SP::kATile, ptg);
-                    convert_staged<KIND, BK, BN, kGT>(box + boxA, d.srow[1], d.sk[1] + half * BK, d.sk_vec4[1],
-                                                      stage + T::kSlices * SP::kATile, SP::kBTile, ptg);
+                    // a pre-converted input's copies go first: they complete
+                    // while the other input is converted
+                    if (d.pk == 1) copy_packed<kPkA, kGT>(pkt + kt * kPkA, stage, ptg);
+                    else if (d.pk == 2) copy_packed<kPkB, kGT>(pkt + kt * kPkB, stage + kPkA, ptg);
+                    if (d.pk != 1)
+                        convert_staged<KIND, BK, kBM, kGT>(box, d.srow[0], d.sk[0] + half * BK, d.sk_vec4[0], stage,
+                                                           SP::kATile, ptg);
+                    if (d.pk != 2)
+                        convert_staged<KIND, BK, BN, kGT>(box + boxA, d.srow[1], d.sk[1] + half * BK, d.sk_vec4[1],
+                                                          stage + kPkA, SP::kBTile, ptg);
+                    if (d.pk) cp_async_wait_all();
                     fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) {
@@ -901,18 +949,29 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                 }
                 char *stage = ops + s * SP::kStage;
                 char *bstage = stage + T::kSlices * SP::kATile;
-                if (TMA && d.tma[0]) {
-                    convert_staged<KIND, BK, kBM>(stg + ss * (boxA + boxB), d.srow[0], d.sk[0] + half * BK,
-                                                  d.sk_vec4[0], stage, SP::kATile, pt);
-                } else {
-                    produce_any<KIND, BK, kBM>(Ap, rA, kA + s * BK, stage, SP::kATile, P.a_map, pt);
+                // a pre-converted input (never in the batched form) is copied
+                // first: its copies complete while the other is produced
+                const int pk = BATCH ? 0 : d.pk;
+                if (pk) {
+                    const char *pkt = d.pk_base + (pk == 1 ? mt : nt) * d.pk_tile_bytes;
+                    if (pk == 1) copy_packed<kPkA, kProducerThreads>(pkt + kt * kPkA, stage, pt);
+                    else copy_packed<kPkB, kProducerThreads>(pkt + kt * kPkB, bstage, pt);
                 }
-                if (TMA && d.tma[1]) {
-                    convert_staged<KIND, BK, BN>(stg + ss * (boxA + boxB) + boxA, d.srow[1],
-                                                 d.sk[1] + half * BK, d.sk_vec4[1], bstage, SP::kBTile, pt);
-                } else {
-                    produce_any<KIND, BK, BN>(Bp, rB, kB + s * BK, bstage, SP::kBTile, P.b_map, pt);
+                if (pk != 1) {
+                    if (TMA && d.tma[0])
+                        convert_staged<KIND, BK, kBM>(stg + ss * (boxA + boxB), d.srow[0], d.sk[0] + half * BK,
+                                                      d.sk_vec4[0], stage, SP::kATile, pt);
+                    else
+                        produce_any<KIND, BK, kBM>(Ap, rA, kA + s * BK, stage, SP::kATile, P.a_map, pt);
                 }
+                if (pk != 2) {
+                    if (TMA && d.tma[1])
+                        convert_staged<KIND, BK, BN>(stg + ss * (boxA + boxB) + boxA, d.srow[1],
+                                                     d.sk[1] + half * BK, d.sk_vec4[1], bstage, SP::kBTile, pt);
+                    else
+                        produce_any<KIND, BK, BN>(Bp, rB, kB + s * BK, bstage, SP::kBTile, P.b_map, pt);
+                }
+                if (pk) cp_async_wait_all();
                 // each lane publishes its stores to the async proxy; the warp's
                 // lanes are ordered by __syncwarp and lane 0 arrives for all
                 fence_proxy_async_smem();
@@ -1203,6 +1262,60 @@ if constexpr (!COMP) {
     }
 }
 
+// Pre-conversion of one FP32 input (op 0 = A, 1 = B): for every row tile
+// (rows rows) and K stage (bk positions) the stage image the converter warps
+// would write to shared memory -- the split-BF16 slices or TF32 words in the
+// core-matrix layout, slice after slice -- with zeros for rows past the
+// extent and K positions past K.  One thread per 16-byte core-matrix row.
+template <int KIND>
+__global__ void __launch_bounds__(256) pack_kernel(const GettDesc d, int op, int rows, int bk, char *out) {
+    using T = KindTraits<KIND, kBKT>;  // chunk and element size do not depend on BK
+    constexpr int CH = T::kChunk;
+    const int kcn = bk / CH;
+    const int64_t nkt = (d.K + bk - 1) / bk;
+    const int64_t R = op == 0 ? d.M : d.N;
+    const int64_t total = (R + rows - 1) / rows * nkt * kcn * rows;
+    const float *__restrict__ src = (const float *)(op == 0 ? d.A : d.B);
+    const int nr = op == 0 ? d.nm : d.nn;
+    const int64_t *rext = op == 0 ? d.m_ext : d.n_ext;
+    const int64_t *rs = op == 0 ? d.m_sA : d.n_sB;
+    const int64_t *ks = op == 0 ? d.k_sA : d.k_sB;
+    const int slice = rows * bk * T::kElemBytes;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t q = c;  // rows fastest, then K chunks, K stages, row tiles
+        const int row = (int)(q % rows);
+        q /= rows;
+        const int kc = (int)(q % kcn);
+        q /= kcn;
+        const int64_t kt = q % nkt, rt = q / nkt;
+        int64_t r = rt * rows + row, ro = -1;
+        if (r < R) {
+            ro = 0;
+            for (int m = 0; m < nr; ++m) {  // first row mode fastest
+                ro += (r % rext[m]) * rs[m];
+                r /= rext[m];
+            }
+        }
+        float x[CH];
+#pragma unroll
+        for (int e = 0; e < CH; ++e) {
+            int64_t k = kt * bk + kc * CH + e;
+            x[e] = 0.0f;
+            if (ro >= 0 && k < d.K) {
+                int64_t ko = 0;
+                for (int m = d.nk - 1; m >= 0; --m) {  // innermost K mode fastest
+                    ko += (k % d.k_ext[m]) * ks[m];
+                    k /= d.k_ext[m];
+                }
+                x[e] = src[ro + ko];
+            }
+        }
+        char *dst = out + (rt * nkt + kt) * (int64_t)(T::kSlices * slice) + (kc * (rows / 8) + row / 8) * 128 +
+                    (row % 8) * 16;
+        store_converted<KIND, CH>(x, dst, slice);
+    }
+}
+
 // ------------------------------------------------------------------ host side
 int g_gett_sms = 0;
 
@@ -1247,8 +1360,10 @@ tc_status launch_kind(GettDesc &d, int bn, bool tma, bool comp, const CUtensorMa
             else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 128, 4, kBKT, 4>(d, ta, tb, st);
             else return launch_gett<KIND, 128, 6, kBKT, 8>(d, ta, tb, st);
         }
-        if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 256, 3, kBKT, 2>(d, ta, tb, st);
-        else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 256, 3, kBKT, 2>(d, ta, tb, st);
+        // two operand stages, three staging slots: the staging ring covers
+        // the box latency (3 slots beat 2 by 10-20 % on 512^3 i=j=16)
+        if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 256, 2, kBKT, 3>(d, ta, tb, st);
+        else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 256, 2, kBKT, 3>(d, ta, tb, st);
         else return launch_gett<KIND, 256, 4, kBKT, 4>(d, ta, tb, st);
     }
     if (bn == 256) {
@@ -1440,7 +1555,40 @@ bool plan_tma_operand(const Plan &p, int opnd, const void *base, int in_bytes, i
 
 }  // namespace
 
-size_t gett_workspace_bytes(const Plan &) { return 0; }
+// Pre-conversion choice for the tensor-core GETT (0 none, 1 A, 2 B: the
+// input with fewer elements) and a bound on its stage images' bytes.
+int pack_choice(const Plan &p, int64_t &bound) {
+    bound = 0;
+    if ((p.dtype != TC_BF16X3 && p.dtype != TC_TF32) || p.gett_pack == 0) return 0;
+    int64_t M = 1, N = 1, K = 1;
+    for (int id : p.freeA) M *= p.ext[id];
+    for (int id : p.freeB) N *= p.ext[id];
+    for (int id : p.contracted) K *= p.ext[id];
+    const bool a_small = M <= N;  // the same choice as the K order's "larger input"
+    const int64_t R = a_small ? M : N;
+    // auto: only where the two inputs are contiguous along different
+    // contracted indices (a K order then has to trade one input's TMA rows
+    // against the other's); elsewhere the small input streams well as it is
+    auto unit_index = [&](int o) {
+        for (int m = 0; m < p.op[o].n; ++m)
+            if (p.op[o].stride_of(p.op[o].idx[m]) == 1) return p.op[o].idx[m];
+        return -1;
+    };
+    const int us = unit_index(a_small ? OP_A : OP_B), ub = unit_index(a_small ? OP_B : OP_A);
+    const bool permuted = us >= 0 && p.cls[us] == CLS_CONTRACTED && us != ub;
+    // rows rounded up to a 256-row tile, K to a 32-position stage
+    const int64_t b = (R + 255) * (K + kBK - 1) * (p.dtype == TC_TF32 ? 4 : 6);
+    if (b > kPackMaxBytes) return 0;
+    if (p.gett_pack == 1 && (!permuted || (a_small ? M : N) * kPackRatio > (a_small ? N : M))) return 0;
+    bound = b;
+    return a_small ? 1 : 2;
+}
+
+size_t gett_workspace_bytes(const Plan &p) {
+    int64_t bound = 0;
+    pack_choice(p, bound);
+    return (size_t)bound;
+}
 
 void gett_release(Plan &) {}
 
@@ -1473,6 +1621,10 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     for (int m = 0; m < p.op[OP_A].n; ++m) sizeA *= p.ext[p.op[OP_A].idx[m]];
     for (int m = 0; m < p.op[OP_B].n; ++m) sizeB *= p.ext[p.op[OP_B].idx[m]];
     const int big = sizeB >= sizeA ? OP_B : OP_A, small = big == OP_B ? OP_A : OP_B;
+    // a pre-converted smaller input is read as stage images, so the K order
+    // follows the larger input alone
+    int64_t pk_bound = 0;
+    const int pk = pack_choice(p, pk_bound);
     std::vector<int> ki(p.contracted);
     std::stable_sort(ki.begin(), ki.end(), [&](int x, int y) {
         return p.op[big].stride_of(x) > p.op[big].stride_of(y);
@@ -1480,7 +1632,7 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     struct KMode { int64_t ext, sA, sB; };
     std::vector<KMode> kmodes;
     for (int id : ki) kmodes.push_back({p.ext[id], p.op[OP_A].stride_of(id), p.op[OP_B].stride_of(id)});
-    if (ki.size() >= 2) {
+    if (ki.size() >= 2 && !pk) {
         const int inner = ki.back();
         int other = -1;
         for (int id : ki)
@@ -1553,10 +1705,10 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     bool tma = false;
     d.spb = 1;
     if (p.gett_tma && d.K < (int64_t(1) << 31)) {  // 32-bit K positions in the TMA warp
-        d.tma[0] = plan_tma_operand(p, OP_A, A, in_bytes, kBM, d.nm, d.m_ext, d.m_sA, d.nk, d.k_ext, d.k_sA, d, tmA,
-                                    kBKT);
-        d.tma[1] = plan_tma_operand(p, OP_B, B, in_bytes, bn, d.nn, d.n_ext, d.n_sB, d.nk, d.k_ext, d.k_sB, d, tmB,
-                                    kBKT);
+        d.tma[0] = pk != 1 && plan_tma_operand(p, OP_A, A, in_bytes, kBM, d.nm, d.m_ext, d.m_sA, d.nk, d.k_ext,
+                                               d.k_sA, d, tmA, kBKT);
+        d.tma[1] = pk != 2 && plan_tma_operand(p, OP_B, B, in_bytes, bn, d.nn, d.n_ext, d.n_sB, d.nk, d.k_ext,
+                                               d.k_sB, d, tmB, kBKT);
         tma = d.tma[0] || d.tma[1];
         // boxes of two stages where the K modes allow them for at least as
         // many operands: each TMA box costs a fixed few hundred cycles on top
@@ -1566,10 +1718,10 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
             CUtensorMap a2, b2;
             std::memset(&a2, 0, sizeof(a2));
             std::memset(&b2, 0, sizeof(b2));
-            const bool ta = plan_tma_operand(p, OP_A, A, in_bytes, kBM, d.nm, d.m_ext, d.m_sA, d.nk, d.k_ext,
-                                             d.k_sA, d2, a2, kBoxK);
-            const bool tb = plan_tma_operand(p, OP_B, B, in_bytes, bn, d.nn, d.n_ext, d.n_sB, d.nk, d.k_ext,
-                                             d.k_sB, d2, b2, kBoxK);
+            const bool ta = pk != 1 && plan_tma_operand(p, OP_A, A, in_bytes, kBM, d.nm, d.m_ext, d.m_sA, d.nk,
+                                                        d.k_ext, d.k_sA, d2, a2, kBoxK);
+            const bool tb = pk != 2 && plan_tma_operand(p, OP_B, B, in_bytes, bn, d.nn, d.n_ext, d.n_sB, d.nk,
+                                                        d.k_ext, d.k_sB, d2, b2, kBoxK);
             if ((ta || tb) && (int)ta + (int)tb >= (int)(bool)d.tma[0] + (int)(bool)d.tma[1]) {
                 d = d2;
                 d.tma[0] = ta;
@@ -1605,6 +1757,27 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     d.tiles_m = (d.M + kBM - 1) / kBM;
     d.tile_frac = probe ? probe->fraction : 1.0;
     cudaStream_t st = (cudaStream_t)stream;
+    if (pk) {
+        // the smaller input's stage images, for the stage depth the launch uses
+        const int bkp = tma ? kBKT : kBK;
+        const int rows = pk == 1 ? kBM : bn;
+        const int64_t R = pk == 1 ? d.M : d.N;
+        const int64_t nktp = (d.K + bkp - 1) / bkp;
+        const int64_t stage_bytes = (int64_t)rows * bkp * (p.dtype == TC_TF32 ? 4 : 6);
+        const int64_t bytes = (R + rows - 1) / rows * nktp * stage_bytes;
+        // bytes <= pk_bound: rows round up by less than 256, K by less than 32
+        s = ensure_device_resources(p, (size_t)pk_bound);
+        if (s != TC_SUCCESS) return s;
+        d.pk = pk;
+        d.pk_base = (const char *)p.workspace;
+        d.pk_tile_bytes = nktp * stage_bytes;
+        const int64_t chunks = bytes / 16 / (p.dtype == TC_TF32 ? 1 : 3);  // one per 16-byte row of slice 0
+        const unsigned grid = (unsigned)std::min<int64_t>((chunks + 255) / 256, 152 * 8);
+        if (p.dtype == TC_TF32) pack_kernel<GK_TF32><<<grid, 256, 0, st>>>(d, pk - 1, rows, bkp, (char *)p.workspace);
+        else pack_kernel<GK_BF16X3><<<grid, 256, 0, st>>>(d, pk - 1, rows, bkp, (char *)p.workspace);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+    }
     switch (p.dtype) {
     case TC_BF16X3: return launch_kind<GK_BF16X3>(d, bn, tma, comp, tmA, tmB, st);
     case TC_BF16: return launch_kind<GK_BF16>(d, bn, tma, comp, tmA, tmB, st);

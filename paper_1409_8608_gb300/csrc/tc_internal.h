@@ -59,6 +59,7 @@ struct Plan {
     int split_products = 6;         // TC_BF16X3: 3, 6 or 9 slice products
     int gett_bn = 0;                // tensor-core GETT tile width (0: by N)
     int gett_tma = 1;               // tensor-core GETT: TMA staging where legal
+    int gett_pack = 1;              // tensor-core GETT: pre-convert the small input (0 never, 1 auto, 2 always)
     int comp_chunk = -1;            // TC_BF16X3: compensated K chunk (-1 default, 0 off)
     // device resources, created lazily by the first execute
     int device = -1;

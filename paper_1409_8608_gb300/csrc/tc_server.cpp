@@ -263,7 +263,11 @@ struct ServerImpl {
             if (it == plans.end()) {
                 tc_plan p = nullptr;
                 tc_status s = tc_plan_create(&p, r->spec.c_str(), r->extents.data(), nullptr, r->dtype);
+                // one cached plan serves requests on several streams at once:
+                // no plan workspace (the GETT's pre-converted input) to share
+                if (s == TC_SUCCESS) s = tc_plan_set_gett_pack(p, 0);
                 if (s != TC_SUCCESS) {
+                    if (p) tc_plan_destroy(p);
                     finish(r, s);
                     continue;
                 }

@@ -84,6 +84,7 @@ SIGNATURES = {
     "tc_plan_set_split": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_plan_set_gett_tile": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_plan_set_gett_tma": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "tc_plan_set_gett_pack": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_plan_set_compensation": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _VP]),
     "tc_access_distances": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _I64P]),
@@ -245,6 +246,10 @@ def tc_plan_set_gett_tile(plan, width):
 
 def tc_plan_set_gett_tma(plan, enable):
     _check(load().tc_plan_set_gett_tma(plan, int(enable)), "tc_plan_set_gett_tma")
+
+
+def tc_plan_set_gett_pack(plan, mode):
+    _check(load().tc_plan_set_gett_pack(plan, int(mode)), "tc_plan_set_gett_pack")
 
 
 def tc_selftest_bounded_wait(limit_ns, signal, stream=None):
@@ -458,6 +463,9 @@ class Plan:
 
     def set_gett_tma(self, enable):
         tc_plan_set_gett_tma(self.handle, enable)
+
+    def set_gett_pack(self, mode):
+        tc_plan_set_gett_pack(self.handle, mode)
 
     def set_compensation(self, chunk):
         tc_plan_set_compensation(self.handle, chunk)

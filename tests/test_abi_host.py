@@ -131,6 +131,12 @@ def test_plan_option_validation(lib):
         plan.set_gett_tile(64)
     with pytest.raises(tc.TcError):
         plan.set_gett_tma(2)
+    for mode in (0, 1, 2):
+        plan.set_gett_pack(mode)
+    for mode in (-1, 3):
+        with pytest.raises(tc.TcError) as e:
+            plan.set_gett_pack(mode)
+        assert tc.STATUS_NAMES[e.value.status] == "TC_ERROR_INVALID_ARGUMENT"
     plan.close()
 
 
@@ -138,3 +144,23 @@ def test_selftest_rejects_bad_limits(lib):
     for limit in (0, -5, 20_000_000_000):
         st = tc.tc_selftest_bounded_wait(limit, 0)
         assert tc.STATUS_NAMES[st] == "TC_ERROR_INVALID_ARGUMENT"
+
+
+def test_gett_pack_choice(lib):
+    # automatic pre-conversion only where the inputs are contiguous along
+    # different contracted indices and one is much smaller; mode 2 forces
+    # it for the FP32-input tensor forms, mode 0 turns it off
+    cases = [("abc=iaj,jbic", [512, 512, 512, 16, 16], True),
+             ("abc=ai,ibc", [512, 512, 512, 64], False),
+             ("ab=aij,jib", [256, 256, 16, 16], False),
+             ("abc=iaj,jbic", [512, 512, 4, 16, 16], False)]   # A not 8x smaller
+    for spec, ext, auto in cases:
+        for dtype in ("bf16x3", "tf32", "bf16", "f32"):
+            plan = tc.Plan(spec, ext, dtype=dtype)
+            float_in = dtype in ("bf16x3", "tf32")
+            assert (plan.workspace(0) > 0) == (auto and float_in), (spec, ext, dtype)
+            plan.set_gett_pack(2)
+            assert (plan.workspace(0) > 0) == float_in, (spec, ext, dtype)
+            plan.set_gett_pack(0)
+            assert plan.workspace(0) == 0
+            plan.close()

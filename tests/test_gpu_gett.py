@@ -345,3 +345,59 @@ def test_gett_degenerate_extents(tcmod, spec, ext, dtype):
     A, B, _ = synth.integer_operands(spec, ext, seed=14)
     dA, dB, _ = device_inputs(dtype, A, B)
     assert np.array_equal(run_gett(tcmod, spec, ext, dtype, dA, dB), oc.contract(spec, ext, A, B))
+
+
+# Pre-converted smaller input (tc_plan_set_gett_pack): the GETT reads the
+# small input's split-BF16 / TF32 stage images written by a pre-pass, and
+# the K order follows the larger input.  Both input paths of the larger
+# input must give the same bits, and every mode stays within the bound.
+PACK_CASES = [
+    ("abc=iaj,jbic", [256, 512, 3, 16, 16]),  # A packed; B keeps 64-byte rows of j
+    ("abc=aic,ib", [200, 100, 48, 72]),       # B packed, N = 100 < one tile, K = 72 (stage tail)
+    ("ab=aij,jib", [300, 40, 24, 12]),        # B packed, K = 288: compensated chunks for BF16X3
+]
+
+
+@pytest.mark.parametrize("dtype", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("spec,ext", PACK_CASES)
+def test_pack_modes_within_bound_and_paths_bitwise(tcmod, spec, ext, dtype):
+    A, B, _ = synth.uniform_operands(spec, ext, seed=12)
+    dA, dB, (Ar, Br) = device_inputs(dtype, A, B)
+    want = oc.contract(spec, ext, Ar, Br)
+    scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
+    n = synth.dense_sizes(spec, ext)[0]
+    K = ksize(spec, ext)
+    bound = (6 * K + 4) * U32 if dtype == "bf16x3" else (K + 1) * U32 / (1 - (K + 1) * U32)
+    outs = {}
+    for pack, tma in ((0, 1), (2, 1), (2, 0)):
+        plan = tcmod.Plan(spec, ext, dtype=dtype)
+        plan.set_gett_pack(pack)
+        plan.set_gett_tma(tma)
+        if pack:
+            assert plan.workspace(0) > 0
+        dC = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda:0")
+        for _ in range(2):  # the second execute reuses the workspace
+            plan.execute(dA, dB, dC)
+        torch.cuda.synchronize()
+        plan.device_status()
+        plan.close()
+        outs[(pack, tma)] = dC.double().cpu().numpy()
+        err = float(np.max(np.abs(outs[(pack, tma)] - want) / scale))
+        assert err <= bound, (pack, tma, err, bound)
+    assert np.array_equal(outs[(2, 1)], outs[(2, 0)])
+
+
+@pytest.mark.parametrize("spec,ext", PACK_CASES)
+def test_pack_integers_exact(tcmod, spec, ext):
+    A, B, C0 = synth.integer_operands(spec, ext, seed=13, with_c=True)
+    S = oc.contract(spec, ext, A, B)
+    for dtype in ("bf16x3", "tf32"):
+        dA, dB, _ = device_inputs(dtype, A, B)
+        plan = tcmod.Plan(spec, ext, dtype=dtype)
+        plan.set_gett_pack(2)
+        dC = torch.from_numpy(C0).float().to("cuda:0")
+        plan.execute(dA, dB, dC, alpha=2.0, beta=0.5)
+        torch.cuda.synchronize()
+        plan.device_status()
+        plan.close()
+        assert np.array_equal(dC.double().cpu().numpy(), 2.0 * S + 0.5 * C0), dtype
