@@ -652,6 +652,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     uint64_t *rfull = (uint64_t *)(trec + SP::kRecs * 8);     // [kRecs] record written
     uint64_t *rempty = rfull + SP::kRecs;                     // [kRecs] record read
     uint64_t *full = rempty + SP::kRecs;                      // operand stage filled
+    constexpr int kRecMod = SP::kRecs > 0 ? SP::kRecs : 1;    // record ring index (batched form only)
     uint64_t *empty = full + STAGES;                          // operand stage consumed
     uint64_t *sfull = empty + STAGES;                         // staged box landed
     uint64_t *sempty = sfull + 2 * SS;                        // staged box converted
@@ -722,6 +723,11 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     if (warp >= kEpiWarps && warp < kMmaWarp) {
         // ---------------------------------------------------------- converters
         const int pt = threadIdx.x - kEpiThreads;
+        // with a pre-converted input the kernel is launched as a programmatic
+        // dependent of the pre-pass: its other roles start at once (the TMA
+        // warp streams the other input), the converters wait here until the
+        // pre-pass grid has completed and its stores are visible
+        if (!BATCH && d.pk) asm volatile("griddepcontrol.wait;" ::: "memory");
         int64_t g = 0;
         int it = 0;
         bool stop = false;
@@ -783,8 +789,8 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                     // what the epilogue needs of this tile, so that it reads no
                     // problem descriptor from global memory: a ring of records
                     // with its own barriers (written here, read there)
-                    const int r = (int)(g % SP::kRecs);
-                    if (g >= SP::kRecs && !mbar_wait(&rempty[r], (uint32_t)(((g / SP::kRecs) - 1) & 1))) {
+                    const int r = (int)(g % kRecMod);
+                    if (g >= kRecMod && !mbar_wait(&rempty[r], (uint32_t)(((g / kRecMod) - 1) & 1))) {
                         *abort_flag = 1;
                         atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
                     }
@@ -1127,8 +1133,8 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             bool rec_ok = true;
             if (BATCH && grouped) {
                 // the tile's record, left by the converters
-                const int r = it % SP::kRecs;
-                rec_ok = mbar_wait(&rfull[r], (uint32_t)((it / SP::kRecs) & 1));
+                const int r = it % kRecMod;
+                rec_ok = mbar_wait(&rfull[r], (uint32_t)((it / kRecMod) & 1));
                 const int64_t *rec = trec + r * 8;
                 C = (float *)rec[0];
                 nval = rec[5];
@@ -1176,7 +1182,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                 atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
             }
             if (role_sync_or<2, kEpiThreads>(*abort_flag)) break;
-            if (BATCH && grouped && et == 0) mbar_arrive(&rempty[it % SP::kRecs]);  // record read by all
+            if (BATCH && grouped && et == 0) mbar_arrive(&rempty[it % kRecMod]);  // record read by all
             const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
             bool aborted = false;
             for (int c = 0; c < nch_t; ++c, ++u) {
@@ -1268,13 +1274,16 @@ if constexpr (!COMP) {
 // core-matrix layout, slice after slice -- with zeros for rows past the
 // extent and K positions past K.  One thread per 16-byte core-matrix row.
 template <int KIND>
-__global__ void __launch_bounds__(256) pack_kernel(const GettDesc d, int op, int rows, int bk, char *out) {
+__global__ void __launch_bounds__(128) pack_kernel(const GettDesc d, int op, int rows, int bk, char *out) {
     using T = KindTraits<KIND, kBKT>;  // chunk and element size do not depend on BK
     constexpr int CH = T::kChunk;
     const int kcn = bk / CH;
     const int64_t nkt = (d.K + bk - 1) / bk;
     const int64_t R = op == 0 ? d.M : d.N;
     const int64_t total = (R + rows - 1) / rows * nkt * kcn * rows;
+    // let the GETT that depends on this grid launch now (its converters
+    // wait for this grid's completion before reading the images)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const float *__restrict__ src = (const float *)(op == 0 ? d.A : d.B);
     const int nr = op == 0 ? d.nm : d.nn;
     const int64_t *rext = op == 0 ? d.m_ext : d.n_ext;
@@ -1282,18 +1291,19 @@ __global__ void __launch_bounds__(256) pack_kernel(const GettDesc d, int op, int
     const int64_t *ks = op == 0 ? d.k_sA : d.k_sB;
     const int slice = rows * bk * T::kElemBytes;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x) {
-        int64_t q = c;  // rows fastest, then K chunks, K stages, row tiles
-        const int row = (int)(q % rows);
-        q /= rows;
-        const int kc = (int)(q % kcn);
-        q /= kcn;
-        const int64_t kt = q % nkt, rt = q / nkt;
+        // rows fastest, then K chunks, K stages, row tiles (divmod: 32-bit
+        // divisions whenever the values fit)
+        int64_t row, kc, kt;
+        int64_t q = divmod(c, rows, row);
+        q = divmod(q, kcn, kc);
+        const int64_t rt = divmod(q, nkt, kt);
         int64_t r = rt * rows + row, ro = -1;
         if (r < R) {
             ro = 0;
             for (int m = 0; m < nr; ++m) {  // first row mode fastest
-                ro += (r % rext[m]) * rs[m];
-                r /= rext[m];
+                int64_t v;
+                r = divmod(r, rext[m], v);
+                ro += v * rs[m];
             }
         }
         float x[CH];
@@ -1304,8 +1314,9 @@ __global__ void __launch_bounds__(256) pack_kernel(const GettDesc d, int op, int
             if (ro >= 0 && k < d.K) {
                 int64_t ko = 0;
                 for (int m = d.nk - 1; m >= 0; --m) {  // innermost K mode fastest
-                    ko += (k % d.k_ext[m]) * ks[m];
-                    k /= d.k_ext[m];
+                    int64_t v;
+                    k = divmod(k, d.k_ext[m], v);
+                    ko += v * ks[m];
                 }
                 x[e] = src[ro + ko];
             }
@@ -1336,7 +1347,20 @@ tc_status launch_gett(const GettDesc &d, const CUtensorMap &ta, const CUtensorMa
         if (g_gett_sms <= 0) g_gett_sms = 1;
     }
     const int64_t grid = std::min<int64_t>(d.num_tiles - d.tile_begin, g_gett_sms);
-    kern<<<(unsigned)grid, kThreads, kSmem, st>>>(d, ta, tb);
+    // after a pre-pass (d.pk): programmatic stream serialization, so the
+    // kernel's prologue and the TMA stream overlap the pre-pass
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = (!BATCH && d.pk) ? 1 : 0;
+    e = cudaLaunchKernelEx(&cfg, kern, d, ta, tb);
+    if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
     e = cudaGetLastError();
     return e == cudaSuccess ? TC_SUCCESS : fail(TC_ERROR_CUDA, cudaGetErrorString(e));
 }
@@ -1772,9 +1796,9 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
         d.pk_base = (const char *)p.workspace;
         d.pk_tile_bytes = nktp * stage_bytes;
         const int64_t chunks = bytes / 16 / (p.dtype == TC_TF32 ? 1 : 3);  // one per 16-byte row of slice 0
-        const unsigned grid = (unsigned)std::min<int64_t>((chunks + 255) / 256, 152 * 8);
-        if (p.dtype == TC_TF32) pack_kernel<GK_TF32><<<grid, 256, 0, st>>>(d, pk - 1, rows, bkp, (char *)p.workspace);
-        else pack_kernel<GK_BF16X3><<<grid, 256, 0, st>>>(d, pk - 1, rows, bkp, (char *)p.workspace);
+        const unsigned grid = (unsigned)std::min<int64_t>((chunks + 127) / 128, 152 * 16);
+        if (p.dtype == TC_TF32) pack_kernel<GK_TF32><<<grid, 128, 0, st>>>(d, pk - 1, rows, bkp, (char *)p.workspace);
+        else pack_kernel<GK_BF16X3><<<grid, 128, 0, st>>>(d, pk - 1, rows, bkp, (char *)p.workspace);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
     }
