@@ -38,7 +38,10 @@
  * Errors: every call returns a tc_status.  Device work is asynchronous:
  * tc_execute reports argument and launch errors at once and device-side
  * timeouts through tc_plan_device_status after the stream is synchronised.
- * A plan is not thread-safe; use one plan per host thread.
+ * A plan is not thread-safe; use one plan per host thread.  A plan runs
+ * on one stream at a time: tc_execute on another stream while the plan's
+ * previous execute is still in flight is refused with
+ * TC_ERROR_INVALID_ARGUMENT.
  */
 #ifndef TC_H
 #define TC_H
@@ -145,13 +148,19 @@ tc_status tc_plan_selected(tc_plan plan, int32_t *alg_id);
  * id 0, the pre-converted input of tc_plan_set_gett_pack, else 0).  The
  * plan allocates it on the first tc_execute of that algorithm and keeps it
  * until tc_plan_destroy; call tc_execute once before capturing a CUDA
- * graph.  Executes of one plan whose work overlaps on the GPU (several
- * streams) share this workspace and race on it: give each stream its own
- * plan. */
+ * graph.  The workspace serves one execute at a time, so tc_execute
+ * refuses a second stream while the plan's last execute is in flight
+ * (below): give each stream its own plan. */
 tc_status tc_algorithm_workspace(tc_plan plan, int32_t alg_id, size_t *bytes);
 
 /* C = alpha * A.B + beta * C with the selected algorithm, enqueued on
- * stream.  Returns after the launches are enqueued. */
+ * stream.  Returns after the launches are enqueued.  When the plan's
+ * previous tc_execute ran on a different stream and has not finished yet
+ * (an event recorded after it is still pending), nothing is enqueued and
+ * TC_ERROR_INVALID_ARGUMENT is returned: concurrent executes of one plan
+ * would share its workspace.  Executes on the same stream queue behind one
+ * another as usual.  While `stream` is capturing a CUDA graph the check is
+ * skipped and nothing is recorded. */
 tc_status tc_execute(tc_plan plan, const void *alpha, const void *A,
                      const void *B, const void *beta, void *C, void *stream);
 
@@ -160,6 +169,9 @@ tc_status tc_execute(tc_plan plan, const void *alpha, const void *A,
  * capture mode (where cudaMalloc fails), code that works inside a fixed
  * device-memory budget owned by its own allocator, or latency-critical
  * loops that cannot afford an allocation.  The paper has no counterpart.
+ * Callers running beside another thread's global-mode capture must pass a
+ * stream of their own created non-blocking: work enqueued on the legacy
+ * default stream (stream NULL) during that capture invalidates it.
  *
  * Runs the selected loop-nest algorithm (ids >= 1, TC_F64 or TC_F32) like
  * tc_execute, but its copy scratch is a fixed 16 MiB array that every GPU

@@ -67,6 +67,7 @@ struct Plan {
     size_t workspace_bytes = 0;
     int *dev_status = nullptr;      // bounded-wait status word
     void *last_stream = nullptr;
+    void *busy_event = nullptr;     // recorded after each tc_execute (cudaEvent_t)
     void *gett_state = nullptr;     // owned by the GETT executor
     void *flush_buf = nullptr;      // predictor: remote regions / L2 flush
     size_t flush_bytes = 0;

@@ -343,6 +343,7 @@ tc_status tc_plan_destroy(tc_plan plan) {
         if (p.workspace) cudaFree(p.workspace);
         if (p.dev_status) cudaFree(p.dev_status);
         if (p.flush_buf) cudaFree(p.flush_buf);
+        if (p.busy_event) cudaEventDestroy((cudaEvent_t)p.busy_event);
         cudaSetDevice(cur);
     }
     delete plan;
@@ -441,9 +442,35 @@ tc_status tc_execute(tc_plan plan, const void *alpha, const void *A, const void 
     if (!alpha || !beta) return fail(TC_ERROR_INVALID_ARGUMENT, "alpha/beta is NULL");
     if (!A || !B || !C) return fail(TC_ERROR_INVALID_ARGUMENT, "operand pointer is NULL");
     Plan &p = plan->p;
+    // One plan runs on one stream at a time: its workspace and status word
+    // serve one execute.  An execute on another stream while the previous
+    // one is still in flight is refused.  Work captured into a graph is
+    // not checked (the graph and its caller order the replays).
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing((cudaStream_t)stream, &cs);
+    if (e != cudaSuccess) return fail(TC_ERROR_CUDA, std::string("stream query: ") + cudaGetErrorString(e));
+    const bool capturing = cs != cudaStreamCaptureStatusNone;
+    if (!capturing && p.busy_event && stream != p.last_stream) {
+        e = cudaEventQuery((cudaEvent_t)p.busy_event);
+        if (e == cudaErrorNotReady)
+            return fail(TC_ERROR_INVALID_ARGUMENT,
+                        "the plan's previous execute is still running on another stream; "
+                        "give each stream its own plan, or wait for that stream first");
+        if (e != cudaSuccess) return fail(TC_ERROR_CUDA, std::string("event query: ") + cudaGetErrorString(e));
+    }
     const Algorithm &alg = p.algs[p.selected];
-    if (alg.kernel == TC_KERNEL_GETT) return exec_gett(p, alpha, A, B, beta, C, stream);
-    return exec_nest(p, alg, alpha, A, B, beta, C, stream);
+    tc_status s = alg.kernel == TC_KERNEL_GETT ? exec_gett(p, alpha, A, B, beta, C, stream)
+                                               : exec_nest(p, alg, alpha, A, B, beta, C, stream);
+    if (s != TC_SUCCESS || capturing) return s;
+    if (!p.busy_event) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail(TC_ERROR_CUDA, std::string("event create: ") + cudaGetErrorString(e));
+        p.busy_event = ev;
+    }
+    e = cudaEventRecord((cudaEvent_t)p.busy_event, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(TC_ERROR_CUDA, std::string("event record: ") + cudaGetErrorString(e));
+    return TC_SUCCESS;
 }
 
 tc_status tc_plan_device_status(tc_plan plan) {

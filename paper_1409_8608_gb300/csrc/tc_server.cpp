@@ -259,22 +259,25 @@ struct ServerImpl {
                 r->offset = off;
                 r->bytes = need;
             }
-            auto it = plans.find(key(*r));
+            // plans are cached per stream: one plan never runs on two
+            // streams at once (tc_execute refuses that)
+            r->stream = rr++ % (int)streams.size();
+            const std::string pkey = key(*r) + "#" + std::to_string(r->stream);
+            auto it = plans.find(pkey);
             if (it == plans.end()) {
                 tc_plan p = nullptr;
                 tc_status s = tc_plan_create(&p, r->spec.c_str(), r->extents.data(), nullptr, r->dtype);
-                // one cached plan serves requests on several streams at once:
-                // no plan workspace (the GETT's pre-converted input) to share
+                // requests on one stream reuse its plan back to back: no plan
+                // workspace (the GETT's pre-converted input) to keep apart
                 if (s == TC_SUCCESS) s = tc_plan_set_gett_pack(p, 0);
                 if (s != TC_SUCCESS) {
                     if (p) tc_plan_destroy(p);
                     finish(r, s);
                     continue;
                 }
-                it = plans.emplace(key(*r), p).first;
+                it = plans.emplace(pkey, p).first;
             }
             r->plan = it->second;  // algorithm 0, the fused GETT
-            r->stream = rr++ % (int)streams.size();
             tc_status s = launch(*r);
             if (s != TC_SUCCESS) {
                 cudaStreamSynchronize(streams[r->stream]);

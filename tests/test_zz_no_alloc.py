@@ -4,9 +4,10 @@ allocate device memory (its copy scratch is a fixed array in the library).
 It is called through the C ABI and must reproduce tc_execute: the same
 algorithm runs the same chain of operations, so the results agree bit for
 bit, and both stay within the FP64 bound the other parity tests use
-(componentwise error <= 1e-12 relative to |A||B|).  Two calls in a row
-check that the shared scratch carries nothing over from one call to the
-next.  This file is collected last on purpose."""
+(componentwise error <= 1e-12 relative to |A||B|).  Consecutive calls run
+on different operands of the same shape, so a call that skipped one of its
+copies and read the previous call's leftovers in the shared scratch would
+differ from tc_execute.  This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -30,47 +31,120 @@ def tcmod():
     return tc
 
 
-def _no_alloc(tc, plan, alpha, dA, dB, beta, dC):
-    a, b = ctypes.c_double(alpha), ctypes.c_double(beta)
+def _no_alloc(tc, plan, alpha, dA, dB, beta, dC, dtype="f64", stream=None):
+    """Calls the C entry point directly (alpha/beta as the plan's scalar type)."""
+    scal = ctypes.c_double if dtype == "f64" else ctypes.c_float
+    a, b = scal(alpha), scal(beta)
     st = tc.load().tc_execute_no_alloc(plan.handle, ctypes.addressof(a), dA.data_ptr(), dB.data_ptr(),
-                                       ctypes.addressof(b), dC.data_ptr(), None)
+                                       ctypes.addressof(b), dC.data_ptr(), stream)
     if st != 0:
         raise tc.TcError(st, "tc_execute_no_alloc", tc.load().tc_last_error().decode())
 
 
+def _operand_sets(spec, ext, dev, tdt, seeds):
+    out = []
+    for s in seeds:
+        A, B, C0 = synth.uniform_operands(spec, ext, seed=s, with_c=True)
+        out.append((A, B, C0, torch.from_numpy(A).to(dev, tdt), torch.from_numpy(B).to(dev, tdt)))
+    return out
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("spec,ext,names", [
     ("abc=iaj,jbic", [40, 36, 24, 16, 16], ["i'c-gemm", "ci'-gemm", "jc'-gemm", "cbj-dot"]),
     ("abc=bi,iac", [9, 7, 5, 4], None),  # C slices copied in and out
 ])
-def test_no_alloc_matches_tc_execute(tcmod, spec, ext, names):
-    A, B, C0 = synth.uniform_operands(spec, ext, seed=2, with_c=True)
+def test_no_alloc_matches_tc_execute(tcmod, spec, ext, names, dtype):
     dev = torch.device("cuda:0")
-    dA, dB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
-    n = C0.size
-    want = oc.contract(spec, ext, A, B)
-    scale = oc.contract(spec, ext, np.abs(A), np.abs(B))
-    plan = tcmod.Plan(spec, ext, dtype="f64")
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    sets = _operand_sets(spec, ext, dev, tdt, seeds=(2, 3))
+    n = sets[0][2].size
+    plan = tcmod.Plan(spec, ext, dtype=dtype)
     algs = plan.algorithms()
     chosen = [a for a in algs if a["id"] > 0 and (names is None and a["copy_mask"] or names and a["name"] in names)]
     assert chosen and any(a["copy_mask"] for a in chosen)
     for a in chosen:
         plan.select(a["id"])
-        ref = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
-        plan.execute(dA, dB, ref)
-        for call in range(2):  # two calls in a row share the scratch
-            got = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
-            _no_alloc(tcmod, plan, 1.0, dA, dB, 0.0, got)
+        # alternate the two operand sets: each call fills the scratch with
+        # its own copies; leftovers of the previous call would show
+        for call, k in enumerate((0, 1, 0)):
+            A, B, _, dA, dB = sets[k]
+            ref = torch.full((n,), float("nan"), dtype=tdt, device=dev)
+            plan.execute(dA, dB, ref)
+            got = torch.full((n,), float("nan"), dtype=tdt, device=dev)
+            _no_alloc(tcmod, plan, 1.0, dA, dB, 0.0, got, dtype)
             torch.cuda.synchronize()
             g, r = got.cpu().numpy(), ref.cpu().numpy()
             assert np.array_equal(g, r), (a["name"], call)
-            assert np.max(np.abs(g - want) / scale) <= 1e-12, (a["name"], call)
+            if dtype == "f64":
+                want = oc.contract(spec, ext, A, B)
+                scale = oc.contract(spec, ext, np.abs(A), np.abs(B))
+                assert np.max(np.abs(g - want) / scale) <= 1e-12, (a["name"], call)
         # beta != 0 reads C through the same path
-        c_ref = torch.from_numpy(C0).to(dev)
+        _, _, C0, dA, dB = sets[1]
+        c_ref = torch.from_numpy(C0).to(dev, tdt)
         c_got = c_ref.clone()
         plan.execute(dA, dB, c_ref, alpha=2.0, beta=0.5)
-        _no_alloc(tcmod, plan, 2.0, dA, dB, 0.5, c_got)
+        _no_alloc(tcmod, plan, 2.0, dA, dB, 0.5, c_got, dtype)
         torch.cuda.synchronize()
         assert np.array_equal(c_got.cpu().numpy(), c_ref.cpu().numpy()), a["name"]
+    plan.close()
+
+
+def test_no_alloc_only_plan_allocates_nothing(tcmod):
+    # A plan that is only ever run through tc_execute_no_alloc (the case the
+    # entry point exists for): correct against the FP64 oracle, and the
+    # device's free memory is the same before and after (tc_execute would
+    # allocate the copy workspace and a status word).  The library's module
+    # is loaded first by another call, so its static array is already there.
+    spec, ext = "abc=iaj,jbic", [40, 36, 24, 16, 16]
+    dev = torch.device("cuda:0")
+    warm = tcmod.Plan(spec, ext, dtype="f64")
+    name = "i'c-gemm"
+    ids = {a["name"]: a["id"] for a in warm.algorithms()}
+    warm.select(ids[name])
+    sets = _operand_sets(spec, ext, dev, torch.float64, seeds=(4, 5))
+    n = sets[0][2].size
+    outs = [torch.full((n,), float("nan"), dtype=torch.float64, device=dev) for _ in sets]
+    _no_alloc(tcmod, warm, 1.0, sets[0][3], sets[0][4], 0.0, outs[0])
+    torch.cuda.synchronize()
+    warm.close()
+    plan = tcmod.Plan(spec, ext, dtype="f64")
+    plan.select(ids[name])
+    assert plan.workspace(ids[name]) > 0  # the algorithm copies a slice
+    free0, _ = torch.cuda.mem_get_info(dev)
+    for (A, B, _, dA, dB), out in zip(sets, outs):
+        _no_alloc(tcmod, plan, 1.0, dA, dB, 0.0, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert free1 == free0
+    for (A, B, _, _, _), out in zip(sets, outs):
+        want = oc.contract(spec, ext, A, B)
+        scale = oc.contract(spec, ext, np.abs(A), np.abs(B))
+        assert np.max(np.abs(out.cpu().numpy() - want) / scale) <= 1e-12
+    plan.close()
+
+
+def test_no_alloc_on_a_created_stream(tcmod):
+    # Callers that run while another thread captures a graph in global mode
+    # must use a non-blocking stream of their own (work on the legacy
+    # default stream would invalidate that capture): one call on a created
+    # stream, checked bitwise against tc_execute.
+    spec, ext = "abc=iaj,jbic", [40, 36, 24, 16, 16]
+    dev = torch.device("cuda:0")
+    (A, B, _, dA, dB), = _operand_sets(spec, ext, dev, torch.float64, seeds=(6,))
+    plan = tcmod.Plan(spec, ext, dtype="f64")
+    plan.select({a["name"]: a["id"] for a in plan.algorithms()}["jc'-gemm"])
+    n = int(np.prod(ext[:3]))
+    ref = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+    plan.execute(dA, dB, ref)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream(device=dev)
+    got = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    _no_alloc(tcmod, plan, 1.0, dA, dB, 0.0, got, stream=side.cuda_stream)
+    side.synchronize()
+    assert np.array_equal(got.cpu().numpy(), ref.cpu().numpy())
     plan.close()
 
 
