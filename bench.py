@@ -1,20 +1,33 @@
 """Benchmark: contraction throughput on one GB300 (or N replicas).
 
-Workload: C[a,b,c] = sum_{i,j} A[i,a,j] * B[j,b,i,c] with a = b = c = 512 and
-i = j = 16 (the permuted plain workload, dense column-major, entries uniform
-in [-1, 1]).  One step = one tc_execute of the selected algorithm over
-inputs already resident in HBM (1.6 GB in FP64, larger than the 129 MB L2,
-so no flush is needed between steps).
+Headline workload (the larger permuted plain method): C[a,b,c] =
+sum_{i,j} A[i,a,j] * B[j,b,i,c] with a = b = c = 512 and i = j = 16, dense
+column-major, entries uniform in [-1, 1], in the paper's double precision.
+One step = one tc_execute of the planner's GETT over inputs already resident
+in HBM (1.6 GB in FP64, larger than the 129 MB L2, so no flush is needed
+between steps).  The same line carries the same workload in FP32 and in the
+chosen precision form (split-BF16 on the tensor cores, FP32 I/O) with its
+measured error, and one object per other workload of the study:
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype f64|f32]
-                    [--alg gett|<name>] [--impl reference]
+  small      abc=ai,ibc a=b=c=64 i=8 FP64: every algorithm, microseconds
+  ranking    abc=iaj,jbic n=128 i=j=16 FP64: predicted vs measured, all 177
+  precision  abc=ai,ibc 512^3 i=64 and ab=aij,jib 4096^2 i=j=64: every
+             precision form, time, roofline, error (uniform and lognormal)
+  batched    4096 x abc=ai,ibc (a,b,c log-uniform [8,128], i in {4,...,32})
+  serving    Poisson request stream, 10 s after 1 s of warm-up, rate sweep
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--quick]
+                    [--impl reference]
 
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
-host cores instead (a bounded slab of the same workload per step).
+host cores instead (a bounded slab of the same workload per step).  The
+oracle runs only in the CPU leg below (timing it, and computing expected
+values for sampled outputs); the GPU numbers come from libtc.so alone.
 """
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -27,11 +40,11 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = "contraction GFLOP/s & %roofline, chosen vs plain FP64 form; p50/p99 latency ms"
 SPEC = "abc=iaj,jbic"
 N_FREE, N_CONTR = 512, 16
 EXTENTS = [N_FREE, N_FREE, N_FREE, N_CONTR, N_CONTR]
-WORKLOAD = "abc=iaj,jbic a=b=c=512 i=j=16 uniform[-1,1]"
-METRIC = "contraction GFLOP/s (abc=iaj,jbic, a=b=c=512, i=j=16)"
+WORKLOAD = "abc=iaj,jbic a=b=c=512 i=j=16 uniform[-1,1], FP64 (the paper's precision)"
 
 
 def set_free_extent(n):
@@ -39,12 +52,14 @@ def set_free_extent(n):
     global N_FREE, EXTENTS, WORKLOAD
     N_FREE = n
     EXTENTS = [n, n, n, N_CONTR, N_CONTR]
-    WORKLOAD = f"abc=iaj,jbic a=b=c={n} i=j=16 uniform[-1,1]"
+    WORKLOAD = f"abc=iaj,jbic a=b=c={n} i=j=16 uniform[-1,1], FP64"
+
+
 SMS = 152
 SM_MAX_MHZ = 2070.0
-# FP64: 2 DFMA per SM per clock (measured 1.20 TFLOP/s at 1.97 GHz); FP32: 128 FFMA.
-ALU_PEAK_TFLOPS = {"f64": SMS * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12,
-                   "f32": SMS * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12}
+TORCH_IN = {"f64": "float64", "f32": "float32", "tf32": "float32", "bf16x3": "float32",
+            "bf16": "bfloat16", "f16": "float16"}
+TENSOR_FORMS = ("tf32", "bf16", "f16", "bf16x3")
 
 
 def flops_of(extents):
@@ -79,6 +94,19 @@ def measured_peaks():
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                 "fallback": True}
+
+
+def alu_peak(dtype):
+    """FP64 DFMA / FP32 FFMA peak (TFLOP/s) and where it comes from: the
+    committed probe summary (profiles/alu_peaks.json, measured on this
+    pool's GB300s), else the unit count x max clock."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "alu_peaks.json")) as f:
+            p = json.load(f)
+        return float(p[dtype]["tflops"]), f"measured ({p[dtype]['how']})"
+    except (OSError, ValueError, KeyError):
+        per_clk = {"f64": 2 * 2, "f32": 128 * 2}[dtype]
+        return SMS * per_clk * SM_MAX_MHZ * 1e6 / 1e12, "derived: 152 SMs x units x 2 x 2070 MHz"
 
 
 class ClockSampler:
@@ -158,55 +186,455 @@ def aggregate_over_ranks(total_ms, steps, flops, world, dist=None, device="cpu")
     return total_ms, total_ms / steps, flops * steps * world / (total_ms / 1e3) / 1e9
 
 
-def cpu_oracle_sample(target_s=12.0, threads=None):
-    """Times the FP64 oracle on a slab of the workload (last C mode c)."""
+def event_median(fn, reps, stream, warm=1):
+    """Median seconds of fn() between CUDA events on `stream`."""
+    import torch
+    for _ in range(warm):
+        fn()
+    out = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1) * 1e-3)
+    return statistics.median(out)
+
+
+def sample_points(spec, extents, count, seed):
+    """Random C multi-indices and their linear (Fortran) offsets."""
+    from paper_1409_8608_gb300 import synth
+    c_modes = synth.spec_modes(spec)[0]
+    e = dict(zip(synth.index_order(spec), [int(x) for x in extents]))
+    rng = np.random.default_rng(seed)
+    pts = np.stack([rng.integers(0, e[m], count) for m in c_modes], axis=1)
+    lin = np.zeros(count, dtype=np.int64)
+    mul = 1
+    for k, m in enumerate(c_modes):
+        lin += pts[:, k] * mul
+        mul *= e[m]
+    return pts, lin
+
+
+# ---------------------------------------------------------------- CPU leg
+# The only code here that runs the oracle: the CPU baseline (the FP64
+# oracle timed on the host cores) and the expected values of sampled
+# outputs, computed one by one.  Nothing on a GPU path calls these.
+
+def cpu_oracle_slab(spec, extents, target_s, threads, seed=0):
+    """Times the FP64 oracle on a slab of the last C mode sized for about
+    target_s seconds; returns (GFLOP/s, threads, slab, total slices, s)."""
     from oracle import contraction as oc
     from paper_1409_8608_gb300 import synth
-    cores = threads or len(os.sched_getaffinity(0))
-    cores = min(cores, oc.max_threads()) if oc.max_threads() > 0 else cores
-    A, B, _ = synth.uniform_operands(SPEC, EXTENTS, seed=0)
-    C = np.zeros(N_FREE ** 3)
-    # calibrate on one c slice, then size the slab for ~target_s
+    if oc.max_threads() > 0:
+        threads = min(threads, oc.max_threads())
+    A, B, _ = synth.uniform_operands(spec, extents, seed=seed)
+    nC = synth.dense_sizes(spec, extents)[0]
+    C = np.zeros(nC)
+    order = synth.index_order(spec)
+    e = dict(zip(order, extents))
+    last = e[synth.spec_modes(spec)[0][-1]]
+    per = max(1, min(threads, last, int(max(1.0, 2e9 / (flops_of(extents) / last)))))
     t0 = time.perf_counter()
-    oc.contract(SPEC, EXTENTS, A, B, C=C, outer_range=(0, cores), threads=cores)
-    t1 = time.perf_counter() - t0
-    per_slice = max(t1 / cores, 1e-5)
-    nsl = int(max(cores, min(N_FREE, target_s / per_slice)))
-    nsl = min(N_FREE, max(1, nsl))
-    return A, B, C, cores, nsl
+    oc.contract(spec, extents, A, B, C=C, outer_range=(0, per), threads=threads)
+    t1 = max(time.perf_counter() - t0, 1e-6) / per
+    nsl = int(max(1, min(last, target_s / t1)))
+    t0 = time.perf_counter()
+    oc.contract(spec, extents, A, B, C=C, outer_range=(0, nsl), threads=threads)
+    dt = time.perf_counter() - t0
+    f = flops_of(extents) * nsl / last
+    return f / dt / 1e9, threads, nsl, last, dt
 
 
-def run_reference(args):
+def cpu_baseline_line(spec, extents, seconds):
+    """OpenMP over all cores (the value) and one thread beside it."""
+    cores = len(os.sched_getaffinity(0))
+    v, used, nsl, last, dt = cpu_oracle_slab(spec, extents, seconds, cores)
+    v1, _, nsl1, _, dt1 = cpu_oracle_slab(spec, extents, seconds / 2, 1)
+    return {"value": v, "unit": "GFLOP/s", "cores": used, "kind": "oracle",
+            "sample": f"FP64 oracle (plain nested loops, OpenMP over the outermost free index) on a slab "
+                      f"of {nsl} of {last} values of the last C index ({dt:.1f} s)",
+            "single_thread": {"value": v1, "unit": "GFLOP/s", "cores": 1,
+                              "sample": f"slab of {nsl1} of {last} ({dt1:.1f} s)"}}
+
+
+def oracle_points(spec, extents, A, B, pts, threads):
+    """Expected values and |A||B| scales at the sampled points (FP64)."""
     from oracle import contraction as oc
-    world, rank, _ = dist_setup()
-    if rank != 0:
-        return 0
-    target = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-    A, B, C, cores, nsl = cpu_oracle_sample(target_s=target)
-    f_slab = flops_of([N_FREE, N_FREE, nsl, N_CONTR, N_CONTR])
+    want = oc.contract_points(spec, extents, A, B, pts, threads=threads)
+    scale = oc.contract_points(spec, extents, np.abs(A), np.abs(B), pts, threads=threads)
+    return want, scale
+
+
+def oracle_full(spec, extents, A, B, threads):
+    from oracle import contraction as oc
+    want = oc.contract(spec, extents, A, B, threads=threads)
+    scale = oc.contract(spec, extents, np.abs(A), np.abs(B), threads=threads)
+    return want, scale
+
+
+def max_rel_err(got, want, scale):
+    return float(np.max(np.abs(np.asarray(got, dtype=np.float64) - want) / scale))
+
+
+def cpu_batch_baseline(rows, seconds, threads):
+    """FP64 oracle over the batched problems in list order until about
+    `seconds` have passed."""
+    from oracle import contraction as oc
+    from paper_1409_8608_gb300 import synth
+    spec = "abc=ai,ibc"
+    done_f, t0, n = 0.0, time.perf_counter(), 0
+    for ext in rows:
+        A, B, _ = synth.uniform_operands(spec, ext, seed=n)
+        oc.contract(spec, ext, A, B, threads=threads)
+        done_f += flops_of(ext)
+        n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done_f / dt / 1e9, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": f"the first {n} of {len(rows)} problems, FP64 ({dt:.1f} s)"}
+
+
+def cpu_serving_baseline(requests, seconds, threads):
+    """FP64 oracle on a slab of each sampled request, about `seconds` in all
+    (requests whose single slice of the last C index exceeds 2 GFLOP are
+    left out: one slice is the smallest unit the slab timing runs)."""
+    from paper_1409_8608_gb300 import synth
+    keep = []
+    for spec, ext in requests:
+        e = dict(zip(synth.index_order(spec), ext))
+        if flops_of(ext) / e[synth.spec_modes(spec)[0][-1]] <= 2e9:
+            keep.append((spec, ext))
+    if not keep:
+        return None
+    per = seconds / len(keep)
+    gf, tt = 0.0, 0.0
+    for spec, ext in keep:
+        v, _, nsl, last, dt = cpu_oracle_slab(spec, ext, per, threads)
+        gf += v * dt
+        tt += dt
+    return {"value": gf / tt, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": f"slabs of {len(keep)} of {len(requests)} sampled requests "
+                      f"(those with at most 2 GFLOP per slice; {tt:.1f} s)"}
+
+
+# ---------------------------------------------------------------- GPU legs
+def measure_form(args, dtype, spec, extents, A, B, dev, stream, dist, world, tc, steps,
+                 alg_name="gett", products=6, e2e=True, sample_lin=None, clocks=True):
+    """Times one form (dtype + algorithm) of a workload; returns its line."""
+    import torch
+    tin = getattr(torch, TORCH_IN[dtype])
+    tout = torch.float64 if dtype == "f64" else torch.float32
+    from paper_1409_8608_gb300 import synth
+    nC = synth.dense_sizes(spec, extents)[0]
+
+    def new_plan():
+        pl = tc.Plan(spec, extents, dtype=dtype)
+        if dtype == "bf16x3":
+            pl.set_split(products)
+        pl.select({a["name"]: a["id"] for a in pl.algorithms()}[alg_name])
+        return pl
+
+    plan = new_plan()
+    alg = next(a for a in plan.algorithms() if a["name"] == alg_name)
+    hA = torch.from_numpy(A).to(tin).pin_memory()
+    hB = torch.from_numpy(B).to(tin).pin_memory()
+    dA, dB = hA.to(dev), hB.to(dev)
+    dC = torch.empty(nC, dtype=tout, device=dev)
+    flops = plan.flops
+    # GETT: one kernel, plus the pre-pass when the plan pre-converts its
+    # smaller input (the only GETT workspace); nests: phases and copies
+    if alg["kernel"] == "gett":
+        launches_per_step = 1 + int(plan.workspace(alg["id"]) > 0)
+    else:
+        launches_per_step = alg["n_phases"] * (1 + sum(1 for lv in alg["copy_level"] if lv != -2))
+
+    def step():
+        plan.execute(dA, dB, dC, alpha=1.0, beta=0.0, stream=stream)
+
     for _ in range(args.warmup):
-        oc.contract(SPEC, EXTENTS, A, B, C=C, outer_range=(0, nsl), threads=cores)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oc.contract(SPEC, EXTENTS, A, B, C=C, outer_range=(0, nsl), threads=cores)
-        times.append(time.perf_counter() - t0)
-    total = sum(times)
-    value = f_slab * args.steps / total / 1e9
-    sample = f"c-slab of {nsl} of {N_FREE} slices ({f_slab / 1e9:.2f} GFLOP) per step"
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": "FP64 CPU oracle (plain nested loops, OpenMP)",
-                   "l2": "n/a (host)"},
-        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
-        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
-    return 0
+        step()
+    torch.cuda.synchronize()
+    plan.device_status()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    est = event_median(step, 2, stream, warm=0)
+    # untimed load around the timed region (about 0.3 s before and after),
+    # so that the clock sampler sees the clocks the timed steps run at
+    pad = max(1, int(0.3 / max(1e-4, est))) if clocks else 0
+    sampler = ClockSampler(torch.cuda.current_device()) if clocks else None
+    if sampler:
+        sampler.__enter__()
+    try:
+        for _ in range(pad):
+            step()
+        t_begin = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_begin.record(stream)
+        for k in range(steps):
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        t_end.record(stream)
+        for _ in range(pad):
+            step()
+        torch.cuda.synchronize()
+    finally:
+        if sampler:
+            sampler.__exit__(None, None, None)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    plan.device_status()
+    total_ms = t_begin.elapsed_time(t_end)
+    step_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    total_ms, ms_per_step, value = aggregate_over_ranks(total_ms, steps, flops, world, dist, dev)
+    samples = dC[torch.from_numpy(sample_lin).to(dev)].double().cpu().numpy() if sample_lin is not None else None
+
+    # end to end through tc_execute_host: pinned host inputs copied in, the
+    # contraction, the result copied back, every step, inside one C ABI
+    # call.  Two plans on two streams take alternate steps, so one step's
+    # result copy overlaps the next step's input copies and kernels.
+    e2e_line = None
+    if e2e:
+        lanes = []
+        for _ in range(2):
+            lanes.append((torch.cuda.Stream(device=dev), new_plan(), torch.empty(nC, dtype=tout).pin_memory()))
+        for st, pl, hc in lanes:  # first call allocates the plan's device copies
+            pl.execute_host(hA, hB, hc, stream=st)
+        torch.cuda.synchronize()
+        e2e_steps = max(4, min(steps, 8))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for st, _, _ in lanes:
+            st.wait_event(e0)
+        for k in range(e2e_steps):
+            st, pl, hc = lanes[k % 2]
+            pl.execute_host(hA, hB, hc, stream=st)
+        for st, _, _ in lanes:
+            done = torch.cuda.Event()
+            done.record(st)
+            stream.wait_event(done)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        for _, pl, _ in lanes:
+            pl.device_status()
+            pl.close()
+        e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        e2e_line = {"value": flops * world / (e2e_ms / 1e3) / 1e9, "unit": "GFLOP/s",
+                    "h2d_bytes_per_step": int(hA.numel() * hA.element_size() + hB.numel() * hB.element_size()),
+                    "d2h_bytes_per_step": int(nC * dC.element_size()),
+                    "call": "tc_execute_host (pinned host buffers; copies in, contraction, copy out)",
+                    "pipelining": "2 plans on 2 streams take alternate steps"}
+
+    peaks = measured_peaks()
+    launch_s = step_ms / 1e3  # every launch of a step: the pre-pass and the GETT, or the phases
+    algorithmic_bytes = int(hA.numel() * hA.element_size() + hB.numel() * hB.element_size() + nC * dC.element_size())
+    nkey = extents[0]
+    if dtype in TENSOR_FORMS:
+        prods = products if dtype == "bf16x3" else 1
+        work = flops * prods
+        peak_tf = peaks["bf16_tflops"] * (0.5 if dtype == "tf32" else 1.0)
+        achieved_tf = work / launch_s / 1e12
+        tkey = f"gett_tc_kernel/{dtype}/{spec}/{nkey}" + (f"/p{prods}" if dtype == "bf16x3" else "")
+        roofline = {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": achieved_tf / peak_tf,
+                    "traffic": captured_traffic(tkey, "paper_1409_8608_gb300/csrc/tc_gett.cu"),
+                    "algorithmic_bytes": algorithmic_bytes,
+                    "kernel": "gett_tc_kernel" + (" + pack_kernel (timed together)" if launches_per_step == 2 else ""),
+                    "work": f"{prods} slice products x 2*prod(extents) = {work / 1e9:.1f} GFLOP per step",
+                    "peak_source": "MEASURED_PEAKS bf16_tflops (burst)" +
+                    (" x 0.5 (TF32 nominal ratio)" if dtype == "tf32" else "") +
+                    (" (fallback)" if peaks.get("fallback") else " (measured)")}
+    else:
+        achieved_tf = flops / launch_s / 1e12
+        peak_tf, src = alu_peak(dtype)
+        kern = "tile_kernel" if alg["kernel"] in ("gett", "gemm") else "elementwise_kernel"
+        tkey = f"{kern}/{dtype}/{spec}/{nkey}"
+        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": achieved_tf / peak_tf,
+                    "traffic": captured_traffic(tkey, "paper_1409_8608_gb300/csrc/tc_exec.cu"),
+                    "algorithmic_bytes": algorithmic_bytes, "kernel": kern,
+                    "work": f"2*prod(extents) = {flops / 1e9:.1f} GFLOP per step",
+                    "peak_source": ("DFMA" if dtype == "f64" else "FFMA") + " " + src}
+    line = {"value": value, "unit": "GFLOP/s", "ms_per_step": ms_per_step, "dtype": dtype,
+            "algorithm": alg_name, "roofline": roofline, "e2e": e2e_line,
+            "gpu_launches": int(steps * launches_per_step), "steps": steps,
+            "clocks": sampler.summary() if sampler else None}
+    plan.close()
+    return line, samples
+
+
+def run_small(tc, seed=0):
+    """abc=ai,ibc a=b=c=64 i=8 FP64: every algorithm, microseconds each
+    (L2-resident and latency-bound, so no roofline), predicted beside it."""
+    from paper_1409_8608_gb300 import ranking
+    r = ranking.study("abc=ai,ibc", [64, 64, 64, 8], "f64", seed=seed, reps=20, cap=1.0)
+    algs = {a["name"]: round(a["measured_s"] * 1e6, 2) for a in r["algorithms"]}
+    return {"workload": "abc=ai,ibc a=b=c=64 i=8 FP64 uniform[-1,1] seed 0",
+            "us_per_algorithm": algs,
+            "predicted_us": {a["name"]: round(a["predicted_s"] * 1e6, 2) for a in r["algorithms"]},
+            "spearman": r["spearman"], "top1_regret": r["top1_regret"],
+            "top_predicted": r["top_pred"], "top_measured": r["top_meas"]}
+
+
+def run_ranking(tc, n=128, dtype="f64"):
+    from paper_1409_8608_gb300 import ranking
+    r = ranking.study(SPEC, [n, n, n, 16, 16], dtype, seed=0, reps=3, cap=1.0)
+    return {"workload": f"{SPEC} a=b=c={n} i=j=16 {dtype.upper()}", "algorithms": len(r["algorithms"]),
+            "spearman": r["spearman"], "kendall": r["kendall"], "top1_regret": r["top1_regret"],
+            "top_predicted": r["top_pred"], "top_measured": r["top_meas"],
+            "prediction_s": r["prediction_seconds"], "measurement_s": r["measurement_seconds"]}
+
+
+PRECISION_WORKLOADS = (
+    ("abc=ai,ibc", [512, 512, 512, 64], "hbm"),
+    ("ab=aij,jib", [4096, 4096, 64, 64], "tensor"),
+)
+# (label, dtype, products, compensation chunk: None = the plan's default)
+PRECISION_FORMS = (
+    ("bf16x3 x6 (chosen)", "bf16x3", 6, None), ("bf16x3 x3", "bf16x3", 3, None),
+    ("bf16x3 x9", "bf16x3", 9, None), ("bf16x3 x6 uncompensated", "bf16x3", 6, 0),
+    ("tf32", "tf32", None, None), ("bf16", "bf16", None, None), ("f16", "f16", None, None),
+    ("f32 (SIMT)", "f32", None, None), ("f64 (plain)", "f64", None, None),
+)
+
+
+def run_precision(tc, dev, stream, points=3000, reps=5):
+    """Every precision form on both precision workloads: time (GPU), sampled
+    outputs (errors are computed in the CPU leg)."""
+    import torch
+    from paper_1409_8608_gb300 import synth
+    peaks = measured_peaks()
+    out = []
+    for spec, ext, bound in PRECISION_WORKLOADS:
+        nC, nA, nB = synth.dense_sizes(spec, ext)
+        flops = flops_of(ext)
+        pts, lin = sample_points(spec, ext, points, seed=7)
+        dlin = torch.from_numpy(lin).to(dev)
+        inputs = {}
+        for dist_name, gen, seed in (("uniform", synth.uniform_operands, 0),
+                                     ("lognormal", synth.lognormal_slice_operands, 1)):
+            A, B, _ = gen(spec, ext, seed=seed)
+            inputs[dist_name] = (A, B)
+        rows = []
+        for label, dtype, prods, comp in PRECISION_FORMS:
+            if dtype == "f64" and bound == "tensor":
+                reps_f = 2
+            else:
+                reps_f = reps
+            tin = getattr(torch, TORCH_IN[dtype])
+            tout = torch.float64 if dtype == "f64" else torch.float32
+            plan = tc.Plan(spec, ext, dtype=dtype)
+            if prods:
+                plan.set_split(prods)
+            if comp is not None:
+                plan.set_compensation(comp)
+            plan.select(0)
+            row = {"form": label, "samples": {}}
+            for dist_name, (A, B) in inputs.items():
+                dA = torch.from_numpy(A).to(tin).to(dev)
+                dB = torch.from_numpy(B).to(tin).to(dev)
+                dC = torch.empty(nC, dtype=tout, device=dev)
+                run1 = lambda: plan.execute(dA, dB, dC, stream=stream)
+                if dist_name == "uniform":
+                    t = event_median(run1, reps_f, stream)
+                    row["ms"] = t * 1e3
+                    row["gflops"] = flops / t / 1e9
+                    esz = 8 if dtype == "f64" else 4
+                    row["hbm_frac"] = (nA + nB) * dA.element_size() / t / 1e9 / peaks["hbm_gbs"] + \
+                        nC * esz / t / 1e9 / peaks["hbm_gbs"]
+                    if dtype in TENSOR_FORMS:
+                        work = flops * (prods or 1)
+                        pk = peaks["bf16_tflops"] * (0.5 if dtype == "tf32" else 1.0)
+                        row["tensor_frac"] = work / t / 1e12 / pk
+                else:
+                    run1()
+                torch.cuda.synchronize()
+                plan.device_status()
+                row["samples"][dist_name] = dC[dlin].double().cpu().numpy()
+                del dA, dB, dC
+            plan.close()
+            torch.cuda.empty_cache()
+            rows.append(row)
+        out.append({"spec": spec, "extents": ext, "bound": bound, "points": pts, "inputs": inputs, "rows": rows})
+    return out
+
+
+def finish_precision(prec, threads):
+    """CPU leg: errors of every form against the FP64 oracle at the sampled
+    points.  The oracle runs on the data as the user holds it: FP64 for the
+    FP64 form, the FP32 values for every other form (so rounding the inputs
+    to BF16 / FP16 / TF32 counts as error)."""
+    out = []
+    for w in prec:
+        spec, ext = w["spec"], w["extents"]
+        ref = {}
+        for dist_name, (A, B) in w["inputs"].items():
+            A32, B32 = A.astype(np.float32).astype(np.float64), B.astype(np.float32).astype(np.float64)
+            ref[dist_name] = {"f64": oracle_points(spec, ext, A, B, w["points"], threads),
+                              "f32": oracle_points(spec, ext, A32, B32, w["points"], threads)}
+        rows = []
+        for row in w["rows"]:
+            key = "f64" if row["form"].startswith("f64") else "f32"
+            errs = {d: max_rel_err(row["samples"][d], *ref[d][key]) for d in row["samples"]}
+            r = {k: v for k, v in row.items() if k != "samples"}
+            r["max_rel_err"] = errs
+            rows.append(r)
+        chosen = rows[0]
+        f64 = next(r for r in rows if r["form"].startswith("f64"))
+        entry = {"workload": f"{spec} {ext}, inputs uniform[-1,1] (seed 0) and lognormal per-slice scales (seed 1)",
+                 "bound": w["bound"], "forms": rows,
+                 "chosen": {"form": chosen["form"], "ms": chosen["ms"], "gflops": chosen["gflops"],
+                            "max_rel_err": chosen["max_rel_err"],
+                            "speedup_vs_f64": f64["ms"] / chosen["ms"]}}
+        if w["bound"] == "hbm":
+            entry["chosen"]["roofline"] = {"bound": "hbm", "frac": chosen["hbm_frac"],
+                                           "unit": "of MEASURED_PEAKS hbm_gbs (compulsory bytes A+B+C)"}
+        else:
+            entry["chosen"]["roofline"] = {"bound": "tensor", "frac": chosen["tensor_frac"],
+                                           "unit": "of MEASURED_PEAKS bf16_tflops (6 products x F)"}
+        out.append(entry)
+    return out
+
+
+def run_batched(args):
+    from paper_1409_8608_gb300 import batch_report
+    out = {}
+    for bdt, label in (("bf16x3", "split-BF16 x6 on the tensor-core GETT tiles"), ("f32", "FP32 SIMT")):
+        b = batch_report.run(4096, bdt, seed=0, reps=10, hbm_gbs=measured_peaks()["hbm_gbs"])
+        out[bdt] = {
+            "workload": f"4096 x abc=ai,ibc, a,b,c log-uniform [8,128], i in {{4,8,16,32}}, {label}",
+            "gflops": b["tuned"]["gflops"], "ms": b["tuned"]["ms"],
+            "roofline": {"bound": "hbm", "achieved": b["tuned"]["gbs"], "peak": measured_peaks()["hbm_gbs"],
+                         "unit": "GB/s", "frac": b["tuned"]["hbm_frac"],
+                         "work": f"compulsory bytes A+B+C once = {b['compulsory_gb']:.2f} GB"},
+            "tiles": b["tuned"]["tiles"], "fixed_tiles_ms": b["untuned"]["ms"],
+            "graph_ms": b["graph"]["ms"], "launch_per_problem_ms": b["launch_per_problem"]["ms"]}
+    return out
+
+
+def run_serving(args):
+    from paper_1409_8608_gb300 import serve_report
+    main = serve_report.run(seconds=args.serve_seconds, warmup=1.0, rate=2000.0, seed=0, check_samples=8)
+    sweep = []
+    for rate in (500.0, 1000.0, 1500.0):
+        r = serve_report.run(seconds=3.0, warmup=0.5, rate=rate, seed=1)
+        sweep.append({k: r[k] for k in ("rate_per_s", "offered_gflops", "served_gflops", "p50_ms", "p99_ms",
+                                        "failed")})
+    sweep.append({k: main[k] for k in ("rate_per_s", "offered_gflops", "served_gflops", "p50_ms", "p99_ms",
+                                       "failed")})
+    sustainable = max([s["rate_per_s"] for s in sweep if s["served_gflops"] >= 0.95 * s["offered_gflops"]
+                       and s["failed"] == 0] or [0.0])
+    main["rate_sweep"] = sweep
+    main["sustainable_rate_per_s"] = sustainable
+    return main
 
 
 def run_gpu(args):
@@ -231,230 +659,107 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
 
     A, B, _ = synth.uniform_operands(SPEC, EXTENTS, seed=rank)
-    res = measure_form(args, args.dtype, args.alg, A, B, dev, stream, dist, world, tc)
-    plain = None
-    if args.dtype != "f64" and not args.no_plain:
-        plain = measure_form(args, "f64", "gett", A, B, dev, stream, dist, world, tc,
-                             steps=min(args.steps, 5), e2e=False)
+    pts, lin = sample_points(SPEC, EXTENTS, 4000, seed=11)
+    with torch.cuda.stream(stream):
+        head, head_samples = measure_form(args, "f64", SPEC, EXTENTS, A, B, dev, stream, dist, world, tc,
+                                          args.steps, sample_lin=lin)
+        forms = {}
+        samples = {}
+        if not args.quick:
+            for dt in ("f32", "bf16x3"):
+                forms[dt], samples[dt] = measure_form(
+                    args, dt, SPEC, EXTENTS, A, B, dev, stream, dist, world, tc, min(args.steps, 10),
+                    e2e=(dt == "bf16x3"), sample_lin=lin, clocks=(dt == "bf16x3"))
+    extras = {}
+    if rank == 0 and world == 1 and not args.quick:
+        with torch.cuda.stream(stream):
+            extras["small"] = run_small(tc)
+            extras["ranking"] = run_ranking(tc)
+            prec = run_precision(tc, dev, stream)
+        torch.cuda.synchronize()
+        extras["batched"] = run_batched(args)
+        extras["serving"] = run_serving(args)
     if rank == 0:
-        line = dict(res["line"])
-        line["n_gpus"] = world
-        if plain is not None:
-            pl = plain["line"]
-            line["plain_f64"] = {"value": pl["value"], "unit": "GFLOP/s", "algorithm": "gett",
-                                 "ms_per_step": pl["ms_per_step"], "roofline": pl["roofline"],
-                                 "speedup_of_chosen": line["value"] / pl["value"]}
-        if world == 1 and not args.no_extras:
-            from paper_1409_8608_gb300 import batch_report, serve_report
-            torch.cuda.synchronize()
-            line["batched"] = {}
-            for bdt, label in (("bf16x3", "split-BF16 x6 (tensor-core GETT tiles)"), ("f32", "FP32 (SIMT)")):
-                b = batch_report.run(4096, bdt, seed=0, reps=10, hbm_gbs=measured_peaks()["hbm_gbs"])
-                line["batched"][bdt] = {
-                    "workload": f"4096 x abc=ai,ibc, a,b,c log-uniform [8,128], i in {{4,8,16,32}}, {label}",
-                    "gflops": b["tuned"]["gflops"], "ms": b["tuned"]["ms"],
-                    "hbm_frac": b["tuned"]["hbm_frac"], "untuned_ms": b["untuned"]["ms"],
-                    "graph_ms": b["graph"]["ms"], "launch_per_problem_ms": b["launch_per_problem"]["ms"]}
-            sv = serve_report.run(seconds=args.serve_seconds, rate=2000.0, seed=0)
-            line["serving"] = {"workload": "Poisson 2000 req/s, specs ai,ibc / iaj,jbic / aij,jib, FP64:FP32:BF16X3 = 1:2:2, 40 GB",
-                               "seconds_of_arrivals": args.serve_seconds, "requests": sv["requests"],
-                               "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"],
-                               "served_gflops": sv["served_gflops"], "offered_gflops": sv["offered_gflops"],
-                               "failed": sv["failed"], "admission_stalls": sv["admission_stalls"]}
-        if world == 1 and not args.no_cpu:
-            from oracle import contraction as oc
-            A64, B64, C64, cores, nsl = cpu_oracle_sample(target_s=args.cpu_seconds)
-            t0 = time.perf_counter()
-            oc.contract(SPEC, EXTENTS, A64, B64, C=C64, outer_range=(0, nsl), threads=cores)
-            dt = time.perf_counter() - t0
-            fs = flops_of([N_FREE, N_FREE, nsl, N_CONTR, N_CONTR])
-            line["cpu_baseline"] = {
-                "value": fs / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-                "sample": f"FP64 oracle on a slab of c = {nsl} of {N_FREE} ({fs / 1e9:.2f} GFLOP, {dt:.1f} s)"}
+        line = {"metric": METRIC, "value": head["value"], "unit": "GFLOP/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "algorithm": "gett (SIMT DFMA tiles)",
+                           "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (no flush needed)"},
+                "roofline": head["roofline"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
+                "clocks": head["clocks"]}
+        threads = len(os.sched_getaffinity(0))
+        if not args.no_cpu and world == 1:
+            # CPU leg: expected values of sampled outputs, then the baselines
+            A32 = A.astype(np.float32).astype(np.float64)
+            B32 = B.astype(np.float32).astype(np.float64)
+            ref64 = oracle_points(SPEC, EXTENTS, A, B, pts, threads)
+            line["max_rel_err"] = max_rel_err(head_samples, *ref64)
+            if forms:
+                ref32 = oracle_points(SPEC, EXTENTS, A32, B32, pts, threads)
+                for dt in forms:
+                    forms[dt]["max_rel_err"] = max_rel_err(samples[dt], *ref32)
+            line["cpu_baseline"] = cpu_baseline_line(SPEC, EXTENTS, args.cpu_seconds)
         else:
             line["cpu_baseline"] = None
+        if forms:
+            forms["bf16x3"]["form"] = "chosen: split-BF16 x6 slice products on tcgen05, FP32 I/O"
+            forms["bf16x3"]["speedup_vs_f64"] = forms["bf16x3"]["value"] / head["value"]
+            forms["f32"]["form"] = "FP32 SIMT (FFMA tiles)"
+            line["forms"] = forms
+        if extras:
+            if not args.no_cpu:
+                extras["precision"] = finish_precision(prec, threads)
+                extras["batched"]["cpu_baseline"] = cpu_batch_baseline(
+                    __import__("paper_1409_8608_gb300.batch_report", fromlist=["problems"]).problems(4096, 0),
+                    min(8.0, args.cpu_seconds), threads)
+                extras["serving"]["cpu_baseline"] = cpu_serving_baseline(
+                    extras["serving"].pop("sampled_requests", []), min(8.0, args.cpu_seconds), threads)
+            line.update(extras)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
 
 
-def launch_estimate(plan, step, stream):
-    """Seconds per step from two timed warm steps."""
-    import torch
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    step()
-    step()
-    e1.record(stream)
-    e1.synchronize()
-    return e0.elapsed_time(e1) / 2e3
-
-
-TORCH_IN = {"f64": "float64", "f32": "float32", "tf32": "float32", "bf16x3": "float32",
-            "bf16": "bfloat16", "f16": "float16"}
-TENSOR_FORMS = ("tf32", "bf16", "f16", "bf16x3")
-
-
-def measure_form(args, dtype, alg_name, A, B, dev, stream, dist, world, tc, steps=None, e2e=True):
-    """Times one form (dtype + algorithm) of the workload; returns its line."""
-    import torch
-    steps = steps or args.steps
-    tin = getattr(torch, TORCH_IN[dtype])
-    tout = torch.float64 if dtype == "f64" else torch.float32
-    nC = N_FREE ** 3
-    plan = tc.Plan(SPEC, EXTENTS, dtype=dtype)
-    if dtype == "bf16x3":
-        plan.set_split(args.products)
-    if dtype in TENSOR_FORMS and args.bn:
-        plan.set_gett_tile(args.bn)
-    algs = {a["name"]: a for a in plan.algorithms()}
-    alg = algs[alg_name]
-    plan.select(alg["id"])
-    hA = torch.from_numpy(A).to(tin).pin_memory()
-    hB = torch.from_numpy(B).to(tin).pin_memory()
-    hC = torch.empty(nC, dtype=tout).pin_memory()
-    dA = hA.to(dev)
-    dB = hB.to(dev)
-    dC = torch.empty(nC, dtype=tout, device=dev)
-    flops = plan.flops
-    # GETT: one kernel, plus the pre-pass when the plan pre-converts its
-    # smaller input (the only GETT workspace)
-    launches_per_step = 1 + (plan.workspace(alg["id"]) > 0) if alg["kernel"] == "gett" else alg["n_phases"] + sum(
-        1 for lv in alg["copy_level"] if lv != -2) * alg["n_phases"]
-
-    def step():
-        plan.execute(dA, dB, dC, alpha=1.0, beta=0.0, stream=stream)
-
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step()
-    args_steps = steps
-    torch.cuda.synchronize()
-    plan.device_status()
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args_steps)]
-    # untimed load around the timed region (about 0.3 s before and after),
-    # so that the clock sampler sees the clocks the timed steps run at
-    pad = max(1, int(0.3 / max(1e-4, launch_estimate(plan, step, stream))))
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        for _ in range(pad):
-            step()
-        t_begin = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_begin.record(stream)
-        for k in range(args_steps):
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-        t_end.record(stream)
-        for _ in range(pad):
-            step()
-        torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    plan.device_status()
-    total_ms = t_begin.elapsed_time(t_end)
-    per_launch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev) / max(1, launches_per_step)
-    total_ms, ms_per_step, value = aggregate_over_ranks(total_ms, args_steps, flops, world, dist, dev)
-
-    # end to end through the public call: pinned host inputs -> device,
-    # execute, result back to pinned host memory, every step.  Two streams
-    # with their own device buffers take alternate steps, so one step's
-    # result copy overlaps the next step's input copies and execute (each
-    # step still copies all of its inputs and its whole result).
-    e2e_steps = max(4, min(args_steps, 8)) if e2e else 0
-    lanes = [(stream, dA, dB, dC, hC, plan)]
-    if e2e_steps:
-        # the second stream gets its own plan (a plan's workspace serves one
-        # stream at a time), set up and run once outside the timed region
-        plan2 = tc.Plan(SPEC, EXTENTS, dtype=dtype)
-        if dtype == "bf16x3":
-            plan2.set_split(args.products)
-        if dtype in TENSOR_FORMS and args.bn:
-            plan2.set_gett_tile(args.bn)
-        plan2.select(alg["id"])
-        lanes.append((torch.cuda.Stream(device=dev), torch.empty_like(dA), torch.empty_like(dB),
-                      torch.empty_like(dC), torch.empty_like(hC).pin_memory(), plan2))
-        with torch.cuda.stream(lanes[1][0]):
-            plan2.execute(dA, dB, lanes[1][3], alpha=1.0, beta=0.0, stream=lanes[1][0])
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for st, *_ in lanes[1:]:
-        st.wait_event(e0)
-    for k in range(e2e_steps):
-        st, a, b, c, hc, pl = lanes[k % len(lanes)]
-        with torch.cuda.stream(st):
-            a.copy_(hA, non_blocking=True)
-            b.copy_(hB, non_blocking=True)
-            pl.execute(a, b, c, alpha=1.0, beta=0.0, stream=st)
-            hc.copy_(c, non_blocking=True)
-    for st, *_ in lanes[1:]:
-        done = torch.cuda.Event()
-        done.record(st)
-        stream.wait_event(done)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_value = None
-    if e2e_steps:
-        e2e_ms = e0.elapsed_time(e1) / e2e_steps
-        e2e_value = flops * world / (e2e_ms / 1e3) / 1e9
-        lanes[1][5].close()
-
-    peaks = measured_peaks()
-    launch_s = per_launch_ms * launches_per_step / 1e3
-    if dtype in TENSOR_FORMS:
-        products = args.products if dtype == "bf16x3" else 1
-        work = flops * products
-        peak_tf = peaks["bf16_tflops"] * (0.5 if dtype == "tf32" else 1.0)
-        achieved_tf = work / launch_s / 1e12
-        tkey = f"gett_tc_kernel/{dtype}/{SPEC}/{N_FREE}" + (f"/p{products}" if dtype == "bf16x3" else "")
-        roofline = {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                    "frac": achieved_tf / peak_tf,
-                    "traffic": captured_traffic(tkey, "paper_1409_8608_gb300/csrc/tc_gett.cu"),
-                    "algorithmic_bytes": int(hA.numel() * hA.element_size() + hB.numel() * hB.element_size()
-                                             + hC.numel() * hC.element_size()),
-                    # with the pre-pass the events time both kernels of the step
-                    "kernel": "gett_tc_kernel" + (" + pack_kernel (timed together)" if launches_per_step == 2 else ""),
-                    "work": f"{products} slice products x 2*prod(extents) = {work / 1e9:.1f} GFLOP per launch",
-                    "peak_source": "MEASURED_PEAKS bf16_tflops (burst)" + (" x 0.5 (TF32 nominal ratio)" if dtype == "tf32" else "")
-                    + (" (fallback)" if peaks.get("fallback") else " (measured)")}
-    else:
-        achieved_tf = flops / launch_s / 1e12
-        peak_tf = ALU_PEAK_TFLOPS[dtype]
-        tkey = f"tile_kernel/{dtype}/{SPEC}/{N_FREE}"
-        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                    "frac": achieved_tf / peak_tf,
-                    "traffic": captured_traffic(tkey, "paper_1409_8608_gb300/csrc/tc_exec.cu"),
-                    "kernel": "tile_kernel" if alg["kernel"] in ("gett", "gemm") else "elementwise_kernel",
-                    "peak_source": f"derived: 152 SMs x {'2 DFMA' if dtype == 'f64' else '128 FFMA'}/clk x 2 x 2070 MHz"}
+def run_reference(args):
+    from oracle import contraction as oc
+    from paper_1409_8608_gb300 import synth
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    cores = len(os.sched_getaffinity(0))
+    if oc.max_threads() > 0:
+        cores = min(cores, oc.max_threads())
+    target = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    _, _, nsl, last, _ = cpu_oracle_slab(SPEC, EXTENTS, target, cores)
+    A, B, _ = synth.uniform_operands(SPEC, EXTENTS, seed=0)
+    C = np.zeros(synth.dense_sizes(SPEC, EXTENTS)[0])
+    f_slab = flops_of(EXTENTS) * nsl / last
+    for _ in range(args.warmup):
+        oc.contract(SPEC, EXTENTS, A, B, C=C, outer_range=(0, nsl), threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oc.contract(SPEC, EXTENTS, A, B, C=C, outer_range=(0, nsl), threads=cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = f_slab * args.steps / total / 1e9
+    sample = f"c-slab of {nsl} of {last} slices ({f_slab / 1e9:.2f} GFLOP) per step"
     line = {
-        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
-        "steps": args_steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": dtype, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "algorithm": alg["name"],
-                   "form": ("split-BF16 x%d products, FP32 I/O" % args.products) if dtype == "bf16x3" else f"{dtype}",
-                   "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (no flush needed)"},
-        "roofline": roofline,
-        "e2e": None if e2e_value is None else {
-            "value": e2e_value, "unit": "GFLOP/s",
-            "h2d_bytes_per_step": int(hA.numel() * hA.element_size() + hB.numel() * hB.element_size()),
-            "d2h_bytes_per_step": int(hC.numel() * hC.element_size()),
-            "pipelining": "2 streams, alternate steps, own device buffers"},
-        "gpu_launches": int(args_steps * launches_per_step),
-        "clocks": clk.summary(),
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "FP64 CPU oracle (plain nested loops, OpenMP)",
+                   "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    plan.close()
-    return {"line": line}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def main():
@@ -462,16 +767,11 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--dtype", default="bf16x3", choices=["f64", "f32", "tf32", "bf16", "f16", "bf16x3"])
-    ap.add_argument("--products", type=int, default=6)
-    ap.add_argument("--bn", type=int, default=0, help="tensor-core GETT tile width (0: auto)")
-    ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
-    ap.add_argument("--serve-seconds", type=float, default=1.0)
-    ap.add_argument("--alg", default="gett")
+    ap.add_argument("--quick", action="store_true", help="the headline form only (no other forms or workloads)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--impl", default="tc", choices=["tc", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--n", type=int, default=512, help="free extent a=b=c (512 = the workload)")
     args = ap.parse_args()
     if args.n != 512:

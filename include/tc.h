@@ -187,6 +187,22 @@ tc_status tc_execute(tc_plan plan, const void *alpha, const void *A,
 tc_status tc_execute_no_alloc(tc_plan plan, const void *alpha, const void *A,
                               const void *B, const void *beta, void *C, void *stream);
 
+/* tc_execute for operands in host memory (no paper counterpart): the
+ * call a host program makes end to end.  Enqueued on `stream`, in order:
+ * copies of hA and hB (and of hC when beta != 0) into device buffers the
+ * plan owns, the selected algorithm as tc_execute runs it, and the copy of
+ * C back into hC.  Returns once everything is enqueued: synchronise the
+ * stream before reading hC or changing hA / hB.  hA, hB, hC use the plan's
+ * layouts (the strides given at tc_plan_create; each buffer spans
+ * 1 + sum (extent - 1) * stride elements) and element types.  Pinned host
+ * memory (cudaHostAlloc / cudaHostRegister) keeps the copies asynchronous;
+ * pageable memory works, but its copies block the calling thread.  The
+ * device buffers are allocated by the first call (do not make it during a
+ * stream capture) and kept until tc_plan_destroy.  The one-stream-at-a-time
+ * rule of tc_execute applies, and is checked before any copy is queued. */
+tc_status tc_execute_host(tc_plan plan, const void *alpha, const void *hA, const void *hB,
+                          const void *beta, void *hC, void *stream);
+
 /* Reads and clears the plan's device status word (waits for the stream
  * the plan last ran on): TC_SUCCESS or TC_ERROR_TIMEOUT. */
 tc_status tc_plan_device_status(tc_plan plan);
@@ -222,6 +238,25 @@ tc_status tc_plan_set_gett_tma(tc_plan plan, int32_t enable);
  * on tc_plan_set_gett_tma: both input paths give the same bits.  With
  * pre-conversion an execute launches two kernels (pre-pass, GETT). */
 tc_status tc_plan_set_gett_pack(tc_plan plan, int32_t mode);
+
+/* Tensor-core GETT, FP32-input kinds (TC_BF16X3, TC_TF32): CTA pairs.
+ * With 1 (default) and where the launch allows it (256-column tiles, no
+ * compensated accumulation, more than 128 rows of M, every input staged by
+ * TMA or pre-converted), clusters of two CTAs share each MMA
+ * (tcgen05.mma.cta_group::2, M = 256): each CTA stages and converts its 128
+ * rows of A and half of the tile's 256 rows of B, so a CTA moves half the
+ * B bytes per MMA; 0 keeps one CTA per tile.  Results are the same bits
+ * either way.  Other values give TC_ERROR_INVALID_ARGUMENT. */
+tc_status tc_plan_set_gett_pair(tc_plan plan, int32_t enable);
+
+/* TC_BF16X3, tensor-core GETT without compensation: split accumulators.
+ * With 1 (default) the weight-1 slice product (0,0) accumulates in one
+ * tensor-memory accumulator and the smaller products in a second one, added
+ * once in the epilogue: only K/16 FP32 roundings then act on the magnitude
+ * of the whole sum instead of 6K/16, at the cost of not double-buffering
+ * the accumulators.  0: one accumulator for every product.  Other values
+ * give TC_ERROR_INVALID_ARGUMENT. */
+tc_status tc_plan_set_split_accumulators(tc_plan plan, int32_t enable);
 
 /* Failure-detection self-test (no paper counterpart).  Launches one CTA on
  * `stream` whose thread 0 waits on an mbarrier with the bounded wait every

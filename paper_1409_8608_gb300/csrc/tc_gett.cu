@@ -109,6 +109,7 @@ struct GettDesc {
     int spb;             // K stages per TMA box: 1 (16 K positions) or 2 (32)
     double tile_frac;    // micro-benchmark: run this fraction of the tiles
     int chunk_stages;    // compensated form: K stages per TMEM chunk
+    int split;           // split-BF16: (0,0) products in their own accumulator
     // batched form: per-problem descriptors (num_tiles, status, nprod,
     // alpha, beta and init are the batch's, in this descriptor), the
     // problem of each tile, and each problem's first tile
@@ -238,6 +239,83 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
+// ---- CTA pairs (cta_group::2): two CTAs of a cluster of two share each MMA.
+// The pair's MMA is M = 256: each CTA holds 128 rows of A and half of the
+// B tile in its own shared memory (at the same offsets), and each CTA's
+// tensor memory receives its 128 rows of the accumulator.  One thread of
+// the even CTA issues the MMAs; its commits arrive on both CTAs' barriers.
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Every thread of both CTAs: release this CTA's prior writes, acquire the
+// peer's.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The shared::cluster address of the same shared-memory offset in CTA `rank`.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// Arrival on an mbarrier of another CTA of the cluster (release at cluster
+// scope: this thread's prior shared-memory writes are visible to a thread
+// that acquires the barrier's phase).
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait_cl(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait that acquires at cluster scope (barriers other CTAs of the
+// pair arrive on); false when the limit expired.
+__device__ __forceinline__ bool mbar_wait_cl(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait_cl(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait_cl(bar, parity)) {
+        if (globaltimer() - t0 > kWaitLimitNs) return false;
+    }
+    return true;
+}
+
+// One warp of each CTA of the pair allocates collectively; the address is
+// the same in both CTAs.
+__device__ __forceinline__ void tmem_alloc2(uint32_t *dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc2(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Commit of the pair's MMAs issued so far by this thread: arrives once on
+// the barrier at this shared-memory offset in every CTA of `mask`.
+__device__ __forceinline__ void mma_commit2(uint64_t *bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
 // Shared-memory matrix descriptor, no swizzle, K-major: core matrices of
 // 8 rows x 16 bytes; lbo = byte distance between core matrices adjacent in
 // K, sbo = byte distance between adjacent 8-row groups.
@@ -250,10 +328,24 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return d;                // base offset 0, swizzle none
 }
 
-template <int KIND>
+template <int KIND, bool PAIR = false>
 __device__ __forceinline__ void mma_issue(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
-    if constexpr (KIND == GK_TF32) {
+    if constexpr (PAIR && KIND == GK_TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.u32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else if constexpr (PAIR) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.u32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else if constexpr (KIND == GK_TF32) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.u32 p, %4, 0;\n\t"
@@ -303,6 +395,33 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Two 32-column loads (the split accumulators) and their FP32 sum: both
+// loads and the wait in one statement, so no use of the registers can be
+// scheduled before the wait.
+__device__ __forceinline__ void tmem_ld32_sum(uint32_t ta, uint32_t tb, uint32_t (&r)[32]) {
+    uint32_t a[32], b[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
+          "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]),
+          "=r"(a[16]), "=r"(a[17]), "=r"(a[18]), "=r"(a[19]), "=r"(a[20]), "=r"(a[21]), "=r"(a[22]), "=r"(a[23]),
+          "=r"(a[24]), "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), "=r"(a[28]), "=r"(a[29]), "=r"(a[30]), "=r"(a[31]),
+          "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]),
+          "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15]),
+          "=r"(b[16]), "=r"(b[17]), "=r"(b[18]), "=r"(b[19]), "=r"(b[20]), "=r"(b[21]), "=r"(b[22]), "=r"(b[23]),
+          "=r"(b[24]), "=r"(b[25]), "=r"(b[26]), "=r"(b[27]), "=r"(b[28]), "=r"(b[29]), "=r"(b[30]), "=r"(b[31])
+        : "r"(ta), "r"(tb)
+        : "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__fadd_rn(__uint_as_float(a[j]), __uint_as_float(b[j])));
+}
+
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
@@ -350,18 +469,20 @@ struct KindTraits {
 // STAGES: depth of the operand ring (converted tiles the MMA reads);
 // SSTG: depth of the TMA staging ring (0 = no TMA staging).  The staging
 // ring is the deeper one: it covers the load latency.
-template <int KIND, int BN, int STAGES, int BK, int SSTG, bool BATCH = false>
+// PAIR: a CTA of a pair holds half of the B tile (BN / 2 rows).
+template <int KIND, int BN, int STAGES, int BK, int SSTG, bool BATCH = false, bool PAIR = false>
 struct SmemPlan {
     static constexpr bool TMA = SSTG > 0;
     static constexpr int kSstg = SSTG > 0 ? SSTG : 1;         // slots of two-stage boxes
+    static constexpr int kBNL = PAIR ? BN / 2 : BN;            // B rows held by this CTA
     using T = KindTraits<KIND, BK>;
     static constexpr int kATile = kBM * BK * T::kElemBytes;    // one slice
-    static constexpr int kBTile = BN * BK * T::kElemBytes;
+    static constexpr int kBTile = kBNL * BK * T::kElemBytes;
     static constexpr int kStage = T::kSlices * (kATile + kBTile);
     static constexpr int kOpBytes = STAGES * kStage;
     // staged input boxes cover up to kBoxK K positions (two stages)
     static constexpr int kStgA = TMA ? kBM * kBoxK * T::kInBytes : 0;
-    static constexpr int kStgB = TMA ? BN * kBoxK * T::kInBytes : 0;
+    static constexpr int kStgB = TMA ? kBNL * kBoxK * T::kInBytes : 0;
     static constexpr int kStgBytes = SSTG * (kStgA + kStgB);
     // K-offset and row-offset tables of the global-load path: per stage slot
     // (or, in the batched form, per converter group and double-buffered)
@@ -632,13 +753,23 @@ __device__ __forceinline__ void store_cols(const uint32_t (&r)[W], float *__rest
 // (hi, lo) kept in TMEM (TwoSum), so the FP32 rounding of the accumulator
 // grows with the chunk length instead of with K.
 // BATCH: the tiles of many problems in one launch (global-load inputs).
-template <int KIND, int BN, int STAGES, int BK, int SSTG, bool COMP, bool BATCH>
+// PAIR: clusters of two CTAs share each MMA (cta_group::2, M = 256): a tile
+// is 256 x BN; each CTA stages and converts its 128 rows of A and half of
+// the BN rows of B, and its tensor memory holds its 128 rows of C.
+// d.split (split-BF16, not COMP): the weight-1 slice product (0,0)
+// accumulates in one tensor-memory accumulator and the smaller products
+// in another, added in the epilogue: only K/16 of the FP32 roundings happen
+// at the magnitude of the whole sum.  The two take both halves of the
+// tensor memory, so the accumulators are not double-buffered then.
+template <int KIND, int BN, int STAGES, int BK, int SSTG, bool COMP, bool BATCH, bool PAIR = false>
 __global__ void __launch_bounds__(kThreads, 1)
 gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
     using T = KindTraits<KIND, BK>;
-    using SP = SmemPlan<KIND, BN, STAGES, BK, SSTG, BATCH>;
+    using SP = SmemPlan<KIND, BN, STAGES, BK, SSTG, BATCH, PAIR>;
+    static_assert(!(PAIR && (COMP || BATCH)), "CTA pairs: plain tensor-core GETT only");
     constexpr bool TMA = SP::TMA;
     constexpr int SS = SP::kSstg;
+    constexpr int BNL = SP::kBNL;  // B rows this CTA stages and converts
     using In = typename T::In;
     extern __shared__ __align__(1024) char smem[];
     char *ops = smem;
@@ -666,6 +797,28 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     const int nkt = (int)((d.K + BK - 1) / BK);
     constexpr uint32_t kTmemCols = COMP ? 4 * BN : 2 * BN;
     static_assert(kTmemCols <= 512, "tensor memory columns");
+    // pairs: this CTA's rank in its pair; a pair (or a lone CTA) is one
+    // slot of the persistent tile walk
+    const uint32_t crank = PAIR ? cluster_ctarank() : 0u;
+    const int64_t slot0 = PAIR ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;
+    const int64_t nslots = PAIR ? (int64_t)(gridDim.x >> 1) : (int64_t)gridDim.x;
+    // accumulators per tile: one (double-buffered) or the split pair
+    const bool split = !COMP && !BATCH && d.split != 0;
+    const int nbuf = split ? 1 : 2;
+    // barriers the other CTA of a pair arrives on are waited on with
+    // acquire at cluster scope; arrivals for the MMA issuer go to rank 0
+    auto bwait = [&](uint64_t *bar, uint32_t parity) -> bool {
+        if constexpr (PAIR) return mbar_wait_cl(bar, parity);
+        else return mbar_wait(bar, parity);
+    };
+    auto btry = [&](uint64_t *bar, uint32_t parity) -> bool {
+        if constexpr (PAIR) return mbar_try_wait_cl(bar, parity);
+        else return mbar_try_wait(bar, parity);
+    };
+    auto arrive_issuer = [&](uint64_t *bar) {
+        if constexpr (PAIR) mbar_arrive_remote(mapa_shared(smem_u32(bar), 0u));
+        else mbar_arrive(bar);
+    };
     // accumulation units per tile: one, or the K chunks of the compensated form
     const int cstg = COMP ? (d.chunk_stages > 0 ? d.chunk_stages : nkt) : nkt;
     const int nch = (nkt + cstg - 1) / cstg;
@@ -693,7 +846,8 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         // or the four of one group when the groups take turns
         const uint32_t conv_warps = grouped ? kProducerThreads / 32 / kConvGroups : kProducerThreads / 32;
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], conv_warps);
+            // pairs: both CTAs' converters arrive on rank 0's barrier
+            mbar_init(&full[s], conv_warps * (PAIR ? 2 : 1));
             mbar_init(&empty[s], 1);
         }
         // a staging slot is free again once every stage of its box is converted
@@ -704,7 +858,8 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], kEpiThreads / 32);  // one arrival per epilogue warp
+            // one arrival per epilogue warp (of both CTAs of a pair)
+            mbar_init(&tempty[b], kEpiThreads / 32 * (PAIR ? 2 : 1));
         }
         for (int r = 0; r < SP::kRecs; ++r) {
             mbar_init(&rfull[r], 1);
@@ -714,7 +869,14 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == kMmaWarp) tmem_alloc(tmem_slot, kTmemCols);
+    if constexpr (PAIR) {
+        // both CTAs run and their barriers are initialised before any
+        // arrival crosses the pair or the pair allocates tensor memory
+        cluster_sync_all();
+        if (warp == kMmaWarp) tmem_alloc2(tmem_slot, kTmemCols);
+    } else {
+        if (warp == kMmaWarp) tmem_alloc(tmem_slot, kTmemCols);
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -817,12 +979,15 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             // both rings have at least kConvGroups slots
             static_assert(!TMA || (STAGES >= kConvGroups && SSTG >= kConvGroups), "ring depth vs groups");
             const int gp = pt / kGT, ptg = pt % kGT;
-            for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x) {
+            for (int64_t tile = d.tile_begin + slot0; tile < d.num_tiles && !stop; tile += nslots) {
                 const char *pkt = nullptr;  // this tile's pre-converted images
                 if (d.pk) {
                     int64_t mt;
                     const int64_t nt = divmod(tile, d.tiles_m, mt);
-                    pkt = d.pk_base + (d.pk == 1 ? mt : nt) * d.pk_tile_bytes;
+                    // pairs: images of 128-row (A) or BN/2-row (B) tiles,
+                    // two per pair tile
+                    const int64_t it_ = d.pk == 1 ? mt : nt;
+                    pkt = d.pk_base + (PAIR ? 2 * it_ + crank : it_) * d.pk_tile_bytes;
                 }
                 for (int kt = 0; kt < nkt; ++kt, ++g) {
                     if ((int)(g % kConvGroups) != gp) continue;  // another group's stage
@@ -832,10 +997,10 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                     const int half = (int)(g - gb * spb_c);
                     const int ss = (int)(gb % NSL);
                     const uint32_t sph = (uint32_t)((gb / NSL) & 1);
-                    const bool e_ok = g < STAGES || mbar_try_wait(&empty[s], ph ^ 1u);
+                    const bool e_ok = g < STAGES || btry(&empty[s], ph ^ 1u);
                     const bool f_ok = mbar_try_wait(&sfull[ss], sph);
                     bool bad = false;
-                    if (!e_ok) bad = !mbar_wait(&empty[s], ph ^ 1u);
+                    if (!e_ok) bad = !bwait(&empty[s], ph ^ 1u);
                     if (!f_ok && !bad) bad = !mbar_wait(&sfull[ss], sph);
                     // named barriers 1, 3, 4, 5 (0: the whole CTA, 2: the epilogue)
                     bool quit;
@@ -861,19 +1026,19 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                         convert_staged<KIND, BK, kBM, kGT>(box, d.srow[0], d.sk[0] + half * BK, d.sk_vec4[0], stage,
                                                            SP::kATile, ptg);
                     if (d.pk != 2)
-                        convert_staged<KIND, BK, BN, kGT>(box + boxA, d.srow[1], d.sk[1] + half * BK, d.sk_vec4[1],
-                                                          stage + kPkA, SP::kBTile, ptg);
+                        convert_staged<KIND, BK, BNL, kGT>(box + boxA, d.srow[1], d.sk[1] + half * BK, d.sk_vec4[1],
+                                                           stage + kPkA, SP::kBTile, ptg);
                     if (d.pk) cp_async_wait_all();
                     fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) {
-                        mbar_arrive(&full[s]);
+                        arrive_issuer(&full[s]);
                         mbar_arrive(&sempty[ss]);
                     }
                 }
             }
         }
-        for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop && !grouped;
+        for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop && !grouped && !PAIR;
              tile += gridDim.x, ++it) {
             const GettDesc &P = tile_desc<BATCH>(d, tile);
             const int64_t lt = BATCH ? tile - P.tile0 : tile;
@@ -1001,14 +1166,16 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                 for (int o = 0; o < 2; ++o)
 #pragma unroll
                     for (int x = 0; x < kTmaRank; ++x) rc[o][x] = 0;
-                int64_t r = mt * kBM, v;
+                // pairs: this CTA's 128 rows of the 256-row tile, and its
+                // half of the tile's B rows
+                int64_t r = (PAIR ? 2 * mt + crank : mt) * kBM, v;
                 for (int m = 0; m < d.nm; ++m) {
                     r = divmod(r, d.m_ext[m], v);
 #pragma unroll
                     for (int x = 0; x < kTmaRank; ++x)
                         if (d.row_dim[0][m] == x) rc[0][x] = (int32_t)v;
                 }
-                r = nt * BN;
+                r = nt * BN + (PAIR ? crank * BNL : 0);
                 for (int m = 0; m < d.nn; ++m) {
                     r = divmod(r, d.n_ext[m], v);
 #pragma unroll
@@ -1039,7 +1206,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             };
             int32_t rc[2][kTmaRank];
             const int spb = d.spb > 1 ? d.spb : 1;  // g counts boxes here
-            for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x) {
+            for (int64_t tile = d.tile_begin + slot0; tile < d.num_tiles && !stop; tile += nslots) {
                 tile_rc(tile, rc);
                 for (int kt = 0; kt < nkt; kt += spb, ++g) {
                     const int s = (int)(g % NSL);
@@ -1063,10 +1230,13 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         __syncwarp();
     } else if (warp == kMmaWarp) {
         // ---------------------------------------------------------- MMA issuer
-        if (lane == 0) {
+        // (pairs: rank 0 issues for both CTAs; the other MMA warp only
+        // takes part in the tensor-memory allocation)
+        if (lane == 0 && crank == 0) {
+            constexpr uint32_t kM = PAIR ? 2 * kBM : kBM;
             constexpr uint32_t idesc = (1u << 4) | (T::kFmt << 7) | (T::kFmt << 10) |
-                                       ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
-            constexpr uint32_t lboA = (kBM / 8) * 128, lboB = (BN / 8) * 128;
+                                       ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+            constexpr uint32_t lboA = (kBM / 8) * 128, lboB = (BNL / 8) * 128;
             // slice pairs in product order (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
             // (1,2) (2,1) (2,2), one nibble per product
             constexpr uint64_t kPa = 0x221210100ull, kPb = 0x212012010ull;
@@ -1075,21 +1245,26 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             int64_t g = 0;
             int64_t u = 0;  // accumulation units (tiles, or K chunks of tiles)
             bool stop = false;
-            for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop; tile += gridDim.x) {
+            auto commit = [&](uint64_t *bar) {
+                if constexpr (PAIR) mma_commit2(bar, (uint16_t)3);  // both CTAs' barriers
+                else mma_commit(bar);
+            };
+            for (int64_t tile = d.tile_begin + slot0; tile < d.num_tiles && !stop; tile += nslots) {
                 const int nkt_t = BATCH ? (int)((tile_desc<BATCH>(d, tile).K + BK - 1) / BK) : nkt;
                 const int cstg_t = BATCH ? nkt_t : cstg, nch_t = BATCH ? 1 : nch;
                 for (int c = 0; c < nch_t && !stop; ++c, ++u) {
-                    const int buf = (int)(u & 1);
-                    if (u >= 2 && !mbar_wait(&tempty[buf], (uint32_t)(((u / 2) - 1) & 1))) {
+                    const int buf = (int)(u % nbuf);
+                    if (u >= nbuf && !bwait(&tempty[buf], (uint32_t)(((u / nbuf) - 1) & 1))) {
                         stop = true;
                         break;
                     }
                     tc_fence_after();
+                    // split: the (0,0) products at column 0, the others at BN
                     const uint32_t dt = tmem + (uint32_t)(buf * BN);
                     const int kt_end = min(nkt_t, (c + 1) * cstg_t);
                     for (int kt = c * cstg_t; kt < kt_end; ++kt, ++g) {
                         const int s = (int)(g % STAGES);
-                        if (*abort_flag || !mbar_wait(&full[s], (uint32_t)((g / STAGES) & 1))) {
+                        if (*abort_flag || !bwait(&full[s], (uint32_t)((g / STAGES) & 1))) {
                             stop = true;
                             break;
                         }
@@ -1103,12 +1278,16 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                                 const uint32_t qa = (uint32_t)(kPa >> (4 * q)) & 15u, qb = (uint32_t)(kPb >> (4 * q)) & 15u;
                                 uint64_t ad = smem_desc(sa + qa * SP::kATile + ks * 2 * lboA, lboA, 128);
                                 uint64_t bd = smem_desc(sb + qb * SP::kBTile + ks * 2 * lboB, lboB, 128);
-                                mma_issue<KIND>(dt, ad, bd, idesc, !(first && ks == 0 && q == 0));
+                                // each accumulator starts from zero with its own
+                                // first product of the unit
+                                const bool fresh = first && ks == 0 && q == (split && q > 0 ? 1 : 0);
+                                const uint32_t dq = split && q > 0 ? dt + (uint32_t)BN : dt;
+                                mma_issue<KIND, PAIR>(dq, ad, bd, idesc, !fresh);
                             }
                         }
-                        mma_commit(&empty[s]);
+                        commit(&empty[s]);
                     }
-                    mma_commit(&tfull[buf]);  // arrives when this unit's MMAs are done
+                    commit(&tfull[buf]);  // arrives when this unit's MMAs are done
                 }
             }
             if (stop) {
@@ -1116,7 +1295,8 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                 atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
             }
             // nothing issued may still run when the tensor memory is freed
-            mma_commit(drain);
+            if constexpr (PAIR) mma_commit2(drain, (uint16_t)1);
+            else mma_commit(drain);
             mbar_wait(drain, 0);
         }
         __syncwarp();
@@ -1125,7 +1305,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         const int et = threadIdx.x;  // 0..127 = accumulator row = TMEM lane
         int it = 0;
         int64_t u = 0;
-        for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles; tile += gridDim.x, ++it) {
+        for (int64_t tile = d.tile_begin + slot0; tile < d.num_tiles; tile += nslots, ++it) {
             const int nch_t = BATCH ? 1 : nch;
             float *__restrict__ C;
             int64_t *cn = cN + (it & 1) * BN;
@@ -1146,7 +1326,9 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                 C = P.C;
                 int64_t mt;
                 const int64_t nt = divmod(lt, P.tiles_m, mt);
-                const int64_t m0 = mt * kBM, n0 = nt * BN;
+                // pairs: this CTA's 128 rows of the 256-row tile; every CTA
+                // holds all BN columns of its rows
+                const int64_t m0 = (PAIR ? 2 * mt + crank : mt) * kBM, n0 = nt * BN;
                 // one stride across the tile's columns: no column table
                 nval = min((int64_t)BN, P.N - n0);
                 if (P.nn == 0) {
@@ -1186,8 +1368,8 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
             bool aborted = false;
             for (int c = 0; c < nch_t; ++c, ++u) {
-                const int buf = (int)(u & 1);
-                bool ok = mbar_wait(&tfull[buf], (uint32_t)((u / 2) & 1));
+                const int buf = (int)(u % nbuf);
+                bool ok = bwait(&tfull[buf], (uint32_t)((u / nbuf) & 1));
                 ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld needs the whole warp
                 if (!ok) {
                     *abort_flag = 1;
@@ -1199,12 +1381,22 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                 const uint32_t acc = tmem + lane_off + (uint32_t)(buf * BN);
                 const uint32_t hi = tmem + lane_off + (uint32_t)(2 * BN), lo = hi + (uint32_t)BN;
                 const bool last = c == nch_t - 1;
-if constexpr (!COMP) {
+                if constexpr (!COMP) {
+                    if (split) {
+                        // (0,0) products + the smaller ones, one rounding
 #pragma unroll 1
-                    for (int c0 = 0; c0 < BN; c0 += 64) {
-                        uint32_t r[64];
-                        tmem_ld64(acc + (uint32_t)c0, r);
-                        store_cols<64>(r, C, om, c0, lin, on0, nval, cn, d.alpha, d.beta, d.init);
+                        for (int c0 = 0; c0 < BN; c0 += 32) {
+                            uint32_t r[32];
+                            tmem_ld32_sum(acc + (uint32_t)c0, acc + (uint32_t)(BN + c0), r);
+                            store_cols<32>(r, C, om, c0, lin, on0, nval, cn, d.alpha, d.beta, d.init);
+                        }
+                    } else {
+#pragma unroll 1
+                        for (int c0 = 0; c0 < BN; c0 += 64) {
+                            uint32_t r[64];
+                            tmem_ld64(acc + (uint32_t)c0, r);
+                            store_cols<64>(r, C, om, c0, lin, on0, nval, cn, d.alpha, d.beta, d.init);
+                        }
                     }
                 } else {
 #pragma unroll 1
@@ -1255,14 +1447,22 @@ if constexpr (!COMP) {
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[buf]);
+                if (lane == 0) arrive_issuer(&tempty[buf]);
             }
             if (aborted) continue;
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == kMmaWarp) {
+    if constexpr (PAIR) {
+        // neither CTA frees its tensor memory or leaves while the pair's
+        // MMAs or the other CTA's arrivals may still reach it
+        cluster_sync_all();
+        if (warp == kMmaWarp) {
+            tc_fence_after();
+            tmem_dealloc2(tmem, kTmemCols);
+        }
+    } else if (warp == kMmaWarp) {
         tc_fence_after();
         tmem_dealloc(tmem, kTmemCols);
     }
@@ -1274,13 +1474,15 @@ if constexpr (!COMP) {
 // core-matrix layout, slice after slice -- with zeros for rows past the
 // extent and K positions past K.  One thread per 16-byte core-matrix row.
 template <int KIND>
-__global__ void __launch_bounds__(128) pack_kernel(const GettDesc d, int op, int rows, int bk, char *out) {
+__global__ void __launch_bounds__(128) pack_kernel(const GettDesc d, int op, int rows, int bk, int64_t rtiles,
+                                                   char *out) {
     using T = KindTraits<KIND, kBKT>;  // chunk and element size do not depend on BK
     constexpr int CH = T::kChunk;
     const int kcn = bk / CH;
     const int64_t nkt = (d.K + bk - 1) / bk;
     const int64_t R = op == 0 ? d.M : d.N;
-    const int64_t total = (R + rows - 1) / rows * nkt * kcn * rows;
+    // rtiles row tiles (the last ones may lie wholly past R: zeros)
+    const int64_t total = rtiles * nkt * kcn * rows;
     // let the GETT that depends on this grid launch now (its converters
     // wait for this grid's completion before reading the images)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -1330,14 +1532,14 @@ __global__ void __launch_bounds__(128) pack_kernel(const GettDesc d, int op, int
 // ------------------------------------------------------------------ host side
 int g_gett_sms = 0;
 
-template <int KIND, int BN, int STAGES, int BK, int SSTG, bool COMP = false, bool BATCH = false>
+template <int KIND, int BN, int STAGES, int BK, int SSTG, bool COMP = false, bool BATCH = false, bool PAIR = false>
 tc_status launch_gett(const GettDesc &d, const CUtensorMap &ta, const CUtensorMap &tb, cudaStream_t st) {
-    using SP = SmemPlan<KIND, BN, STAGES, BK, SSTG, BATCH>;
+    using SP = SmemPlan<KIND, BN, STAGES, BK, SSTG, BATCH, PAIR>;
     static_assert(SP::kTotal <= 227 * 1024, "shared memory budget");
     // at least 116 KB so that one CTA (and one tensor-memory allocation of
     // up to 512 columns) occupies each SM
     constexpr int kSmem = SP::kTotal > 116 * 1024 ? SP::kTotal : 116 * 1024;
-    auto kern = gett_tc_kernel<KIND, BN, STAGES, BK, SSTG, COMP, BATCH>;
+    auto kern = gett_tc_kernel<KIND, BN, STAGES, BK, SSTG, COMP, BATCH, PAIR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
     if (g_gett_sms == 0) {
@@ -1346,19 +1548,46 @@ tc_status launch_gett(const GettDesc &d, const CUtensorMap &ta, const CUtensorMa
         cudaDeviceGetAttribute(&g_gett_sms, cudaDevAttrMultiProcessorCount, dev);
         if (g_gett_sms <= 0) g_gett_sms = 1;
     }
-    const int64_t grid = std::min<int64_t>(d.num_tiles - d.tile_begin, g_gett_sms);
     // after a pre-pass (d.pk): programmatic stream serialization, so the
     // kernel's prologue and the TMA stream overlap the pre-pass
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = kSmem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchAttribute attr[2];
+    int na = 0;
+    if (!BATCH && d.pk) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
+    int64_t grid = std::min<int64_t>(d.num_tiles - d.tile_begin, g_gett_sms);
+    if constexpr (PAIR) {
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = 2;
+        attr[na].val.clusterDim.y = 1;
+        attr[na].val.clusterDim.z = 1;
+        ++na;
+        // one pair per two SMs that can hold one at the same time (the
+        // persistent walk assumes every pair is resident)
+        static int max_pairs = 0;
+        if (max_pairs == 0) {
+            cudaLaunchConfig_t q = cfg;
+            q.gridDim = dim3((unsigned)(2 * (g_gett_sms / 2)));
+            q.attrs = &attr[na - 1];
+            q.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, kern, &q) != cudaSuccess || n <= 0) {
+                cudaGetLastError();
+                n = g_gett_sms / 2;
+            }
+            max_pairs = std::min(n, g_gett_sms / 2);
+        }
+        grid = 2 * std::min<int64_t>(d.num_tiles - d.tile_begin, max_pairs);
+    }
+    cfg.gridDim = dim3((unsigned)grid);
     cfg.attrs = attr;
-    cfg.numAttrs = (!BATCH && d.pk) ? 1 : 0;
+    cfg.numAttrs = na;
     e = cudaLaunchKernelEx(&cfg, kern, d, ta, tb);
     if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
     e = cudaGetLastError();
@@ -1366,11 +1595,16 @@ tc_status launch_gett(const GettDesc &d, const CUtensorMap &ta, const CUtensorMa
 }
 
 template <int KIND>
-tc_status launch_kind(GettDesc &d, int bn, bool tma, bool comp, const CUtensorMap &ta, const CUtensorMap &tb,
-                      cudaStream_t st) {
+tc_status launch_kind(GettDesc &d, int bn, bool tma, bool comp, bool pair, const CUtensorMap &ta,
+                      const CUtensorMap &tb, cudaStream_t st) {
     d.tiles_n = (d.N + bn - 1) / bn;
     d.num_tiles = d.tiles_m * d.tiles_n;
     if (d.tile_frac < 1.0) d.num_tiles = std::max<int64_t>(1, (int64_t)(d.num_tiles * d.tile_frac));
+    // CTA pairs (tiles of 256 x 256): four operand stages of 128 + 128
+    // rows and three staging slots of two-stage boxes
+    if constexpr (KIND == GK_BF16X3 || KIND == GK_TF32) {
+        if (pair) return launch_gett<KIND, 256, 4, kBKT, 3, false, false, true>(d, ta, tb, st);
+    }
     // <KIND, BN, operand stages, BK, staging slots (boxes of up to two stages; 0 = no TMA)>
     if constexpr (KIND == GK_BF16X3) {
         if (comp) {  // 128 x 128 tiles: two chunk accumulators and (hi, lo) fill the tensor memory
@@ -1722,42 +1956,64 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     if (p.dtype == TC_BF16X3) comp_k = p.comp_chunk < 0 ? kCompChunkK : p.comp_chunk;
     const bool comp = comp_k > 0 && d.K > comp_k;
     if (comp) bn = 128;
-    // TMA staging for each operand TMA can describe (tiles of 128 x bn)
+    // TMA staging for each operand TMA can describe (tiles of 128 x bn, or
+    // in a CTA pair 128 rows of A and bn / 2 rows of B per CTA)
     CUtensorMap tmA, tmB;
     std::memset(&tmA, 0, sizeof(tmA));
     std::memset(&tmB, 0, sizeof(tmB));
     bool tma = false;
     d.spb = 1;
-    if (p.gett_tma && d.K < (int64_t(1) << 31)) {  // 32-bit K positions in the TMA warp
-        d.tma[0] = pk != 1 && plan_tma_operand(p, OP_A, A, in_bytes, kBM, d.nm, d.m_ext, d.m_sA, d.nk, d.k_ext,
-                                               d.k_sA, d, tmA, kBKT);
-        d.tma[1] = pk != 2 && plan_tma_operand(p, OP_B, B, in_bytes, bn, d.nn, d.n_ext, d.n_sB, d.nk, d.k_ext,
-                                               d.k_sB, d, tmB, kBKT);
-        tma = d.tma[0] || d.tma[1];
+    auto plan_tma = [&](GettDesc &dd, CUtensorMap &ma, CUtensorMap &mb, int brows) -> bool {
+        dd.tma[0] = pk != 1 && plan_tma_operand(p, OP_A, A, in_bytes, kBM, dd.nm, dd.m_ext, dd.m_sA, dd.nk, dd.k_ext,
+                                                dd.k_sA, dd, ma, kBKT);
+        dd.tma[1] = pk != 2 && plan_tma_operand(p, OP_B, B, in_bytes, brows, dd.nn, dd.n_ext, dd.n_sB, dd.nk,
+                                                dd.k_ext, dd.k_sB, dd, mb, kBKT);
+        bool any = dd.tma[0] || dd.tma[1];
         // boxes of two stages where the K modes allow them for at least as
         // many operands: each TMA box costs a fixed few hundred cycles on top
         // of its bytes, so fewer, larger boxes move more data per SM
-        if (d.K % kBoxK == 0 && d.K >= kTwoStageBoxMinK) {
-            GettDesc d2 = d;
+        if (dd.K % kBoxK == 0 && dd.K >= kTwoStageBoxMinK) {
+            GettDesc d2 = dd;
             CUtensorMap a2, b2;
             std::memset(&a2, 0, sizeof(a2));
             std::memset(&b2, 0, sizeof(b2));
-            const bool ta = pk != 1 && plan_tma_operand(p, OP_A, A, in_bytes, kBM, d.nm, d.m_ext, d.m_sA, d.nk,
-                                                        d.k_ext, d.k_sA, d2, a2, kBoxK);
-            const bool tb = pk != 2 && plan_tma_operand(p, OP_B, B, in_bytes, bn, d.nn, d.n_ext, d.n_sB, d.nk,
-                                                        d.k_ext, d.k_sB, d2, b2, kBoxK);
-            if ((ta || tb) && (int)ta + (int)tb >= (int)(bool)d.tma[0] + (int)(bool)d.tma[1]) {
-                d = d2;
-                d.tma[0] = ta;
-                d.tma[1] = tb;
-                tmA = a2;
-                tmB = b2;
-                d.spb = kBoxK / kBKT;
-                tma = true;
+            const bool ta = pk != 1 && plan_tma_operand(p, OP_A, A, in_bytes, kBM, dd.nm, dd.m_ext, dd.m_sA, dd.nk,
+                                                        dd.k_ext, dd.k_sA, d2, a2, kBoxK);
+            const bool tb = pk != 2 && plan_tma_operand(p, OP_B, B, in_bytes, brows, dd.nn, dd.n_ext, dd.n_sB, dd.nk,
+                                                        dd.k_ext, dd.k_sB, d2, b2, kBoxK);
+            if ((ta || tb) && (int)ta + (int)tb >= (int)(bool)dd.tma[0] + (int)(bool)dd.tma[1]) {
+                dd = d2;
+                dd.tma[0] = ta;
+                dd.tma[1] = tb;
+                ma = a2;
+                mb = b2;
+                dd.spb = kBoxK / kBKT;
+                any = true;
             }
         }
-        const int kpb = d.spb * kBKT;
-        d.tma_bytes = (uint32_t)((d.tma[0] ? kBM * kpb * in_bytes : 0) + (d.tma[1] ? bn * kpb * in_bytes : 0));
+        const int kpb = dd.spb * kBKT;
+        dd.tma_bytes = (uint32_t)((dd.tma[0] ? kBM * kpb * in_bytes : 0) + (dd.tma[1] ? brows * kpb * in_bytes : 0));
+        return any;
+    };
+    // CTA pairs: FP32-input tensor kinds on 256-wide tiles without
+    // compensation, more than one 128-row tile, and every operand either
+    // TMA-staged or pre-converted (the converters' grouped path)
+    bool pair = false;
+    if (p.gett_tma && d.K < (int64_t(1) << 31)) {  // 32-bit K positions in the TMA warp
+        if (p.gett_pair && (p.dtype == TC_BF16X3 || p.dtype == TC_TF32) && !comp && bn == 256 && d.M > kBM) {
+            GettDesc dp = d;
+            CUtensorMap pa, pb;
+            std::memset(&pa, 0, sizeof(pa));
+            std::memset(&pb, 0, sizeof(pb));
+            if (plan_tma(dp, pa, pb, bn / 2) && (dp.tma[0] || pk == 1) && (dp.tma[1] || pk == 2)) {
+                d = dp;
+                tmA = pa;
+                tmB = pb;
+                tma = true;
+                pair = true;
+            }
+        }
+        if (!pair) tma = plan_tma(d, tmA, tmB, bn);
     }
     if (comp) d.chunk_stages = (int)(comp_k / (tma ? kBKT : kBK));
     // global-load mappings (used by operands without TMA staging)
@@ -1778,17 +2034,21 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     d.init = d.beta == 0.0f ? 2 : 1;
     d.nprod = p.split_products;
     d.status = p.dev_status;
-    d.tiles_m = (d.M + kBM - 1) / kBM;
+    d.tiles_m = pair ? (d.M + 2 * kBM - 1) / (2 * kBM) : (d.M + kBM - 1) / kBM;
     d.tile_frac = probe ? probe->fraction : 1.0;
+    // split accumulators: split-BF16 without the compensated form
+    d.split = (p.dtype == TC_BF16X3 && !comp && p.gett_split != 0) ? 1 : 0;
     cudaStream_t st = (cudaStream_t)stream;
     if (pk) {
-        // the smaller input's stage images, for the stage depth the launch uses
+        // the smaller input's stage images, for the stage depth the launch
+        // uses; pairs read them as two images per pair tile (an even count)
         const int bkp = tma ? kBKT : kBK;
-        const int rows = pk == 1 ? kBM : bn;
+        const int rows = pk == 1 ? kBM : (pair ? bn / 2 : bn);
         const int64_t R = pk == 1 ? d.M : d.N;
         const int64_t nktp = (d.K + bkp - 1) / bkp;
         const int64_t stage_bytes = (int64_t)rows * bkp * (p.dtype == TC_TF32 ? 4 : 6);
-        const int64_t bytes = (R + rows - 1) / rows * nktp * stage_bytes;
+        const int64_t rtiles = pair ? 2 * ((R + 2 * rows - 1) / (2 * rows)) : (R + rows - 1) / rows;
+        const int64_t bytes = rtiles * nktp * stage_bytes;
         // bytes <= pk_bound: rows round up by less than 256, K by less than 32
         s = ensure_device_resources(p, (size_t)pk_bound);
         if (s != TC_SUCCESS) return s;
@@ -1797,16 +2057,18 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
         d.pk_tile_bytes = nktp * stage_bytes;
         const int64_t chunks = bytes / 16 / (p.dtype == TC_TF32 ? 1 : 3);  // one per 16-byte row of slice 0
         const unsigned grid = (unsigned)std::min<int64_t>((chunks + 127) / 128, 152 * 16);
-        if (p.dtype == TC_TF32) pack_kernel<GK_TF32><<<grid, 128, 0, st>>>(d, pk - 1, rows, bkp, (char *)p.workspace);
-        else pack_kernel<GK_BF16X3><<<grid, 128, 0, st>>>(d, pk - 1, rows, bkp, (char *)p.workspace);
+        if (p.dtype == TC_TF32)
+            pack_kernel<GK_TF32><<<grid, 128, 0, st>>>(d, pk - 1, rows, bkp, rtiles, (char *)p.workspace);
+        else
+            pack_kernel<GK_BF16X3><<<grid, 128, 0, st>>>(d, pk - 1, rows, bkp, rtiles, (char *)p.workspace);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
     }
     switch (p.dtype) {
-    case TC_BF16X3: return launch_kind<GK_BF16X3>(d, bn, tma, comp, tmA, tmB, st);
-    case TC_BF16: return launch_kind<GK_BF16>(d, bn, tma, comp, tmA, tmB, st);
-    case TC_F16: return launch_kind<GK_F16>(d, bn, tma, comp, tmA, tmB, st);
-    case TC_TF32: return launch_kind<GK_TF32>(d, bn, tma, comp, tmA, tmB, st);
+    case TC_BF16X3: return launch_kind<GK_BF16X3>(d, bn, tma, comp, pair, tmA, tmB, st);
+    case TC_BF16: return launch_kind<GK_BF16>(d, bn, tma, comp, false, tmA, tmB, st);
+    case TC_F16: return launch_kind<GK_F16>(d, bn, tma, comp, false, tmA, tmB, st);
+    case TC_TF32: return launch_kind<GK_TF32>(d, bn, tma, comp, pair, tmA, tmB, st);
     default: return fail(TC_ERROR_UNSUPPORTED_DTYPE, "dtype has no tensor-core GETT");
     }
 }

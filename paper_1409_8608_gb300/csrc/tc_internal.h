@@ -61,6 +61,8 @@ struct Plan {
     int gett_tma = 1;               // tensor-core GETT: TMA staging where legal
     int gett_pack = 1;              // tensor-core GETT: pre-convert the small input (0 never, 1 auto, 2 always)
     int comp_chunk = -1;            // TC_BF16X3: compensated K chunk (-1 default, 0 off)
+    int gett_pair = 0;              // tensor-core GETT: CTA pairs (cta_group::2) where legal
+    int gett_split = 1;             // TC_BF16X3: (0,0) products in their own accumulator
     // device resources, created lazily by the first execute
     int device = -1;
     void *workspace = nullptr;
@@ -68,6 +70,8 @@ struct Plan {
     int *dev_status = nullptr;      // bounded-wait status word
     void *last_stream = nullptr;
     void *busy_event = nullptr;     // recorded after each tc_execute (cudaEvent_t)
+    void *host_dev[3] = {nullptr, nullptr, nullptr};  // tc_execute_host: device copies of A, B, C
+    size_t host_dev_bytes[3] = {0, 0, 0};
     void *gett_state = nullptr;     // owned by the GETT executor
     void *flush_buf = nullptr;      // predictor: remote regions / L2 flush
     size_t flush_bytes = 0;

@@ -344,6 +344,8 @@ tc_status tc_plan_destroy(tc_plan plan) {
         if (p.dev_status) cudaFree(p.dev_status);
         if (p.flush_buf) cudaFree(p.flush_buf);
         if (p.busy_event) cudaEventDestroy((cudaEvent_t)p.busy_event);
+        for (void *d : p.host_dev)
+            if (d) cudaFree(d);
         cudaSetDevice(cur);
     }
     delete plan;
@@ -420,6 +422,20 @@ tc_status tc_plan_set_gett_pack(tc_plan plan, int32_t mode) {
     return TC_SUCCESS;
 }
 
+tc_status tc_plan_set_gett_pair(tc_plan plan, int32_t enable) {
+    if (!plan) return fail(TC_ERROR_INVALID_ARGUMENT, "plan is NULL");
+    if (enable != 0 && enable != 1) return fail(TC_ERROR_INVALID_ARGUMENT, "enable must be 0 or 1");
+    plan->p.gett_pair = enable;
+    return TC_SUCCESS;
+}
+
+tc_status tc_plan_set_split_accumulators(tc_plan plan, int32_t enable) {
+    if (!plan) return fail(TC_ERROR_INVALID_ARGUMENT, "plan is NULL");
+    if (enable != 0 && enable != 1) return fail(TC_ERROR_INVALID_ARGUMENT, "enable must be 0 or 1");
+    plan->p.gett_split = enable;
+    return TC_SUCCESS;
+}
+
 tc_status tc_plan_set_compensation(tc_plan plan, int32_t chunk) {
     if (!plan) return fail(TC_ERROR_INVALID_ARGUMENT, "plan is NULL");
     if (chunk < -1 || (chunk > 0 && chunk % 32 != 0))
@@ -470,6 +486,60 @@ tc_status tc_execute(tc_plan plan, const void *alpha, const void *A, const void 
     }
     e = cudaEventRecord((cudaEvent_t)p.busy_event, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(TC_ERROR_CUDA, std::string("event record: ") + cudaGetErrorString(e));
+    return TC_SUCCESS;
+}
+
+// Elements an operand's strided layout spans: 1 + sum (extent - 1) * stride.
+static size_t operand_span_bytes(const Plan &p, int o) {
+    int64_t span = 1;
+    for (int m = 0; m < p.op[o].n; ++m) span += (p.ext[p.op[o].idx[m]] - 1) * p.op[o].stride[m];
+    return (size_t)span * (o == OP_C ? elem_bytes_c(p.dtype) : elem_bytes_ab(p.dtype));
+}
+
+tc_status tc_execute_host(tc_plan plan, const void *alpha, const void *hA, const void *hB, const void *beta,
+                          void *hC, void *stream) {
+    if (!plan) return fail(TC_ERROR_INVALID_ARGUMENT, "plan is NULL");
+    if (!alpha || !beta) return fail(TC_ERROR_INVALID_ARGUMENT, "alpha/beta is NULL");
+    if (!hA || !hB || !hC) return fail(TC_ERROR_INVALID_ARGUMENT, "operand pointer is NULL");
+    Plan &p = plan->p;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+    if (p.device >= 0 && p.device != dev)
+        return fail(TC_ERROR_INVALID_ARGUMENT, "plan used on a different device than its first execute");
+    // device copies of the three operands, allocated once (outside any
+    // graph capture) and kept with the plan
+    const size_t bytes[3] = {operand_span_bytes(p, OP_A), operand_span_bytes(p, OP_B), operand_span_bytes(p, OP_C)};
+    for (int o = 0; o < 3; ++o) {
+        if (p.host_dev[o] && p.host_dev_bytes[o] >= bytes[o]) continue;
+        if (p.host_dev[o]) cudaFree(p.host_dev[o]);
+        p.host_dev[o] = nullptr;
+        p.host_dev_bytes[o] = 0;
+        e = cudaMalloc(&p.host_dev[o], bytes[o]);
+        if (e != cudaSuccess) {
+            p.host_dev[o] = nullptr;
+            return fail(TC_ERROR_OUT_OF_MEMORY, std::string("device copy of an operand: ") + cudaGetErrorString(e));
+        }
+        p.host_dev_bytes[o] = bytes[o];
+    }
+    const bool beta_zero = p.dtype == TC_F64 ? *(const double *)beta == 0.0 : *(const float *)beta == 0.0f;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the same stream rule as tc_execute, checked before any copy is queued
+    if (p.busy_event && stream != p.last_stream) {
+        e = cudaEventQuery((cudaEvent_t)p.busy_event);
+        if (e == cudaErrorNotReady)
+            return fail(TC_ERROR_INVALID_ARGUMENT, "the plan's previous execute is still running on another stream");
+    }
+    const void *src[3] = {hA, hB, hC};
+    for (int o = 0; o < 3; ++o) {
+        if (o == OP_C && beta_zero) continue;
+        e = cudaMemcpyAsync(p.host_dev[o], src[o], bytes[o], cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return fail(TC_ERROR_CUDA, std::string("host to device copy: ") + cudaGetErrorString(e));
+    }
+    tc_status s = tc_execute(plan, alpha, p.host_dev[OP_A], p.host_dev[OP_B], beta, p.host_dev[OP_C], stream);
+    if (s != TC_SUCCESS) return s;
+    e = cudaMemcpyAsync(hC, p.host_dev[OP_C], bytes[OP_C], cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return fail(TC_ERROR_CUDA, std::string("device to host copy: ") + cudaGetErrorString(e));
     return TC_SUCCESS;
 }
 

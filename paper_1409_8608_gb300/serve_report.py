@@ -1,7 +1,7 @@
 """Serving measurement: a Poisson stream of contraction requests through
 tc_server (continuous batching).
 
-    python -m paper_1409_8608_gb300.serve_report [--seconds 10] [--rate 2000]
+    python -m paper_1409_8608_gb300.serve_report [--seconds 10] [--warmup 1] [--rate 2000]
 
 Requests: specs abc=ai,ibc / abc=iaj,jbic / ab=aij,jib (one third each);
 free extents log-uniform in [16, 384], contracted extents log-uniform in
@@ -39,7 +39,15 @@ def draw_request(rng):
     return spec, ext, dtype
 
 
-def run(seconds=2.0, rate=2000.0, seed=0, budget=40 << 30, slots=64, streams=16, pool_bytes=4 << 30):
+def run(seconds=2.0, rate=2000.0, seed=0, budget=40 << 30, slots=64, streams=16, pool_bytes=4 << 30,
+        warmup=0.0, check_samples=0):
+    """Submits a Poisson stream for warmup + seconds of arrivals.  Requests
+    arriving during the warm-up are served but not counted; the rest form
+    the measured window: offered and served GFLOP/s (served = their flops
+    over first measured arrival to last measured completion), latency
+    percentiles overall and per dtype.  check_samples requests of the
+    window also copy their result to host memory and are then run again
+    alone on the idle server: both results must be the same bits."""
     import torch
     rng = np.random.default_rng(seed)
     pools = {}
@@ -50,13 +58,14 @@ def run(seconds=2.0, rate=2000.0, seed=0, budget=40 << 30, slots=64, streams=16,
         pools[dt] = pool
     pools["bf16x3"] = pools["f32"]
     server = tc.Server(budget, slots, streams)
+    total = warmup + seconds
     arrivals, t = [], 0.0
     while True:
         t += rng.exponential(1.0 / rate)
-        if t >= seconds:
+        if t >= total:
             break
         arrivals.append(t)
-    reqs, offered = [], 0.0
+    reqs = []
     for _ in arrivals:
         while True:
             spec, ext, dtype = draw_request(rng)
@@ -70,30 +79,60 @@ def run(seconds=2.0, rate=2000.0, seed=0, budget=40 << 30, slots=64, streams=16,
         ob = int(rng.integers(0, (limit - nb) // 64 + 1)) * 64
         base = pool.data_ptr()
         reqs.append((spec, ext, dtype, base + oa * esz, base + ob * esz))
-        offered += 2.0 * math.prod(ext)
-    ids = []
+    window = [q for q, ta in enumerate(arrivals) if ta >= warmup]
+    checks = {}
+    if check_samples and window:
+        for q in window[:: max(1, len(window) // check_samples)][:check_samples]:
+            spec, ext, dtype, _, _ = reqs[q]
+            tdt = torch.float64 if dtype == "f64" else torch.float32
+            checks[q] = torch.full((synth.dense_sizes(spec, ext)[0],), float("nan"), dtype=tdt).pin_memory()
+    ids, t_sub = [], []
     t0 = time.perf_counter()
-    for ta, (spec, ext, dtype, pa, pb) in zip(arrivals, reqs):
+    for q, (ta, (spec, ext, dtype, pa, pb)) in enumerate(zip(arrivals, reqs)):
         while time.perf_counter() - t0 < ta:
             pass
-        ids.append(server.submit(spec, ext, dtype, pa, pb, None))
+        t_sub.append(time.perf_counter() - t0)
+        ids.append(server.submit(spec, ext, dtype, pa, pb, checks.get(q)))
     for rid, (spec, ext, dtype, _, _) in zip(ids, reqs):
         try:
             server.wait(rid, timeout=600.0)
         except tc.TcError as e:
             raise RuntimeError(f"request {rid} ({spec} {ext} {dtype}) failed: {e}") from e
-    wall = time.perf_counter() - t0
+    lat = [server.poll(rid)[1] for rid in ids]
     st = server.stats()
+    # alone: each checked request again, one at a time, on the idle server
+    alone_equal = 0
+    for q, hc in checks.items():
+        spec, ext, dtype, pa, pb = reqs[q]
+        again = torch.full_like(hc, float("nan")).pin_memory()
+        server.wait(server.submit(spec, ext, dtype, pa, pb, again), timeout=600.0)
+        alone_equal += int(torch.equal(again, hc))
     server.close()
-    return {
-        "requests": len(ids), "seconds_of_arrivals": seconds, "rate_per_s": rate,
-        "offered_gflops": offered / seconds / 1e9,
-        "served_gflops": st["flops_served"] / wall / 1e9,
-        "p50_ms": st["p50_seconds"] * 1e3, "p99_ms": st["p99_seconds"] * 1e3,
-        "max_ms": st["max_seconds"] * 1e3, "admission_stalls": st["admission_stalls"],
-        "peak_inflight": st["peak_inflight"], "completed": st["completed"], "failed": st["failed"],
-        "wall_s": wall,
-    }
+
+    def pct(v, qq):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(qq * (len(v) - 1) + 0.5))] * 1e3 if v else None
+
+    def summarize(sel):
+        fl = [2.0 * math.prod(reqs[q][1]) for q in sel]
+        if not sel:
+            return {"requests": 0}
+        t_first = min(arrivals[q] for q in sel)
+        t_done = max(t_sub[q] + lat[q] for q in sel)
+        return {"requests": len(sel), "offered_gflops": sum(fl) / seconds / 1e9,
+                "served_gflops": sum(fl) / max(1e-9, t_done - t_first) / 1e9,
+                "p50_ms": pct([lat[q] for q in sel], 0.50), "p99_ms": pct([lat[q] for q in sel], 0.99)}
+
+    out = summarize(window)
+    out.update({"seconds_of_arrivals": seconds, "warmup_seconds": warmup, "rate_per_s": rate,
+                "max_ms": max(lat[q] for q in window) * 1e3 if window else None,
+                "admission_stalls": st["admission_stalls"], "peak_inflight": st["peak_inflight"],
+                "completed": st["completed"], "failed": st["failed"],
+                "by_dtype": {dt: summarize([q for q in window if reqs[q][2] == dt]) for dt in DTYPES}})
+    if checks:
+        out["alone_vs_mix"] = {"checked": len(checks), "bitwise_equal": alone_equal}
+        out["sampled_requests"] = [(reqs[q][0], reqs[q][1]) for q in checks]
+    return out
 
 
 def main():
@@ -101,8 +140,11 @@ def main():
     ap.add_argument("--seconds", type=float, default=10.0)
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--warmup", type=float, default=1.0)
     args = ap.parse_args()
-    print(json.dumps(run(args.seconds, args.rate, args.seed)))
+    r = run(args.seconds, args.rate, args.seed, warmup=args.warmup, check_samples=8)
+    r.pop("sampled_requests", None)
+    print(json.dumps(r))
 
 
 if __name__ == "__main__":

@@ -79,6 +79,7 @@ SIGNATURES = {
     "tc_algorithm_workspace": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
     "tc_execute": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "tc_execute_no_alloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "tc_execute_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "tc_plan_device_status": (ctypes.c_int, [_VP]),
     "tc_plan_flops": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "tc_plan_set_split": (ctypes.c_int, [_VP, ctypes.c_int32]),
@@ -86,6 +87,8 @@ SIGNATURES = {
     "tc_plan_set_gett_tma": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_plan_set_gett_pack": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_plan_set_compensation": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "tc_plan_set_gett_pair": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "tc_plan_set_split_accumulators": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "tc_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _VP]),
     "tc_access_distances": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _I64P]),
     "tc_prediction_cases": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
@@ -226,6 +229,13 @@ def tc_execute(plan, alpha, A, B, beta, C, stream=None, dtype="f64"):
                              _ptr(C), _stream(stream)), "tc_execute")
 
 
+def tc_execute_host(plan, alpha, hA, hB, beta, hC, stream=None, dtype="f64"):
+    """Host buffers (pointers or pinned CPU tensors); enqueued on stream."""
+    a, b = _scalar(alpha, dtype), _scalar(beta, dtype)
+    _check(load().tc_execute_host(plan, ctypes.addressof(a), _ptr(hA), _ptr(hB), ctypes.addressof(b),
+                                  _ptr(hC), _stream(stream)), "tc_execute_host")
+
+
 def tc_execute_no_alloc(plan, alpha, A, B, beta, C, stream=None, dtype="f64"):
     a, b = _scalar(alpha, dtype), _scalar(beta, dtype)
     _check(load().tc_execute_no_alloc(plan, ctypes.addressof(a), _ptr(A), _ptr(B), ctypes.addressof(b),
@@ -259,6 +269,14 @@ def tc_selftest_bounded_wait(limit_ns, signal, stream=None):
 
 def tc_plan_set_compensation(plan, chunk):
     _check(load().tc_plan_set_compensation(plan, int(chunk)), "tc_plan_set_compensation")
+
+
+def tc_plan_set_gett_pair(plan, enable):
+    _check(load().tc_plan_set_gett_pair(plan, int(enable)), "tc_plan_set_gett_pair")
+
+
+def tc_plan_set_split_accumulators(plan, enable):
+    _check(load().tc_plan_set_split_accumulators(plan, int(enable)), "tc_plan_set_split_accumulators")
 
 
 def tc_plan_flops(plan):
@@ -455,6 +473,9 @@ class Plan:
     def execute(self, A, B, C, alpha=1.0, beta=0.0, stream=None):
         tc_execute(self.handle, alpha, A, B, beta, C, stream, self.dtype)
 
+    def execute_host(self, hA, hB, hC, alpha=1.0, beta=0.0, stream=None):
+        tc_execute_host(self.handle, alpha, hA, hB, beta, hC, stream, self.dtype)
+
     def set_split(self, products):
         tc_plan_set_split(self.handle, products)
 
@@ -469,6 +490,12 @@ class Plan:
 
     def set_compensation(self, chunk):
         tc_plan_set_compensation(self.handle, chunk)
+
+    def set_gett_pair(self, enable):
+        tc_plan_set_gett_pair(self.handle, enable)
+
+    def set_split_accumulators(self, enable):
+        tc_plan_set_split_accumulators(self.handle, enable)
 
     def predict(self, alg_ids=None, A=None, B=None, C=None, stream=None):
         return tc_predict(self.handle, alg_ids, A, B, C, stream)
