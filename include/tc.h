@@ -240,13 +240,13 @@ tc_status tc_plan_set_gett_tma(tc_plan plan, int32_t enable);
 tc_status tc_plan_set_gett_pack(tc_plan plan, int32_t mode);
 
 /* Tensor-core GETT, FP32-input kinds (TC_BF16X3, TC_TF32): CTA pairs.
- * With 1 (default) and where the launch allows it (256-column tiles, no
+ * With 1, and where the launch allows it (256-column tiles, no
  * compensated accumulation, more than 128 rows of M, every input staged by
  * TMA or pre-converted), clusters of two CTAs share each MMA
  * (tcgen05.mma.cta_group::2, M = 256): each CTA stages and converts its 128
  * rows of A and half of the tile's 256 rows of B, so a CTA moves half the
- * B bytes per MMA; 0 keeps one CTA per tile.  Results are the same bits
- * either way.  Other values give TC_ERROR_INVALID_ARGUMENT. */
+ * B bytes per MMA; 0 (default) keeps one CTA per tile.  Results are the
+ * same bits either way.  Other values give TC_ERROR_INVALID_ARGUMENT. */
 tc_status tc_plan_set_gett_pair(tc_plan plan, int32_t enable);
 
 /* TC_BF16X3, tensor-core GETT without compensation: split accumulators.
