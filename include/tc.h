@@ -250,12 +250,12 @@ tc_status tc_plan_set_gett_pack(tc_plan plan, int32_t mode);
 tc_status tc_plan_set_gett_pair(tc_plan plan, int32_t enable);
 
 /* TC_BF16X3, tensor-core GETT without compensation: split accumulators.
- * With 1 (default) the weight-1 slice product (0,0) accumulates in one
- * tensor-memory accumulator and the smaller products in a second one, added
- * once in the epilogue: only K/16 FP32 roundings then act on the magnitude
- * of the whole sum instead of 6K/16, at the cost of not double-buffering
- * the accumulators.  0: one accumulator for every product.  Other values
- * give TC_ERROR_INVALID_ARGUMENT. */
+ * With 1 the weight-1 slice product (0,0) accumulates in one tensor-memory
+ * accumulator and the smaller products in a second one, added once in the
+ * epilogue: only K/16 FP32 roundings then act on the magnitude of the whole
+ * sum instead of 6K/16, at the cost of not double-buffering the
+ * accumulators.  0: one accumulator for every product.  -1 (default): split
+ * when K > 64.  Other values give TC_ERROR_INVALID_ARGUMENT. */
 tc_status tc_plan_set_split_accumulators(tc_plan plan, int32_t enable);
 
 /* Failure-detection self-test (no paper counterpart).  Launches one CTA on

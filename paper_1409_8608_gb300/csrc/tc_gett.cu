@@ -2036,8 +2036,13 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     d.status = p.dev_status;
     d.tiles_m = pair ? (d.M + 2 * kBM - 1) / (2 * kBM) : (d.M + kBM - 1) / kBM;
     d.tile_frac = probe ? probe->fraction : 1.0;
-    // split accumulators: split-BF16 without the compensated form
-    d.split = (p.dtype == TC_BF16X3 && !comp && p.gett_split != 0) ? 1 : 0;
+    // split accumulators: split-BF16 without the compensated form; by
+    // default only past 64 contracted positions (6K/16 > 24 accumulations
+    // into one FP32 accumulator), where the roundings of the single
+    // accumulator reach the 1e-6 level
+    constexpr int64_t kSplitMinK = 65;
+    const bool want_split = p.gett_split > 0 || (p.gett_split < 0 && d.K >= kSplitMinK);
+    d.split = (p.dtype == TC_BF16X3 && !comp && want_split) ? 1 : 0;
     cudaStream_t st = (cudaStream_t)stream;
     if (pk) {
         // the smaller input's stage images, for the stage depth the launch

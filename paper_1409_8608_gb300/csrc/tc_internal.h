@@ -62,7 +62,7 @@ struct Plan {
     int gett_pack = 1;              // tensor-core GETT: pre-convert the small input (0 never, 1 auto, 2 always)
     int comp_chunk = -1;            // TC_BF16X3: compensated K chunk (-1 default, 0 off)
     int gett_pair = 0;              // tensor-core GETT: CTA pairs (cta_group::2) where legal
-    int gett_split = 1;             // TC_BF16X3: (0,0) products in their own accumulator
+    int gett_split = -1;            // TC_BF16X3: (0,0) products in their own accumulator (-1 auto)
     // device resources, created lazily by the first execute
     int device = -1;
     void *workspace = nullptr;

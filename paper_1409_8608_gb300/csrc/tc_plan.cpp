@@ -431,7 +431,7 @@ tc_status tc_plan_set_gett_pair(tc_plan plan, int32_t enable) {
 
 tc_status tc_plan_set_split_accumulators(tc_plan plan, int32_t enable) {
     if (!plan) return fail(TC_ERROR_INVALID_ARGUMENT, "plan is NULL");
-    if (enable != 0 && enable != 1) return fail(TC_ERROR_INVALID_ARGUMENT, "enable must be 0 or 1");
+    if (enable < -1 || enable > 1) return fail(TC_ERROR_INVALID_ARGUMENT, "enable must be -1, 0 or 1");
     plan->p.gett_split = enable;
     return TC_SUCCESS;
 }

@@ -133,4 +133,7 @@ def test_pair_setters_reject_bad_values(tcmod):
     for fn in (plan.set_gett_pair, plan.set_split_accumulators):
         with pytest.raises(tcmod.TcError):
             fn(2)
+    with pytest.raises(tcmod.TcError):
+        plan.set_gett_pair(-1)
+    plan.set_split_accumulators(-1)  # automatic: by K
     plan.close()
