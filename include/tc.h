@@ -420,13 +420,20 @@ tc_status tc_batch_device_status(tc_batch batch);
 /* ---- Serving: continuous batching of contraction requests ---------------
  * No paper counterpart.  A worker thread admits queued requests in arrival
  * order when a slot is free and their operands fit in the remaining device
- * budget (one allocation made at creation, carved first-fit), runs each on
- * one of its streams (inputs copied in, the fused GETT with a plan cached
- * per (spec, extents, dtype), result copied out if asked) and frees its
- * memory and slot when its completion event fires.  Requests that arrive
- * while others run are admitted as soon as room appears; their work
- * overlaps on the device.  A request's plan depends only on the request, so
- * its result is the same alone and in a mix. */
+ * budget (one allocation made at creation, carved first-fit).  Admitted
+ * requests wait by batch class -- FP64, FP32 (SIMT GETT), TC_BF16X3 with
+ * K <= 64, TC_BF16X3 with 64 < K <= 256 (split accumulators) -- and
+ * whenever one of the server's streams is free, the class whose oldest
+ * request has waited longest becomes ONE persistent batched launch over the
+ * tiles of all its admitted requests (inputs copied in, one descriptor per
+ * request, results copied out if asked, one completion event).  TC_BF16X3
+ * with longer K (compensated) and the other tensor dtypes run one launch
+ * each.  Requests that arrive while batches run form the next batches, and
+ * batches on different streams overlap.  A request's class, K order and
+ * tile shapes follow from the request alone, so its result is the same
+ * alone and in any mix.  The server allocates at creation only: the budget,
+ * and per stream a pinned and a device staging area for its batch tables
+ * (256 descriptors, 2^20 tiles). */
 
 typedef struct tc_server_s *tc_server;
 
@@ -437,6 +444,8 @@ typedef struct {
     double flops_served;        /* sum of 2*prod(extents) over completed */
     double span_seconds;        /* first submission to last completion */
     double p50_seconds, p99_seconds, max_seconds;  /* submit -> result ready */
+    int64_t batches;            /* launches made (a batch, or one solo request) */
+    int64_t max_batch;          /* most requests in one launch */
 } tc_server_report;
 
 /* budget_bytes of device memory (allocated now), at most `slots` requests

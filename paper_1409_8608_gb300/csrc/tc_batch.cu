@@ -450,7 +450,7 @@ tc_status tc_batch_execute(tc_batch batch, const void *alpha, const void *beta, 
         for (const auto &P : b.probs)
             if (P.K > 32) one_stage = 0;
         auto run = [&](int64_t t0, int64_t t1) {
-            return gett_launch_batch(b.ddescs, b.dtile_prob, t0, t1, b.bn, a, be, b.nprod, b.dstatus, one_stage,
+            return gett_launch_batch(b.ddescs, b.dtile_prob, t0, t1, b.bn, a, be, b.nprod, b.dstatus, one_stage, 0,
                                      stream);
         };
         if (one_launch_per_problem) {

@@ -67,6 +67,7 @@ struct TileDesc {
     double alpha, beta;
     int init, alpha_one;
     int a_m_fast, b_n_fast;  // load mapping: M (N) contiguous in memory
+    int64_t tile0;           // batched form: the problem's first tile in the list
 };
 
 struct GatherDesc {
@@ -159,8 +160,7 @@ __global__ void __launch_bounds__(256) elementwise_kernel(const PhaseDesc d) {
 // One CTA computes a BM x BN tile of one task's C slice; K runs over the
 // linearised contracted space in chunks of BK staged through shared memory.
 template <typename T, int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
-tile_kernel(const TileDesc d) {
+__device__ __forceinline__ void tile_body(const TileDesc &d, int64_t bid) {
     constexpr int TX = BN / TN, TY = BM / TM, NT = TX * TY;
     // A thread owns rows ty*V + r + g*TY*V (r < V, g < TM/V) and likewise
     // columns: with V = 4 for FP32 each group is one 16-byte shared-memory
@@ -183,7 +183,6 @@ tile_kernel(const TileDesc d) {
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
 
-    int64_t bid = blockIdx.x;
     const int64_t tm = bid % d.tiles_m;
     bid /= d.tiles_m;
     const int64_t tn = bid % d.tiles_n;
@@ -380,6 +379,29 @@ tile_kernel(const TileDesc d) {
             if (om >= 0 && on >= 0) C[om + on] = acc[i][j];
         }
     }
+}
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN)) tile_kernel(const TileDesc d) {
+    tile_body<T, BM, BN, BK, TM, TN>(d, blockIdx.x);
+}
+
+// Batched form of the SIMT GETT (no paper counterpart): CTA t computes tile
+// t of the flattened tile list of many problems, each with its own
+// descriptor (modes, strides, operands); the descriptor of the tile's
+// problem is copied to shared memory first.  A problem's tiles compute
+// exactly as tile_kernel computes them, whatever else is in the batch.
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+tile_batch_kernel(const TileDesc *__restrict__ descs, const int32_t *__restrict__ tile_prob) {
+    __shared__ __align__(16) TileDesc sd;
+    static_assert(sizeof(TileDesc) % 8 == 0, "descriptor in 8-byte words");
+    constexpr int kWords = sizeof(TileDesc) / 8;
+    const int q = tile_prob[blockIdx.x];
+    for (int w = threadIdx.x; w < kWords; w += blockDim.x)
+        ((int64_t *)&sd)[w] = ((const int64_t *)(descs + q))[w];
+    __syncthreads();
+    tile_body<T, BM, BN, BK, TM, TN>(sd, (int64_t)blockIdx.x - sd.tile0);
 }
 
 // ---------------------------------------------------------------- copy
@@ -702,10 +724,12 @@ tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *
 
 // SIMT GETT: the whole contraction as one tiled kernel, M = free indices
 // of A, N = free indices of B, K = contracted indices.
+// The SIMT GETT's descriptor: M = free indices of A, N = free indices of B
+// (each sorted by their C stride), K = contracted indices with the one
+// contiguous in A (or else in B) innermost; tiles of 64 x 64 (FP64) or
+// 128 x 128 (FP32).
 template <typename T>
-tc_status run_gett_simt(Plan &p, T alpha, const T *A, const T *B, T beta, T *C,
-                        cudaStream_t st, const Probe *probe) {
-    TileDesc td;
+void describe_gett_simt(const Plan &p, T alpha, const T *A, const T *B, T beta, T *C, TileDesc &td) {
     std::memset(&td, 0, sizeof(td));
     auto by_c_stride = [&](std::vector<int> ids) {
         std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) {
@@ -746,18 +770,23 @@ tc_status run_gett_simt(Plan &p, T alpha, const T *A, const T *B, T beta, T *C,
     int64_t kinB = td.red.n ? td.red.sB[td.red.n - 1] : 0;
     td.a_m_fast = td.m.n ? (td.m.sA[0] <= kinA || kinA == 0) : 0;
     td.b_n_fast = td.n.n ? (td.n.sB[0] <= kinB || kinB == 0) : 0;
+    const int64_t bm = sizeof(T) == 8 ? 64 : 128;
+    td.tiles_m = (td.M + bm - 1) / bm;
+    td.tiles_n = (td.N + bm - 1) / bm;
+}
+
+template <typename T>
+tc_status run_gett_simt(Plan &p, T alpha, const T *A, const T *B, T beta, T *C,
+                        cudaStream_t st, const Probe *probe) {
+    TileDesc td;
+    describe_gett_simt<T>(p, alpha, A, B, beta, C, td);
     auto cut = [&](int64_t n) {
         return !probe || probe->fraction >= 1.0 ? n : std::max<int64_t>(1, (int64_t)(n * probe->fraction));
     };
-    if constexpr (sizeof(T) == 8) {
-        td.tiles_m = (td.M + 63) / 64;
-        td.tiles_n = (td.N + 63) / 64;
+    if constexpr (sizeof(T) == 8)
         tile_kernel<T, 64, 64, 16, 4, 4><<<(unsigned)cut(td.tiles_m * td.tiles_n), 256, 0, st>>>(td);
-    } else {
-        td.tiles_m = (td.M + 127) / 128;
-        td.tiles_n = (td.N + 127) / 128;
+    else
         tile_kernel<T, 128, 128, 16, 8, 8><<<(unsigned)cut(td.tiles_m * td.tiles_n), 256, 0, st>>>(td);
-    }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? TC_SUCCESS
                             : fail(TC_ERROR_CUDA, std::string("GETT tile_kernel launch (") +
@@ -766,6 +795,34 @@ tc_status run_gett_simt(Plan &p, T alpha, const T *A, const T *B, T beta, T *C,
 }
 
 }  // namespace
+
+size_t simt_desc_bytes() { return sizeof(TileDesc); }
+
+int64_t simt_fill_desc(const Plan &p, const void *A, const void *B, void *C, int64_t tile0, void *out) {
+    TileDesc td;
+    if (p.dtype == TC_F64)
+        describe_gett_simt<double>(p, 1.0, (const double *)A, (const double *)B, 0.0, (double *)C, td);
+    else
+        describe_gett_simt<float>(p, 1.0f, (const float *)A, (const float *)B, 0.0f, (float *)C, td);
+    td.tile0 = tile0;
+    std::memcpy(out, &td, sizeof(td));
+    return td.tiles_m * td.tiles_n;
+}
+
+tc_status simt_launch_batch(tc_dtype dt, const void *ddescs, const int32_t *dtile_prob, int64_t ntiles,
+                            void *stream) {
+    if (ntiles <= 0) return TC_SUCCESS;
+    if (ntiles > 0x7fffffff) return fail(TC_ERROR_INVALID_ARGUMENT, "batch has too many tiles");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dt == TC_F64)
+        tile_batch_kernel<double, 64, 64, 16, 4, 4>
+            <<<(unsigned)ntiles, 256, 0, st>>>((const TileDesc *)ddescs, dtile_prob);
+    else
+        tile_batch_kernel<float, 128, 128, 16, 8, 8>
+            <<<(unsigned)ntiles, 256, 0, st>>>((const TileDesc *)ddescs, dtile_prob);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? TC_SUCCESS : fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+}
 
 int64_t nest_phase_items(const Plan &p, const Algorithm &alg, bool *tiled) {
     NestLayout L = layout_for(p, alg);

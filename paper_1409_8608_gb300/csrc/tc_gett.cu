@@ -803,7 +803,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     const int64_t slot0 = PAIR ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;
     const int64_t nslots = PAIR ? (int64_t)(gridDim.x >> 1) : (int64_t)gridDim.x;
     // accumulators per tile: one (double-buffered) or the split pair
-    const bool split = !COMP && !BATCH && d.split != 0;
+    const bool split = !COMP && d.split != 0;
     const int nbuf = split ? 1 : 2;
     // barriers the other CTA of a pair arrives on are waited on with
     // acquire at cluster scope; arrivals for the MMA issuer go to rank 0
@@ -1850,14 +1850,10 @@ size_t gett_workspace_bytes(const Plan &p) {
 
 void gett_release(Plan &) {}
 
-tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, const void *beta,
-                    void *C, void *stream, const Probe *probe) {
-    if (p.dtype == TC_F64 || p.dtype == TC_F32) return exec_gett_simt(p, alpha, A, B, beta, C, stream, probe);
-    tc_status s = ensure_device_resources(p, 0);
-    if (s != TC_SUCCESS) return s;
-    p.last_stream = stream;
-    GettDesc d;
-    std::memset(&d, 0, sizeof(d));
+// The GETT's modes: M = free indices of A and N = free indices of B, each
+// sorted by their C stride; the K order as below.  pk: the pre-converted
+// input (0 none, 1 A, 2 B).
+tc_status describe_modes(const Plan &p, int pk, GettDesc &d) {
     auto by_c_stride = [&](std::vector<int> ids) {
         std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) {
             return p.op[OP_C].stride_of(x) < p.op[OP_C].stride_of(y);
@@ -1879,10 +1875,8 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     for (int m = 0; m < p.op[OP_A].n; ++m) sizeA *= p.ext[p.op[OP_A].idx[m]];
     for (int m = 0; m < p.op[OP_B].n; ++m) sizeB *= p.ext[p.op[OP_B].idx[m]];
     const int big = sizeB >= sizeA ? OP_B : OP_A, small = big == OP_B ? OP_A : OP_B;
-    // a pre-converted smaller input is read as stage images, so the K order
-    // follows the larger input alone
-    int64_t pk_bound = 0;
-    const int pk = pack_choice(p, pk_bound);
+    // a pre-converted smaller input (pk) is read as stage images, so the K
+    // order follows the larger input alone
     std::vector<int> ki(p.contracted);
     std::stable_sort(ki.begin(), ki.end(), [&](int x, int y) {
         return p.op[big].stride_of(x) > p.op[big].stride_of(y);
@@ -1949,6 +1943,25 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
         d.k_sB[m] = kmodes[m].sB;
         d.K *= kmodes[m].ext;
     }
+    return TC_SUCCESS;
+}
+
+tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, const void *beta,
+                    void *C, void *stream, const Probe *probe) {
+    if (p.dtype == TC_F64 || p.dtype == TC_F32) return exec_gett_simt(p, alpha, A, B, beta, C, stream, probe);
+    tc_status s = ensure_device_resources(p, 0);
+    if (s != TC_SUCCESS) return s;
+    p.last_stream = stream;
+    GettDesc d;
+    std::memset(&d, 0, sizeof(d));
+    // a pre-converted smaller input is read as stage images, so the K order
+    // follows the larger input alone
+    int64_t pk_bound = 0;
+    const int pk = pack_choice(p, pk_bound);
+    s = describe_modes(p, pk, d);
+    if (s != TC_SUCCESS) return s;
+    const int in_bytes = (p.dtype == TC_BF16 || p.dtype == TC_F16) ? 2 : 4;
+    const int vec = 16 / in_bytes;
     const int chunk = p.dtype == TC_TF32 ? 4 : 8;
     int bn = p.gett_bn == 128 || p.gett_bn == 256 ? p.gett_bn : (d.N >= 256 ? 256 : 128);
     // compensated accumulation (split-BF16 only): K chunks of comp_k elements
@@ -2115,8 +2128,34 @@ void gett_fill_batch_desc(const BatchProblem &P, int bn, void *out) {
     std::memcpy(out, &d, sizeof(d));
 }
 
+int64_t gett_fill_plan_desc(const Plan &p, int bn, const void *A, const void *B, void *C, int64_t tile0, void *out) {
+    GettDesc d;
+    std::memset(&d, 0, sizeof(d));
+    if (describe_modes(p, 0, d) != TC_SUCCESS) return -1;
+    const int in_bytes = (p.dtype == TC_BF16 || p.dtype == TC_F16) ? 2 : 4;
+    const int vec = 16 / in_bytes, chunk = p.dtype == TC_TF32 ? 4 : 8;
+    auto pick = [&](const void *base, int rows, int nrow, const int64_t *rext, const int64_t *rs,
+                    const int64_t *ks) {
+        if (vec_ok(base, vec, nrow, rs, d.nk, d.k_ext, ks)) return 2;
+        int64_t s0 = sectors_for(0, rows, chunk, in_bytes, nrow, rext, rs, d.nk, d.k_ext, ks);
+        int64_t s1 = sectors_for(1, rows, chunk, in_bytes, nrow, rext, rs, d.nk, d.k_ext, ks);
+        return s1 < s0 ? 1 : 0;
+    };
+    d.a_map = pick(A, kBM, d.nm, d.m_ext, d.m_sA, d.k_sA);
+    d.b_map = pick(B, bn, d.nn, d.n_ext, d.n_sB, d.k_sB);
+    d.A = A;
+    d.B = B;
+    d.C = (float *)C;
+    d.tiles_m = (d.M + kBM - 1) / kBM;
+    d.tiles_n = (d.N + bn - 1) / bn;
+    d.tile0 = tile0;
+    std::memcpy(out, &d, sizeof(d));
+    return d.tiles_m * d.tiles_n;
+}
+
 tc_status gett_launch_batch(const void *ddescs, const int32_t *dtile_prob, int64_t t_begin, int64_t t_end, int bn,
-                            float alpha, float beta, int nprod, int *dstatus, int one_stage, void *stream) {
+                            float alpha, float beta, int nprod, int *dstatus, int one_stage, int split,
+                            void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     GettDesc d;
     std::memset(&d, 0, sizeof(d));
@@ -2131,6 +2170,7 @@ tc_status gett_launch_batch(const void *ddescs, const int32_t *dtile_prob, int64
     d.status = dstatus;
     d.tile_frac = 1.0;
     d.one_stage = one_stage;
+    d.split = split;
     CUtensorMap none;
     std::memset(&none, 0, sizeof(none));
     if (bn == 128) return launch_gett<GK_BF16X3, 128, 4, kBK, 0, false, true>(d, none, none, st);

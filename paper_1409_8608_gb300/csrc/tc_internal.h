@@ -92,6 +92,11 @@ struct Probe {
 // error reporting (thread-local message)
 tc_status fail(tc_status st, const std::string &msg);
 
+// Parses and validates a spec into p; with enumerate = false only the
+// fused GETT (algorithm 0) is listed (tc_plan.cpp).
+tc_status build_plan(Plan &p, const char *spec, const int64_t *extents, const int64_t *strides, tc_dtype dtype,
+                     bool enumerate);
+
 // element size of A/B and of C for a dtype
 size_t elem_bytes_ab(tc_dtype dt);
 size_t elem_bytes_c(tc_dtype dt);
@@ -110,6 +115,16 @@ tc_status exec_gett_simt(Plan &p, const void *alpha, const void *A, const void *
 size_t gett_workspace_bytes(const Plan &p);
 void gett_release(Plan &p);
 tc_status ensure_device_resources(Plan &p, size_t workspace_bytes);
+
+// Batched SIMT GETT (FP64 / FP32; the serving form's batches): one
+// descriptor per problem (simt_desc_bytes each) holding its modes, strides
+// and operands with alpha = 1, beta = 0; simt_fill_desc returns the
+// problem's tile count, tile0 is its first tile in the batch's list.  The
+// launch runs tile t of the list in CTA t (dtile_prob[t] = its problem).
+size_t simt_desc_bytes();
+int64_t simt_fill_desc(const Plan &p, const void *A, const void *B, void *C, int64_t tile0, void *out);
+tc_status simt_launch_batch(tc_dtype dt, const void *ddescs, const int32_t *dtile_prob, int64_t ntiles,
+                            void *stream);
 
 // One problem of the batched form: a strided GEMM over the merged free
 // modes of A (m), of B (n) and the merged contracted modes (k).
@@ -131,8 +146,14 @@ size_t gett_desc_bytes();
 void gett_fill_batch_desc(const BatchProblem &P, int bn, void *out);
 // one_stage: every problem's K fits one 32-element stage (the converter
 // groups then take alternate tiles).
+// split: the (0,0) slice products in their own accumulator (every problem).
 tc_status gett_launch_batch(const void *ddescs, const int32_t *dtile_prob, int64_t t_begin, int64_t t_end, int bn,
-                            float alpha, float beta, int nprod, int *dstatus, int one_stage, void *stream);
+                            float alpha, float beta, int nprod, int *dstatus, int one_stage, int split,
+                            void *stream);
+// A general problem (any modes and strides the plan describes, global-load
+// inputs, 128 x bn tiles) as one descriptor of the batched tensor-core
+// GETT; returns its tile count (-1 if the GETT cannot describe it).
+int64_t gett_fill_plan_desc(const Plan &p, int bn, const void *A, const void *B, void *C, int64_t tile0, void *out);
 
 }  // namespace tc
 

@@ -140,8 +140,10 @@ void finish_algorithm(const Plan &p, Algorithm &a) {
 
 }  // namespace
 
-static tc_status build_plan(Plan &p, const char *spec, const int64_t *extents,
-                            const int64_t *strides, tc_dtype dtype) {
+// enumerate = false: spec, index classes, layouts and the fused GETT only
+// (no Section 2 algorithms), for callers that only run the GETT.
+tc_status build_plan(Plan &p, const char *spec, const int64_t *extents, const int64_t *strides, tc_dtype dtype,
+                     bool enumerate) {
     if (!spec) return fail(TC_ERROR_INVALID_ARGUMENT, "spec is NULL");
     if (!extents) return fail(TC_ERROR_INVALID_ARGUMENT, "extents is NULL");
     if (dtype < TC_F64 || dtype > TC_BF16X3)
@@ -268,7 +270,7 @@ static tc_status build_plan(Plan &p, const char *spec, const int64_t *extents,
     }
     // Section 2: every kernel, every admissible kernel-index choice, every
     // permutation of the sliced loops
-    for (int kernel = TC_KERNEL_DOT; kernel <= TC_KERNEL_GEMM; ++kernel) {
+    for (int kernel = TC_KERNEL_DOT; kernel <= TC_KERNEL_GEMM && enumerate; ++kernel) {
         for (const auto &kc : kernel_choices(kernel, p)) {
             std::vector<int> sliced;
             for (int x = 0; x < p.nidx; ++x)
@@ -323,7 +325,7 @@ tc_status tc_plan_create(tc_plan *out, const char *spec, const int64_t *extents,
     *out = nullptr;
     tc_plan_s *h = new (std::nothrow) tc_plan_s();
     if (!h) return fail(TC_ERROR_OUT_OF_MEMORY, "host allocation failed");
-    tc_status st = build_plan(h->p, spec, extents, strides, dtype);
+    tc_status st = build_plan(h->p, spec, extents, strides, dtype, true);
     if (st != TC_SUCCESS) {
         delete h;
         return st;

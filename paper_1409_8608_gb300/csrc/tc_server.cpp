@@ -2,20 +2,31 @@
 // project's serving addition).
 //
 // A worker thread owns the device side.  Requests (spec, extents, dtype,
-// host inputs, optional host output) queue in arrival order.  The worker
+// host inputs, optional host output) queue in arrival order; each keeps the
+// plan its submission built (spec, index classes, layouts: no algorithm
+// enumeration).  The worker
 //   * admits the head of the queue when a slot is free and its operands
 //     (A, B, C) fit in what is left of the device-memory budget -- a
 //     first-fit arena carved out of one allocation made at creation -- and
 //     otherwise counts an admission stall and waits (no reordering);
-//   * runs each admitted request on one of its streams: inputs copied in,
-//     the contraction with the plan cached for the request's key (spec,
-//     extents, dtype: a request's arithmetic never depends on its
-//     neighbours), the result copied out when the caller asked for it;
-//   * polls the in-flight requests' events, frees their memory and slots as
-//     they finish, and admits more -- requests that arrive while others run
-//     join at once, and their kernels overlap on the device.
-// Latency is measured from submission to the moment the worker sees the
-// request's completion event.
+//   * files every admitted request under its batch class: FP64 or FP32 (the
+//     SIMT GETT), split-BF16 with K <= 64, split-BF16 with 64 < K <= 256
+//     (split accumulators), or solo (split-BF16 with longer K, compensated,
+//     and the other tensor dtypes: one launch each);
+//   * whenever one of its streams is free, turns the class whose oldest
+//     request waited longest into ONE batched launch of all its admitted
+//     requests (up to a problem and tile cap): their inputs copied in, one
+//     descriptor per request and the flattened tile table uploaded from the
+//     stream's pinned staging, one persistent kernel over every tile, the
+//     results copied out, one completion event;
+//   * polls the streams' events, frees the finished batch's memory and
+//     slots, and admits more -- requests that arrive while batches run form
+//     the next batches, and batches on different streams overlap.
+// A request's arithmetic depends only on the request: its class, its K
+// order and its tile shapes follow from its own spec, extents and dtype,
+// never from the batch around it, so its result is the same alone and in
+// any mix.  Latency is measured from submission to the moment the worker
+// sees the completion of the request's batch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,22 +51,27 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+constexpr int kClasses = 4;              // batched classes (see above)
+constexpr int kSolo = -1;
+constexpr int kMaxBatchProblems = 256;
+constexpr int64_t kMaxBatchTiles = int64_t(1) << 20;
+constexpr int64_t kSplitMinK = 65;       // split accumulators past K = 64
+constexpr int64_t kBatchMaxK = 256;      // longer split-BF16 K runs compensated, solo
+
 struct Request {
     int64_t id = 0;
-    std::string spec;
-    std::vector<int64_t> extents;
+    std::unique_ptr<Plan> plan;  // spec, classes, layouts (GETT only)
     tc_dtype dtype = TC_F32;
     const void *hA = nullptr;
     const void *hB = nullptr;
     void *hC = nullptr;
     size_t bytesA = 0, bytesB = 0, bytesC = 0;
     double flops = 0;
+    int cls = kSolo;
+    int64_t K = 1;
     Clock::time_point t_submit;
     // device side
     size_t offset = 0, bytes = 0;
-    int stream = 0;
-    cudaEvent_t done_event = nullptr;
-    tc_plan plan = nullptr;
 };
 
 struct Result {
@@ -63,6 +79,17 @@ struct Result {
     tc_status status = TC_SUCCESS;
     double latency = 0;
     std::string message;  // error text of a failed request
+};
+
+// One stream's batch in flight and the stream's own staging buffers.
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    std::vector<std::unique_ptr<Request>> reqs;
+    char *hdesc = nullptr, *ddesc = nullptr;        // descriptors (pinned host, device)
+    int32_t *htile = nullptr, *dtile = nullptr;     // tile -> problem
+    int *hstatus = nullptr, *dstatus = nullptr;     // bounded-wait status word
 };
 
 // First-fit allocator over one device allocation, blocks coalesced on free.
@@ -122,10 +149,12 @@ size_t operand_bytes(const Plan &p, int o) {
 struct ServerImpl {
     int64_t budget = 0;
     int slots = 0;
-    std::vector<cudaStream_t> streams;
+    std::vector<Slot> streams;
     void *arena_base = nullptr;
     Arena arena;
     int device = 0;
+    size_t desc_bytes = 0;  // one problem descriptor (the larger of the two kinds)
+    void *ctrl_dev = nullptr, *ctrl_host = nullptr;  // every slot's staging, one allocation each
 
     std::mutex mu;
     std::condition_variable cv;
@@ -137,30 +166,22 @@ struct ServerImpl {
     std::thread worker;
 
     // worker-only state
-    std::vector<std::unique_ptr<Request>> inflight;
+    std::deque<std::unique_ptr<Request>> pending[kClasses + 1];  // [kClasses]: solo
+    int admitted = 0;  // admitted and not finished (pending or on the device)
     const char *last_action = "start";  // the worker's last CUDA call, for diagnostics
     bool warned = false;
-    std::map<std::string, tc_plan> plans;
-    int rr = 0;
 
     // statistics (under mu)
     std::vector<double> latencies;
     double flops_served = 0;
-    int64_t stalls = 0, completed = 0, failed = 0, peak_inflight = 0;
+    int64_t stalls = 0, completed = 0, failed = 0, peak_inflight = 0, batches = 0, max_batch = 0;
     Clock::time_point t_first, t_last;
     bool any = false;
-
-    std::string key(const Request &r) {
-        std::string k = r.spec + "|" + std::to_string((int)r.dtype);
-        for (int64_t e : r.extents) k += "," + std::to_string(e);
-        return k;
-    }
 
     void finish(std::unique_ptr<Request> &r, tc_status st, const std::string &msg = "") {
         const double lat = std::chrono::duration<double>(Clock::now() - r->t_submit).count();
         arena.release(r->offset, r->bytes);
-        last_action = "cudaEventDestroy";
-        if (r->done_event) cudaEventDestroy(r->done_event);
+        --admitted;
         std::lock_guard<std::mutex> g(mu);
         Result &res = results[r->id];
         res.done = true;
@@ -178,115 +199,229 @@ struct ServerImpl {
         done_cv.notify_all();
     }
 
-    tc_status launch(Request &r) {
-        // an error left by an earlier call on this thread must not be
-        // attributed to this request's launches
-        cudaError_t stale = cudaGetLastError();
+    void operands(const Request &r, char **dA, char **dB, char **dC) {
+        char *base = (char *)arena_base + r.offset;
+        *dA = base;
+        *dB = *dA + (r.bytesA + 255) / 256 * 256;
+        *dC = *dB + (r.bytesB + 255) / 256 * 256;
+    }
+
+    // Inputs of one request in, on the slot's stream.
+    tc_status copy_in(const Request &r, cudaStream_t st) {
+        char *dA, *dB, *dC;
+        operands(r, &dA, &dB, &dC);
+        last_action = "cudaMemcpyAsync (inputs)";
+        cudaError_t e = cudaMemcpyAsync(dA, r.hA, r.bytesA, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dB, r.hB, r.bytesB, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess)
+            return fail(TC_ERROR_CUDA, std::string("copy of the inputs (arena offset ") + std::to_string(r.offset) +
+                                           "): " + cudaGetErrorString(e));
+        return TC_SUCCESS;
+    }
+
+    // The class whose oldest pending request arrived first.
+    int next_class() {
+        int best = -2;
+        int64_t best_id = 0;
+        for (int c = 0; c <= kClasses; ++c) {
+            if (pending[c].empty()) continue;
+            const int64_t id = pending[c].front()->id;
+            if (best == -2 || id < best_id) {
+                best = c;
+                best_id = id;
+            }
+        }
+        return best;
+    }
+
+    // Forms and launches one batch of class c on slot k (solo: one request).
+    void launch(int c, int k) {
+        cudaError_t stale = cudaGetLastError();  // not this batch's
         if (stale != cudaSuccess && !warned) {
             warned = true;
-            std::fprintf(stderr, "tc_server: cleared a CUDA error left by '%s' before request %lld: %s\n",
-                         last_action, (long long)r.id, cudaGetErrorString(stale));
+            std::fprintf(stderr, "tc_server: cleared a CUDA error left by '%s': %s\n", last_action,
+                         cudaGetErrorString(stale));
         }
-        cudaStream_t st = streams[r.stream];
-        last_action = "cudaMemcpyAsync (inputs)";
-        char *base = (char *)arena_base + r.offset;
-        char *dA = base;
-        char *dB = dA + (r.bytesA + 255) / 256 * 256;
-        char *dC = dB + (r.bytesB + 255) / 256 * 256;
-        cudaError_t e = cudaMemcpyAsync(dA, r.hA, r.bytesA, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess)
-            return fail(TC_ERROR_CUDA, std::string("copy of A (") + std::to_string(r.bytesA) + " bytes at arena offset " +
-                                           std::to_string(r.offset) + "): " + cudaGetErrorString(e));
-        e = cudaMemcpyAsync(dB, r.hB, r.bytesB, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess)
-            return fail(TC_ERROR_CUDA, std::string("copy of B (") + std::to_string(r.bytesB) + " bytes at arena offset " +
-                                           std::to_string(r.offset) + "): " + cudaGetErrorString(e));
-        const double one = 1.0, zero = 0.0;
-        const float onef = 1.0f, zerof = 0.0f;
-        const bool f64 = r.dtype == TC_F64;
-        last_action = "tc_execute";
-        tc_status s = tc_execute(r.plan, f64 ? (const void *)&one : (const void *)&onef, dA, dB,
-                                 f64 ? (const void *)&zero : (const void *)&zerof, dC, st);
-        if (s != TC_SUCCESS) return fail(s, std::string("execute: ") + tc_last_error());
-        if (r.hC) {
+        Slot &S = streams[k];
+        cudaStream_t st = S.stream;
+        S.reqs.clear();
+        tc_status s = TC_SUCCESS;
+        std::string msg;
+        if (c == kClasses) {  // solo: the plan's own GETT (compensated or other tensor dtypes)
+            std::unique_ptr<Request> r = std::move(pending[c].front());
+            pending[c].pop_front();
+            s = copy_in(*r, st);
+            char *dA, *dB, *dC;
+            operands(*r, &dA, &dB, &dC);
+            if (s == TC_SUCCESS) {
+                Plan &p = *r->plan;
+                p.device = device;
+                p.dev_status = S.dstatus;  // the slot's status word: nothing to allocate
+                p.gett_pack = 0;           // no workspace
+                const double one = 1.0, zero = 0.0;
+                const float onef = 1.0f, zerof = 0.0f;
+                const bool f64 = r->dtype == TC_F64;
+                last_action = "exec_gett (solo)";
+                s = exec_gett(p, f64 ? (const void *)&one : (const void *)&onef, dA, dB,
+                              f64 ? (const void *)&zero : (const void *)&zerof, dC, st);
+                p.dev_status = nullptr;
+                if (s != TC_SUCCESS) msg = std::string("execute: ") + tc_last_error();
+            }
+            S.reqs.push_back(std::move(r));
+        } else {
+            // one descriptor per request, the flattened tile list, one launch
+            const bool simt = c < 2;
+            int bn = 128;
+            if (!simt) {
+                const Plan &p0 = *pending[c].front()->plan;
+                int64_t N = 1;
+                for (int id : p0.freeB) N *= p0.ext[id];
+                bn = N >= 256 ? 256 : 128;
+            }
+            // descriptors at the stride of the kernel's own descriptor type
+            const size_t stride = simt ? simt_desc_bytes() : gett_desc_bytes();
+            int64_t ntiles = 0;
+            while (!pending[c].empty() && (int)S.reqs.size() < kMaxBatchProblems) {
+                Request &r = *pending[c].front();
+                char *dA, *dB, *dC;
+                operands(r, &dA, &dB, &dC);
+                char *hd = S.hdesc + S.reqs.size() * stride;
+                const int64_t t = simt ? simt_fill_desc(*r.plan, dA, dB, dC, ntiles, hd)
+                                       : gett_fill_plan_desc(*r.plan, bn, dA, dB, dC, ntiles, hd);
+                if (t >= 0 && ntiles + t > kMaxBatchTiles && !S.reqs.empty()) break;  // the next batch's
+                if (t < 0 || ntiles + t > kMaxBatchTiles) {
+                    // a request no batch can hold: it fails alone, the batch goes on
+                    std::unique_ptr<Request> bad = std::move(pending[c].front());
+                    pending[c].pop_front();
+                    finish(bad, fail(TC_ERROR_INVALID_ARGUMENT, t < 0 ? "request has too many contracted modes"
+                                                                      : "request has more tiles than a batch holds"));
+                    continue;
+                }
+                for (int64_t x = 0; x < t; ++x) S.htile[ntiles + x] = (int32_t)S.reqs.size();
+                ntiles += t;
+                s = copy_in(r, st);
+                S.reqs.push_back(std::move(pending[c].front()));
+                pending[c].pop_front();
+                if (s != TC_SUCCESS) break;
+            }
+            if (s == TC_SUCCESS && !S.reqs.empty()) {
+                last_action = "cudaMemcpyAsync (batch tables)";
+                cudaError_t e = cudaMemcpyAsync(S.ddesc, S.hdesc, S.reqs.size() * stride,
+                                                cudaMemcpyHostToDevice, st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(S.dtile, S.htile, (size_t)ntiles * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+                if (e != cudaSuccess) s = fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+            }
+            if (s == TC_SUCCESS && !S.reqs.empty()) {
+                last_action = "batched launch";
+                if (simt)
+                    s = simt_launch_batch(c == 0 ? TC_F64 : TC_F32, S.ddesc, S.dtile, ntiles, st);
+                else
+                    s = gett_launch_batch(S.ddesc, S.dtile, 0, ntiles, bn, 1.0f, 0.0f, 6, S.dstatus, 0,
+                                          c == 3 ? 1 : 0, st);
+                if (s != TC_SUCCESS) msg = std::string("batched launch: ") + tc_last_error();
+            }
+        }
+        // results out, the status word, the completion event
+        for (auto &r : S.reqs) {
+            if (s != TC_SUCCESS || !r->hC) continue;
+            char *dA, *dB, *dC;
+            operands(*r, &dA, &dB, &dC);
             last_action = "cudaMemcpyAsync (result)";
-            e = cudaMemcpyAsync(r.hC, dC, r.bytesC, cudaMemcpyDeviceToHost, st);
-            if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+            cudaError_t e = cudaMemcpyAsync(r->hC, dC, r->bytesC, cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) s = fail(TC_ERROR_CUDA, cudaGetErrorString(e));
         }
-        last_action = "cudaEventCreate/Record";
-        e = cudaEventCreateWithFlags(&r.done_event, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventRecord(r.done_event, st);
-        return e == cudaSuccess ? TC_SUCCESS : fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+        if (s == TC_SUCCESS) {
+            last_action = "status word / event";
+            cudaError_t e = cudaMemcpyAsync(S.hstatus, S.dstatus, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaEventRecord(S.done, st);
+            if (e != cudaSuccess) s = fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+        }
+        if (s != TC_SUCCESS) {
+            cudaStreamSynchronize(st);
+            for (auto &r : S.reqs) finish(r, s, msg);
+            S.reqs.clear();
+            return;
+        }
+        S.busy = true;
+        std::lock_guard<std::mutex> g(mu);
+        ++batches;
+        max_batch = std::max<int64_t>(max_batch, (int64_t)S.reqs.size());
     }
 
     void run() {
         cudaSetDevice(device);
         for (;;) {
-            // completions
-            for (size_t i = 0; i < inflight.size();) {
+            bool progressed = false;
+            // completions: a batch is done when its event is
+            for (Slot &S : streams) {
+                if (!S.busy) continue;
                 last_action = "cudaEventQuery";
-                cudaError_t q = cudaEventQuery(inflight[i]->done_event);
-                if (q == cudaErrorNotReady) {
-                    ++i;
-                    continue;
+                cudaError_t q = cudaEventQuery(S.done);
+                if (q == cudaErrorNotReady) continue;
+                tc_status st = TC_SUCCESS;
+                std::string msg;
+                if (q != cudaSuccess) {
+                    st = TC_ERROR_CUDA;
+                    msg = std::string("completion: ") + cudaGetErrorString(q);
+                } else if (*S.hstatus != 0) {
+                    st = TC_ERROR_TIMEOUT;
+                    msg = "a bounded device wait gave up";
+                    *S.hstatus = 0;
+                    cudaMemsetAsync(S.dstatus, 0, sizeof(int), S.stream);
                 }
-                finish(inflight[i], q == cudaSuccess ? TC_SUCCESS : TC_ERROR_CUDA,
-                       q == cudaSuccess ? "" : std::string("completion: ") + cudaGetErrorString(q));
-                inflight.erase(inflight.begin() + i);
+                for (auto &r : S.reqs) finish(r, st, msg);
+                S.reqs.clear();
+                S.busy = false;
+                progressed = true;
             }
             // admissions, in arrival order
-            std::unique_ptr<Request> r;
+            for (;;) {
+                std::unique_ptr<Request> r;
+                {
+                    std::unique_lock<std::mutex> g(mu);
+                    if (queue.empty() || admitted >= slots) break;
+                    Request &h = *queue.front();
+                    const size_t need = (h.bytesA + 255) / 256 * 256 + (h.bytesB + 255) / 256 * 256 +
+                                        (h.bytesC + 255) / 256 * 256;
+                    size_t off = 0;
+                    if (!arena.alloc(need, &off)) {
+                        ++stalls;  // waits for memory to come back
+                        break;
+                    }
+                    r = std::move(queue.front());
+                    queue.pop_front();
+                    r->offset = off;
+                    r->bytes = need;
+                    ++admitted;
+                    peak_inflight = std::max<int64_t>(peak_inflight, (int64_t)admitted);
+                }
+                const int c = r->cls == kSolo ? kClasses : r->cls;
+                pending[c].push_back(std::move(r));
+                progressed = true;
+            }
+            // launches: every free stream takes the next class's batch
+            for (size_t k = 0; k < streams.size(); ++k) {
+                if (streams[k].busy) continue;
+                const int c = next_class();
+                if (c < 0) break;
+                launch(c, (int)k);
+                progressed = true;
+            }
             {
                 std::unique_lock<std::mutex> g(mu);
-                if (stop && queue.empty() && inflight.empty()) return;
-                if (queue.empty() || (int)inflight.size() >= slots) {
-                    if (inflight.empty()) cv.wait_for(g, std::chrono::milliseconds(5));
-                    else g.unlock(), std::this_thread::sleep_for(std::chrono::microseconds(20));
-                    continue;
+                bool busy = false;
+                for (Slot &S : streams) busy |= S.busy;
+                bool waiting = next_class() >= 0;
+                if (stop && queue.empty() && !busy && !waiting) return;
+                if (!progressed) {
+                    if (!busy && !waiting && queue.empty()) cv.wait_for(g, std::chrono::milliseconds(5));
+                    else {
+                        g.unlock();
+                        std::this_thread::sleep_for(std::chrono::microseconds(20));
+                    }
                 }
-                Request &h = *queue.front();
-                const size_t need = (h.bytesA + 255) / 256 * 256 + (h.bytesB + 255) / 256 * 256 +
-                                    (h.bytesC + 255) / 256 * 256;
-                size_t off = 0;
-                if (!arena.alloc(need, &off)) {
-                    ++stalls;  // waits for memory to come back
-                    g.unlock();
-                    std::this_thread::sleep_for(std::chrono::microseconds(20));
-                    continue;
-                }
-                r = std::move(queue.front());
-                queue.pop_front();
-                r->offset = off;
-                r->bytes = need;
             }
-            // plans are cached per stream: one plan never runs on two
-            // streams at once (tc_execute refuses that)
-            r->stream = rr++ % (int)streams.size();
-            const std::string pkey = key(*r) + "#" + std::to_string(r->stream);
-            auto it = plans.find(pkey);
-            if (it == plans.end()) {
-                tc_plan p = nullptr;
-                tc_status s = tc_plan_create(&p, r->spec.c_str(), r->extents.data(), nullptr, r->dtype);
-                // requests on one stream reuse its plan back to back: no plan
-                // workspace (the GETT's pre-converted input) to keep apart
-                if (s == TC_SUCCESS) s = tc_plan_set_gett_pack(p, 0);
-                if (s != TC_SUCCESS) {
-                    if (p) tc_plan_destroy(p);
-                    finish(r, s);
-                    continue;
-                }
-                it = plans.emplace(pkey, p).first;
-            }
-            r->plan = it->second;  // algorithm 0, the fused GETT
-            tc_status s = launch(*r);
-            if (s != TC_SUCCESS) {
-                cudaStreamSynchronize(streams[r->stream]);
-                finish(r, s);
-                continue;
-            }
-            inflight.push_back(std::move(r));
-            std::lock_guard<std::mutex> g(mu);
-            peak_inflight = std::max<int64_t>(peak_inflight, (int64_t)inflight.size());
         }
     }
 };
@@ -312,16 +447,36 @@ tc_status tc_server_create(tc_server *out, int64_t budget_bytes, int32_t slots, 
     cudaGetDevice(&S.device);
     S.budget = budget_bytes;
     S.slots = slots;
+    S.desc_bytes = std::max(simt_desc_bytes(), gett_desc_bytes());
+    // per stream: descriptors, tile table, status word (256-byte aligned parts)
+    const size_t dbytes = ((size_t)kMaxBatchProblems * S.desc_bytes + 255) / 256 * 256;
+    const size_t tbytes = (size_t)kMaxBatchTiles * sizeof(int32_t);
+    const size_t per = dbytes + tbytes + 256;
     cudaError_t e = cudaMalloc(&S.arena_base, (size_t)budget_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&S.ctrl_dev, per * streams);
+    if (e == cudaSuccess) e = cudaHostAlloc(&S.ctrl_host, per * streams, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMemset(S.ctrl_dev, 0, per * streams);
     if (e != cudaSuccess) {
+        if (S.arena_base) cudaFree(S.arena_base);
+        if (S.ctrl_dev) cudaFree(S.ctrl_dev);
+        if (S.ctrl_host) cudaFreeHost(S.ctrl_host);
         delete h;
         return fail(TC_ERROR_OUT_OF_MEMORY, cudaGetErrorString(e));
     }
+    std::memset(S.ctrl_host, 0, per * streams);
     S.arena.init((size_t)budget_bytes);
+    S.streams.resize(streams);
     for (int i = 0; i < streams; ++i) {
-        cudaStream_t st;
-        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        S.streams.push_back(st);
+        Slot &k = S.streams[i];
+        cudaStreamCreateWithFlags(&k.stream, cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&k.done, cudaEventDisableTiming);
+        char *hd = (char *)S.ctrl_host + per * i, *dd = (char *)S.ctrl_dev + per * i;
+        k.hdesc = hd;
+        k.ddesc = dd;
+        k.htile = (int32_t *)(hd + dbytes);
+        k.dtile = (int32_t *)(dd + dbytes);
+        k.hstatus = (int *)(hd + dbytes + tbytes);
+        k.dstatus = (int *)(dd + dbytes + tbytes);
     }
     S.worker = std::thread([&S] { S.run(); });
     *out = h;
@@ -333,24 +488,29 @@ tc_status tc_server_submit(tc_server server, const char *spec, const int64_t *ex
     if (!server || !spec || !extents || !A || !B || !request_id)
         return fail(TC_ERROR_INVALID_ARGUMENT, "NULL argument");
     ServerImpl &S = server->s;
-    // validate and size the request with a throw-away plan (host work only)
-    tc_plan p = nullptr;
-    tc_status s = tc_plan_create(&p, spec, extents, nullptr, dtype);
-    if (s != TC_SUCCESS) return s;
+    // validate and size the request: spec, classes and layouts only (the
+    // request runs the GETT; its plan has no other algorithm)
     auto r = std::make_unique<Request>();
-    r->spec = spec;
-    r->extents.assign(extents, extents + p->p.nidx);
+    r->plan = std::make_unique<Plan>();
+    tc_status s = build_plan(*r->plan, spec, extents, nullptr, dtype, false);
+    if (s != TC_SUCCESS) return s;
+    const Plan &p = *r->plan;
     r->dtype = dtype;
     r->hA = A;
     r->hB = B;
     r->hC = C;
-    r->bytesA = operand_bytes(p->p, OP_A);
-    r->bytesB = operand_bytes(p->p, OP_B);
-    r->bytesC = operand_bytes(p->p, OP_C);
-    double f = 0;
-    tc_plan_flops(p, &f);
+    r->bytesA = operand_bytes(p, OP_A);
+    r->bytesB = operand_bytes(p, OP_B);
+    r->bytesC = operand_bytes(p, OP_C);
+    double f = 2.0;
+    for (int x = 0; x < p.nidx; ++x) f *= (double)p.ext[x];
     r->flops = f;
-    tc_plan_destroy(p);
+    for (int id : p.contracted) r->K *= p.ext[id];
+    // batch class: the SIMT GETT (FP64, FP32), split-BF16 by K, else solo
+    if (dtype == TC_F64) r->cls = 0;
+    else if (dtype == TC_F32) r->cls = 1;
+    else if (dtype == TC_BF16X3 && r->K <= kBatchMaxK) r->cls = r->K >= kSplitMinK ? 3 : 2;
+    else r->cls = kSolo;
     const size_t need = (r->bytesA + 255) / 256 * 256 + (r->bytesB + 255) / 256 * 256 + (r->bytesC + 255) / 256 * 256;
     if ((int64_t)need > S.budget) return fail(TC_ERROR_ADMISSION, "request larger than the whole budget");
     r->t_submit = Clock::now();
@@ -407,6 +567,8 @@ tc_status tc_server_stats(tc_server server, tc_server_report *out) {
     out->peak_inflight = S.peak_inflight;
     out->queued = (int64_t)S.queue.size();
     out->flops_served = S.flops_served;
+    out->batches = S.batches;
+    out->max_batch = S.max_batch;
     if (S.any && S.completed > 0)
         out->span_seconds = std::chrono::duration<double>(S.t_last - S.t_first).count();
     if (!S.latencies.empty()) {
@@ -429,9 +591,13 @@ tc_status tc_server_destroy(tc_server server) {
     }
     S.cv.notify_all();
     if (S.worker.joinable()) S.worker.join();  // drains the queue first
-    for (auto &kv : S.plans) tc_plan_destroy(kv.second);
-    for (cudaStream_t st : S.streams) cudaStreamDestroy(st);
+    for (Slot &k : S.streams) {
+        cudaStreamDestroy(k.stream);
+        cudaEventDestroy(k.done);
+    }
     if (S.arena_base) cudaFree(S.arena_base);
+    if (S.ctrl_dev) cudaFree(S.ctrl_dev);
+    if (S.ctrl_host) cudaFreeHost(S.ctrl_host);
     delete server;
     return TC_SUCCESS;
 }

@@ -62,7 +62,8 @@ class tc_server_report(ctypes.Structure):
                 ("admission_stalls", ctypes.c_int64), ("peak_inflight", ctypes.c_int64),
                 ("queued", ctypes.c_int64), ("flops_served", ctypes.c_double),
                 ("span_seconds", ctypes.c_double), ("p50_seconds", ctypes.c_double),
-                ("p99_seconds", ctypes.c_double), ("max_seconds", ctypes.c_double)]
+                ("p99_seconds", ctypes.c_double), ("max_seconds", ctypes.c_double),
+                ("batches", ctypes.c_int64), ("max_batch", ctypes.c_int64)]
 
 
 _lib = None

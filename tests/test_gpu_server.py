@@ -104,3 +104,60 @@ def test_oversize_request_is_refused(tcmod):
         server.submit("abc=ai,ibc", [256, 256, 256, 16], "f32", hA, hA, None)
     assert tcmod.STATUS_NAMES[e.value.status] == "TC_ERROR_ADMISSION"
     server.close()
+
+
+def test_requests_share_launches(tcmod):
+    # 48 requests submitted at once on two streams: they are batched into
+    # shared launches (far fewer launches than requests), every result
+    # matches the oracle, and each equals the same request run alone
+    rng = np.random.default_rng(11)
+    reqs = []
+    for q in range(48):
+        spec = ("abc=ai,ibc", "abc=iaj,jbic", "ab=aij,jib")[q % 3]
+        dtype = ("f64", "f32", "bf16x3")[q % 3 if q < 24 else (q // 3) % 3]
+        order = synth.index_order(spec)
+        c, a, b = synth.spec_modes(spec)
+        ext = [int(rng.integers(4, 20)) if (x in a and x in b and x not in c) else int(rng.integers(8, 90))
+               for x in order]
+        reqs.append((spec, ext, dtype))
+    bufs = [host_buffers(s, e, d, seed=300 + q) for q, (s, e, d) in enumerate(reqs)]
+    server = tcmod.Server(budget_bytes=1 << 30, slots=64, streams=2)
+    ids = [server.submit(s, e, d, hA, hB, hC) for (s, e, d), (hA, hB, hC) in zip(reqs, bufs)]
+    for rid in ids:
+        server.wait(rid, 120.0)
+    st = server.stats()
+    assert st["completed"] == 48 and st["failed"] == 0
+    assert st["batches"] < 48 and st["max_batch"] > 1, st
+    mixed = [hC.clone() for _, _, hC in bufs]
+    for q, ((spec, ext, dtype), (hA, hB, hC)) in enumerate(zip(reqs, bufs)):
+        Ar, Br = hA.double().numpy(), hB.double().numpy()
+        want = oc.contract(spec, ext, Ar, Br)
+        scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
+        c, a, b = synth.spec_modes(spec)
+        K = int(np.prod([e for x, e in zip(synth.index_order(spec), ext) if x in a and x in b and x not in c]))
+        bound = {"f64": 1e-12, "f32": (K + 1) * U32, "bf16x3": 1e-6}[dtype]
+        assert np.max(np.abs(mixed[q].double().numpy() - want) / scale) <= bound, (q, spec, ext, dtype)
+    for q in range(0, 48, 5):  # alone, on the idle server
+        (spec, ext, dtype), (hA, hB, hC) = reqs[q], bufs[q]
+        hC.fill_(float("nan"))
+        server.wait(server.submit(spec, ext, dtype, hA, hB, hC), 60.0)
+        assert torch.equal(hC, mixed[q]), (q, spec, ext, dtype)
+    server.close()
+
+
+@pytest.mark.parametrize("spec,ext,dtype", [
+    ("ab=aij,jib", [100, 120, 24, 20], "bf16x3"),   # K = 480: compensated, one launch of its own
+    ("abc=iaj,jbic", [40, 36, 24, 16, 16], "bf16x3"),  # K = 256: the split-accumulator class
+    ("abc=ai,ibc", [64, 48, 40, 32], "tf32"),      # another tensor dtype: one launch of its own
+])
+def test_solo_and_split_classes(tcmod, spec, ext, dtype):
+    hA, hB, hC = host_buffers(spec, ext, dtype, seed=7)
+    server = tcmod.Server(budget_bytes=1 << 28, slots=4, streams=2)
+    server.wait(server.submit(spec, ext, dtype, hA, hB, hC), 60.0)
+    assert server.stats()["failed"] == 0
+    server.close()
+    Ar, Br = hA.double().numpy(), hB.double().numpy()
+    want = oc.contract(spec, ext, Ar, Br)
+    scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
+    err = float(np.max(np.abs(hC.double().numpy() - want) / scale))
+    assert err <= (1e-6 if dtype == "bf16x3" else 2 * 2.0 ** -11 + 1e-5), err
