@@ -8,7 +8,10 @@
  *     C[f] = alpha * sum_{k contracted} A[f_A, k] * B[f_B, k] + beta * C[f]
  *
  * An index that appears in both inputs and not in C is contracted; an index
- * that appears in exactly one input and in C is free.  Every algorithm the
+ * that appears in exactly one input and in C is free.  Beyond the paper's
+ * notation, an index in A, B and C is a batch (Hadamard) index: C and both
+ * inputs are indexed by it, nothing is summed over it, and in every
+ * algorithm it is a sliced loop (never a kernel index).  Every algorithm the
  * library runs is one of the loop nests of Section 2 (slicing rules of
  * Table 1: a loop nest around one dot, axpy, gemv, ger or gemm kernel, with
  * copies where a matrix slice has no unit-stride dimension), or the fused
@@ -117,11 +120,11 @@ typedef struct {
 } tc_algorithm;
 
 /* Parses the spec, classifies the indices, validates extents and strides
- * and enumerates the algorithms (Section 2, Table 1).  No device work and
- * no device memory.  Rejects: an index in all three operands or in one
- * input only, a repeated index within an operand, more than 8 modes per
- * operand, extents < 1, strides < 1, and C strides under which two C
- * elements share an address.  *out is NULL on failure. */
+ * and enumerates the algorithms (Section 2, Table 1; batch indices are
+ * sliced in all of them).  No device work and no device memory.  Rejects:
+ * an index in one input only, a repeated index within an operand, more
+ * than 8 modes per operand, extents < 1, strides < 1, and C strides under
+ * which two C elements share an address.  *out is NULL on failure. */
 tc_status tc_plan_create(tc_plan *out, const char *spec, const int64_t *extents,
                          const int64_t *strides, tc_dtype dtype);
 

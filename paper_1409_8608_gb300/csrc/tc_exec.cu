@@ -754,7 +754,7 @@ void describe_gett_simt(const Plan &p, T alpha, const T *A, const T *B, T beta, 
     fill(td.m, mi);
     fill(td.n, ni);
     fill(td.red, ki);
-    td.task.n = 0;
+    fill(td.task, p.batch);  // batch indices: one task per value, all three operands offset
     td.M = td.N = td.K = 1;
     for (int id : mi) td.M *= p.ext[id];
     for (int id : ni) td.N *= p.ext[id];
@@ -775,6 +775,12 @@ void describe_gett_simt(const Plan &p, T alpha, const T *A, const T *B, T beta, 
     td.tiles_n = (td.N + bm - 1) / bm;
 }
 
+int64_t task_count(const TileDesc &td) {
+    int64_t t = 1;
+    for (int m = 0; m < td.task.n; ++m) t *= td.task.ext[m];
+    return t;
+}
+
 template <typename T>
 tc_status run_gett_simt(Plan &p, T alpha, const T *A, const T *B, T beta, T *C,
                         cudaStream_t st, const Probe *probe) {
@@ -783,10 +789,12 @@ tc_status run_gett_simt(Plan &p, T alpha, const T *A, const T *B, T beta, T *C,
     auto cut = [&](int64_t n) {
         return !probe || probe->fraction >= 1.0 ? n : std::max<int64_t>(1, (int64_t)(n * probe->fraction));
     };
+    const int64_t tiles = td.tiles_m * td.tiles_n * task_count(td);
+    if (tiles > 0x7fffffff) return fail(TC_ERROR_INVALID_EXTENT, "too many tiles for one launch");
     if constexpr (sizeof(T) == 8)
-        tile_kernel<T, 64, 64, 16, 4, 4><<<(unsigned)cut(td.tiles_m * td.tiles_n), 256, 0, st>>>(td);
+        tile_kernel<T, 64, 64, 16, 4, 4><<<(unsigned)cut(tiles), 256, 0, st>>>(td);
     else
-        tile_kernel<T, 128, 128, 16, 8, 8><<<(unsigned)cut(td.tiles_m * td.tiles_n), 256, 0, st>>>(td);
+        tile_kernel<T, 128, 128, 16, 8, 8><<<(unsigned)cut(tiles), 256, 0, st>>>(td);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? TC_SUCCESS
                             : fail(TC_ERROR_CUDA, std::string("GETT tile_kernel launch (") +
@@ -806,7 +814,7 @@ int64_t simt_fill_desc(const Plan &p, const void *A, const void *B, void *C, int
         describe_gett_simt<float>(p, 1.0f, (const float *)A, (const float *)B, 0.0f, (float *)C, td);
     td.tile0 = tile0;
     std::memcpy(out, &td, sizeof(td));
-    return td.tiles_m * td.tiles_n;
+    return td.tiles_m * td.tiles_n * task_count(td);
 }
 
 tc_status simt_launch_batch(tc_dtype dt, const void *ddescs, const int32_t *dtile_prob, int64_t ntiles,
@@ -840,13 +848,14 @@ int64_t nest_phase_items(const Plan &p, const Algorithm &alg, bool *tiled) {
 }
 
 int64_t gett_items(const Plan &p) {
-    int64_t M = 1, N = 1;
+    int64_t M = 1, N = 1, H = 1;
     for (int id : p.freeA) M *= p.ext[id];
     for (int id : p.freeB) N *= p.ext[id];
-    if (p.dtype == TC_F64) return ((M + 63) / 64) * ((N + 63) / 64);
-    if (p.dtype == TC_F32) return ((M + 127) / 128) * ((N + 127) / 128);
+    for (int id : p.batch) H *= p.ext[id];
+    if (p.dtype == TC_F64) return ((M + 63) / 64) * ((N + 63) / 64) * H;
+    if (p.dtype == TC_F32) return ((M + 127) / 128) * ((N + 127) / 128) * H;
     const int64_t bn = p.gett_bn ? p.gett_bn : (N >= 256 ? 256 : 128);
-    return ((M + 127) / 128) * ((N + bn - 1) / bn);
+    return ((M + 127) / 128) * ((N + bn - 1) / bn) * H;
 }
 
 size_t nest_workspace_bytes(const Plan &p, const Algorithm &alg) {

@@ -84,6 +84,10 @@ struct GettDesc {
     int64_t k_ext[kMaxModes], k_sA[kMaxModes], k_sB[kMaxModes];  // outermost first
     int64_t M, N, K;
     int64_t tiles_m, tiles_n;
+    // batch (Hadamard) indices, in A, B and C: the tile list runs over
+    // batch values outermost, then N tiles, then M tiles (batch_offsets)
+    int nb;
+    int64_t b_ext[kMaxModes], b_sA[kMaxModes], b_sB[kMaxModes], b_sC[kMaxModes];
     const void *A;
     const void *B;
     float *C;
@@ -125,6 +129,13 @@ struct GettDesc {
     const char *pk_base;
     int64_t pk_tile_bytes;  // one row tile's images (every K stage)
 };
+
+// number of batch values of a descriptor (1 without batch indices)
+inline int64_t batch_count(const GettDesc &d) {
+    int64_t h = 1;
+    for (int m = 0; m < d.nb; ++m) h *= d.b_ext[m];
+    return h;
+}
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -706,6 +717,25 @@ __device__ __forceinline__ void copy_packed(const char *src, char *dst, int pt) 
     }
 }
 
+// Batch indices: tile lt of a problem is tile lt % (tiles_m * tiles_n) of
+// batch value lt / (tiles_m * tiles_n); returns the former and adds the
+// batch value's offsets in A, B and C (first batch index fastest).
+__device__ __forceinline__ int64_t batch_offsets(const GettDesc &P, int64_t lt, int64_t &oA, int64_t &oB,
+                                                 int64_t &oC) {
+    oA = oB = oC = 0;
+    if (P.nb == 0) return lt;
+    int64_t r;
+    int64_t bt = divmod(lt, P.tiles_m * P.tiles_n, r);
+    for (int m = 0; m < P.nb; ++m) {
+        int64_t v;
+        bt = divmod(bt, P.b_ext[m], v);
+        oA += v * P.b_sA[m];
+        oB += v * P.b_sB[m];
+        oC += v * P.b_sC[m];
+    }
+    return r;
+}
+
 // The descriptor of a tile's problem: the launch's own, or in the batched
 // form the one its tile-to-problem table names.
 template <bool BATCH>
@@ -1041,10 +1071,11 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop && !grouped && !PAIR;
              tile += gridDim.x, ++it) {
             const GettDesc &P = tile_desc<BATCH>(d, tile);
-            const int64_t lt = BATCH ? tile - P.tile0 : tile;
+            int64_t boA, boB, boC;
+            const int64_t lt = batch_offsets(P, BATCH ? tile - P.tile0 : tile, boA, boB, boC);
             const int nkt_t = BATCH ? (int)((P.K + BK - 1) / BK) : nkt;
-            const In *__restrict__ Ap = (const In *)P.A;
-            const In *__restrict__ Bp = (const In *)P.B;
+            const In *__restrict__ Ap = (const In *)P.A + boA;
+            const In *__restrict__ Bp = (const In *)P.B + boB;
             int64_t mt;
             const int64_t nt = divmod(lt, P.tiles_m, mt);
             const int64_t m0 = mt * kBM, n0 = nt * BN;
@@ -1322,8 +1353,9 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                 om = et < rec[1] ? rec[4] + (int64_t)et * rec[2] : -1;
             } else {
                 const GettDesc &P = tile_desc<BATCH>(d, tile);
-                const int64_t lt = BATCH ? tile - P.tile0 : tile;
-                C = P.C;
+                int64_t boA, boB, boC;
+                const int64_t lt = batch_offsets(P, BATCH ? tile - P.tile0 : tile, boA, boB, boC);
+                C = P.C + boC;
                 int64_t mt;
                 const int64_t nt = divmod(lt, P.tiles_m, mt);
                 // pairs: this CTA's 128 rows of the 256-row tile; every CTA
@@ -1598,7 +1630,7 @@ template <int KIND>
 tc_status launch_kind(GettDesc &d, int bn, bool tma, bool comp, bool pair, const CUtensorMap &ta,
                       const CUtensorMap &tb, cudaStream_t st) {
     d.tiles_n = (d.N + bn - 1) / bn;
-    d.num_tiles = d.tiles_m * d.tiles_n;
+    d.num_tiles = d.tiles_m * d.tiles_n * batch_count(d);
     if (d.tile_frac < 1.0) d.num_tiles = std::max<int64_t>(1, (int64_t)(d.num_tiles * d.tile_frac));
     // CTA pairs (tiles of 256 x 256): four operand stages of 128 + 128
     // rows and three staging slots of two-stage boxes
@@ -1817,7 +1849,7 @@ bool plan_tma_operand(const Plan &p, int opnd, const void *base, int in_bytes, i
 // input with fewer elements) and a bound on its stage images' bytes.
 int pack_choice(const Plan &p, int64_t &bound) {
     bound = 0;
-    if ((p.dtype != TC_BF16X3 && p.dtype != TC_TF32) || p.gett_pack == 0) return 0;
+    if ((p.dtype != TC_BF16X3 && p.dtype != TC_TF32) || p.gett_pack == 0 || !p.batch.empty()) return 0;
     int64_t M = 1, N = 1, K = 1;
     for (int id : p.freeA) M *= p.ext[id];
     for (int id : p.freeB) N *= p.ext[id];
@@ -1943,8 +1975,17 @@ tc_status describe_modes(const Plan &p, int pk, GettDesc &d) {
         d.k_sB[m] = kmodes[m].sB;
         d.K *= kmodes[m].ext;
     }
+    d.nb = (int)p.batch.size();
+    for (int m = 0; m < d.nb; ++m) {
+        const int id = p.batch[m];
+        d.b_ext[m] = p.ext[id];
+        d.b_sA[m] = p.op[OP_A].stride_of(id);
+        d.b_sB[m] = p.op[OP_B].stride_of(id);
+        d.b_sC[m] = p.op[OP_C].stride_of(id);
+    }
     return TC_SUCCESS;
 }
+
 
 tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, const void *beta,
                     void *C, void *stream, const Probe *probe) {
@@ -2012,7 +2053,9 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     // compensation, more than one 128-row tile, and every operand either
     // TMA-staged or pre-converted (the converters' grouped path)
     bool pair = false;
-    if (p.gett_tma && d.K < (int64_t(1) << 31)) {  // 32-bit K positions in the TMA warp
+    // batch indices: the global-load path (the TMA warp and the
+    // pre-converted images walk M and N tiles only)
+    if (p.gett_tma && d.nb == 0 && d.K < (int64_t(1) << 31)) {  // 32-bit K positions in the TMA warp
         if (p.gett_pair && (p.dtype == TC_BF16X3 || p.dtype == TC_TF32) && !comp && bn == 256 && d.M > kBM) {
             GettDesc dp = d;
             CUtensorMap pa, pb;
@@ -2150,7 +2193,7 @@ int64_t gett_fill_plan_desc(const Plan &p, int bn, const void *A, const void *B,
     d.tiles_n = (d.N + bn - 1) / bn;
     d.tile0 = tile0;
     std::memcpy(out, &d, sizeof(d));
-    return d.tiles_m * d.tiles_n;
+    return d.tiles_m * d.tiles_n * batch_count(d);
 }
 
 tc_status gett_launch_batch(const void *ddescs, const int32_t *dtile_prob, int64_t t_begin, int64_t t_end, int bn,

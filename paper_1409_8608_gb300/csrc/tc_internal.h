@@ -16,7 +16,9 @@ constexpr int kMaxIdx = 24;     // distinct indices per spec
 
 enum OperandId { OP_A = 0, OP_B = 1, OP_C = 2 };
 
-enum IndexClass { CLS_FREE_A = 0, CLS_FREE_B = 1, CLS_CONTRACTED = 2 };
+// CLS_BATCH: an index in A, B and C (a batch or Hadamard index, outside the
+// paper's notation): never a kernel index, always a sliced (free) loop.
+enum IndexClass { CLS_FREE_A = 0, CLS_FREE_B = 1, CLS_CONTRACTED = 2, CLS_BATCH = 3 };
 
 struct Layout {
     int n = 0;                    // number of modes
@@ -53,7 +55,7 @@ struct Plan {
     int64_t ext[kMaxIdx] = {};
     int cls[kMaxIdx] = {};
     Layout op[3];                   // A, B, C
-    std::vector<int> contracted, freeA, freeB;  // first-appearance order
+    std::vector<int> contracted, freeA, freeB, batch;  // first-appearance order
     std::vector<Algorithm> algs;    // algs[0] is the fused GETT
     int selected = 0;
     int split_products = 6;         // TC_BF16X3: 3, 6 or 9 slice products

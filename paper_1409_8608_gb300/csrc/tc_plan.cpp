@@ -186,16 +186,16 @@ tc_status build_plan(Plan &p, const char *spec, const int64_t *extents, const in
             if (p.letter[x] == ch) return x;
         return -1;
     };
-    // Section 1: contracted = in A and B, not in C; free = in one input and C
+    // Section 1: contracted = in A and B, not in C; free = in one input and
+    // C.  Beyond the paper: an index in A, B and C is a batch (Hadamard)
+    // index -- free, and carried by both inputs.
     for (int x = 0; x < p.nidx; ++x) {
         char ch = p.letter[x];
         bool inA = a.find(ch) != std::string::npos;
         bool inB = b.find(ch) != std::string::npos;
         bool inC = c.find(ch) != std::string::npos;
-        if (inA && inB && inC)
-            return fail(TC_ERROR_INVALID_SPEC,
-                        std::string("index in A, B and C (batch index) not supported: ") + ch);
-        if (inA && inB) p.cls[x] = CLS_CONTRACTED;
+        if (inA && inB && inC) p.cls[x] = CLS_BATCH;
+        else if (inA && inB) p.cls[x] = CLS_CONTRACTED;
         else if (inA && inC) p.cls[x] = CLS_FREE_A;
         else if (inB && inC) p.cls[x] = CLS_FREE_B;
         else
@@ -252,7 +252,8 @@ tc_status build_plan(Plan &p, const char *spec, const int64_t *extents, const in
     for (int x = 0; x < p.nidx; ++x) {
         if (p.cls[x] == CLS_CONTRACTED) p.contracted.push_back(x);
         else if (p.cls[x] == CLS_FREE_A) p.freeA.push_back(x);
-        else p.freeB.push_back(x);
+        else if (p.cls[x] == CLS_FREE_B) p.freeB.push_back(x);
+        else p.batch.push_back(x);
     }
     p.spec = s;
     p.dtype = dtype;

@@ -37,6 +37,11 @@ def test_binding_covers_the_header(lib):
     ("a=iaj,ji", [5, 4, 3]),
     ("ab=ai,ib", [3, 4, 5]),
     ("abcd=iabj,jcid", [2, 3, 4, 5, 2, 3]),
+    # batch (Hadamard) indices: in A, B and C, always sliced loops
+    ("habc=hai,hibc", [3, 6, 5, 4, 2]),
+    ("abh=aih,ibh", [4, 5, 3, 2]),
+    ("hab=ha,hb", [3, 4, 5]),
+    ("gha=giah,hig", [2, 3, 4, 5]),
 ])
 def test_enumeration_matches_oracle(lib, spec, extents):
     plan = tc.Plan(spec, extents)
@@ -78,7 +83,6 @@ def test_phase_counts(lib):
 @pytest.mark.parametrize("spec,extents,strides,status", [
     ("abc", [1, 2, 3], None, "TC_ERROR_INVALID_SPEC"),
     ("abc=ai,ibc,x", [1, 2, 3, 4], None, "TC_ERROR_INVALID_SPEC"),
-    ("abc=aic,ibc", [2, 2, 2, 2], None, "TC_ERROR_INVALID_SPEC"),      # batch index c
     ("ab=aik,ib", [2, 2, 2, 2], None, "TC_ERROR_INVALID_SPEC"),       # k in A only
     ("ab=aai,ib", [2, 2, 2], None, "TC_ERROR_INVALID_SPEC"),          # repeated index
     ("aB=ai,iB", [2, 2, 2], None, "TC_ERROR_INVALID_SPEC"),           # not a-z
@@ -164,3 +168,14 @@ def test_gett_pack_choice(lib):
             plan.set_gett_pack(0)
             assert plan.workspace(0) == 0
             plan.close()
+
+
+def test_batch_indices_are_accepted_and_never_kernel_indices(lib):
+    # an index in A, B and C is a batch index: the plan accepts it, and in
+    # every algorithm it is one of the sliced loops, never a kernel index
+    plan = tc.Plan("habc=hai,hibc", [3, 6, 5, 4, 2])
+    algs = plan.algorithms()
+    assert len(algs) == 1 + 130  # 24 dot + 72 axpy + 18 gemv + 12 ger + 4 gemm
+    for a in algs[1:]:
+        assert "h" in a["loops"] and "h" not in a["kernel_indices"], a["name"]
+    plan.close()

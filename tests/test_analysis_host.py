@@ -59,6 +59,7 @@ def _oracle_cases(spec, ext, alg, cache, line):
     ("abc=iaj,jbic", [24, 20, 16, 16, 16], 50000, 16),
     ("a=iaj,ji", [100, 30, 50], 4096, 8),
     ("ab=aij,jib", [40, 30, 8, 6], 3000, 4),
+    ("habc=hai,hibc", [6, 40, 30, 20, 8], 20000, 8),   # a batch index, always a loop
 ])
 def test_every_case_matches_oracle(lib, spec, extents, cache, line):
     plan = tc.Plan(spec, extents)

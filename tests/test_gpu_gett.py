@@ -91,6 +91,10 @@ CASES = [
     ("abc=iaj,jbic", [130, 40, 9, 5, 7]),     # permuted operands, K = 35
     ("ab=aij,jib", [257, 129, 16, 8]),        # M and N tails, K = 128
     ("abc=ai,ibc", [64, 64, 64, 8]),          # the small plain shape, K < one stage
+    # batch (Hadamard) indices: one tile walk per batch value (global loads)
+    ("habc=hai,hibc", [3, 150, 20, 13, 24]),  # batch outermost in C, ragged M and N
+    ("abh=aih,ibh", [130, 300, 3, 40]),       # batched matrix product, batch last
+    ("hab=ha,hb", [5, 140, 260]),             # Hadamard outer product, no contracted index
 ]
 DTYPES = ["bf16", "f16", "tf32", "bf16x3"]
 

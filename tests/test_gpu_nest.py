@@ -82,6 +82,11 @@ CASES = [
     ("ab=aij,jib", [70, 67, 5, 3]),           # ragged, gemm tiles with tails
     ("a=iaj,ji", [37, 9, 11]),                # Test 2: BLAS-1/2 only
     ("abc=bi,iac", [9, 7, 5, 4]),             # C slices without a unit stride: C copies
+    # batch (Hadamard) indices: always sliced, free loops with strides in A, B and C
+    ("habc=hai,hibc", [3, 20, 13, 9, 8]),     # 130 algorithms
+    ("abh=aih,ibh", [33, 27, 3, 7]),          # batched matrix product
+    ("hab=ha,hb", [4, 30, 20]),               # Hadamard outer product, no contracted index
+    ("gha=giah,hig", [3, 4, 20, 5]),          # two batch indices in different orders
 ]
 
 

@@ -82,3 +82,30 @@ def test_strides_decide_copies():
     gemm = [a for a in algs if a["kernel"] == "gemm"]
     assert len(gemm) == 1 and gemm[0]["copies"] == {"A": -1}
     assert gemm[0]["name"] == "'-gemm"
+
+
+@pytest.mark.parametrize("spec", ["habc=hai,hibc", "abh=aih,ibh", "hab=ha,hb", "gha=giah,hig"])
+def test_batch_indices_counts_and_roles(spec):
+    # Table 1 read with batch indices (in A, B and C; beyond the paper's
+    # notation): they fit no kernel role, so they are sliced in every
+    # algorithm.  Per kernel the count is then (kernel-index choices) x
+    # (number of sliced indices)!, written out here from the role counts of
+    # Table 1, not from the generator.
+    import math
+    c, a, b = (s for s in spec.replace(" ", "").replace("=", ",").split(","))
+    order = index_order(spec)
+    n = len(order)
+    K = [x for x in order if x in a and x in b and x not in c]
+    FA = [x for x in order if x in a and x in c and x not in b]
+    FB = [x for x in order if x in b and x in c and x not in a]
+    H = [x for x in order if x in a and x in b and x in c]
+    assert H
+    f = math.factorial
+    want = {"dot": len(K) * f(n - 1), "axpy": (len(FA) + len(FB)) * f(n - 1),
+            "gemv": (len(FA) + len(FB)) * len(K) * f(n - 2) if n >= 2 else 0,
+            "ger": len(FA) * len(FB) * f(n - 2) if n >= 2 else 0,
+            "gemm": len(FA) * len(FB) * len(K) * f(n - 3) if n >= 3 else 0}
+    algs = oa.enumerate_algorithms(spec)
+    assert oa.count_by_kernel(algs) == want
+    for alg in algs:
+        assert set(H) <= set(alg["loops"]) and not set(H) & set(alg["kernel_indices"]), alg["name"]

@@ -18,6 +18,12 @@ SPECS = [
     ("a=iaj,ji", [4, 3, 5]),            # a i j
     ("abc=ija,jbic", [3, 2, 4, 3, 2]),
     ("ab=ai,ib", [7, 6, 5]),
+    # batch (Hadamard) indices, in A, B and C: beyond the paper's notation;
+    # the definition extends with f_A and f_B sharing the batch index
+    ("habc=hai,hibc", [3, 4, 3, 5, 2]),
+    ("abh=aih,ibh", [4, 5, 3, 2]),
+    ("hab=ha,hb", [3, 4, 5]),
+    ("gha=giah,hig", [2, 3, 4, 5]),
 ]
 
 
@@ -199,3 +205,21 @@ def test_scalar_output():
     B = np.arange(2.0, 9.0)
     C = oc.contract("=i,i", [7], A, B)
     assert C.shape == (1,) and C[0] == float(np.dot(A, B))
+
+
+def test_batch_index_is_a_loop_of_matrix_products():
+    # C[:,:,h] = A[:,:,h] @ B[:,:,h] for every h (brute force over the
+    # batch index with numpy.matmul), and the Hadamard case C[h,a,b] =
+    # A[h,a] * B[h,b] with no contracted index
+    a, i, b, h = 9, 7, 8, 5
+    rng = np.random.default_rng(13)
+    A = rng.uniform(-1, 1, a * i * h)
+    B = rng.uniform(-1, 1, i * b * h)
+    C = oc.contract("abh=aih,ibh", [a, b, h, i], A, B).reshape(a, b, h, order="F")
+    A3, B3 = A.reshape(a, i, h, order="F"), B.reshape(i, b, h, order="F")
+    for x in range(h):
+        np.testing.assert_allclose(C[:, :, x], A3[:, :, x] @ B3[:, :, x], rtol=1e-13, atol=1e-13)
+    Ah, Bh = rng.integers(-8, 9, h * a).astype(float), rng.integers(-8, 9, h * b).astype(float)
+    Ch = oc.contract("hab=ha,hb", [h, a, b], Ah, Bh).reshape(h, a, b, order="F")
+    want = Ah.reshape(h, a, order="F")[:, :, None] * Bh.reshape(h, b, order="F")[:, None, :]
+    assert np.array_equal(Ch, want)
