@@ -538,7 +538,8 @@ tc_status launch_gather(const GatherDesc &g, cudaStream_t st) {
     return e == cudaSuccess ? TC_SUCCESS : fail(TC_ERROR_CUDA, cudaGetErrorString(e));
 }
 
-template <typename T>
+// The gather moves elements of the operand's own size (FP64, FP32, or the
+// 16-bit inputs of the BF16 / FP16 forms).
 tc_status launch_copy(const Plan &p, int o, const OpView &v, const char *src_base,
                       void *dst, bool scatter, cudaStream_t st, double frac = 1.0) {
     GatherDesc g;
@@ -555,7 +556,10 @@ tc_status launch_copy(const Plan &p, int o, const OpView &v, const char *src_bas
     g.total = frac >= 1.0 ? v.elems : std::max<int64_t>(1, (int64_t)(v.elems * frac));
     g.src = scatter ? dst : src_base;
     g.dst = scatter ? (void *)src_base : dst;
-    return launch_gather<T>(g, st);
+    const size_t eb = o == OP_C ? elem_bytes_c(p.dtype) : elem_bytes_ab(p.dtype);
+    if (eb == 8) return launch_gather<double>(g, st);
+    if (eb == 2) return launch_gather<unsigned short>(g, st);
+    return launch_gather<float>(g, st);
 }
 
 template <typename T>
@@ -564,7 +568,9 @@ tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *
     NestLayout L = layout_for(p, alg);
     char *ws = (char *)p.workspace;
     const char *base[3] = {(const char *)A, (const char *)B, (const char *)C};
-    const size_t esz = sizeof(T);
+    const size_t esz = elem_bytes_ab(p.dtype);  // A and B (16 bits for the BF16 / FP16 forms)
+    // tensor-core dtypes run their gemm phases on the tensor-core GETT
+    const bool tensor = p.dtype != TC_F64 && p.dtype != TC_F32;
     // stride of index id in operand o as the phase kernel sees it
     auto stride_in = [&](int o, int id) -> int64_t {
         if (L.view[o].copied) return L.view[o].ws_has[id] ? L.view[o].ws_stride[id] : 0;
@@ -624,7 +630,7 @@ tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *
     if (L.view[OP_C].copied) {
         Cptr = ws + L.ws_offset[OP_C];
         if (init0 != 2 && first_probe) {
-            s = launch_copy<T>(p, OP_C, L.view[OP_C], base[OP_C], Cptr, false, st, frac0);
+            s = launch_copy(p, OP_C, L.view[OP_C], base[OP_C], Cptr, false, st, frac0);
             if (s != TC_SUCCESS) return s;
         }
     }
@@ -651,7 +657,7 @@ tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *
                     if (L.phase_pos[k] <= level) redo = true;
             }
             if (redo) {
-                tc_status cs = launch_copy<T>(p, o, L.view[o], opb[o], dst, false, st, frac);
+                tc_status cs = launch_copy(p, o, L.view[o], opb[o], dst, false, st, frac);
                 if (cs != TC_SUCCESS) return cs;
             }
             if (o == 0) Aeff = dst;
@@ -659,7 +665,27 @@ tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *
         }
         const int init = first ? init0 : 0;
         auto cut = [&](int64_t n) { return frac >= 1.0 ? n : std::max<int64_t>(1, (int64_t)(n * frac)); };
-        if (tiled) {
+        if (tiled && tensor) {
+            NestGemm g;
+            std::memset(&g, 0, sizeof(g));
+            g.m = {td.m.ext[0], td.m.sA[0], 0, td.m.sC[0]};
+            g.n = {td.n.ext[0], 0, td.n.sB[0], td.n.sC[0]};
+            g.nk = td.red.n;
+            for (int m = 0; m < td.red.n; ++m) g.k[m] = {td.red.ext[m], td.red.sA[m], td.red.sB[m], 0};
+            g.nt = td.task.n;  // innermost task loop first (fastest)
+            for (int m = 0; m < td.task.n; ++m) {
+                const int x = td.task.n - 1 - m;
+                g.t[m] = {td.task.ext[x], td.task.sA[x], td.task.sB[x], td.task.sC[x]};
+            }
+            g.A = Aeff;
+            g.B = Beff;
+            g.C = Cptr;
+            g.alpha = (float)alpha;
+            // init 0 (C += alpha acc, the later phases) is beta = 1
+            g.init = init == 2 ? 2 : 1;
+            g.beta = init == 1 ? (float)beta : 1.0f;
+            return gett_launch_nest(p, g, frac, st);
+        } else if (tiled) {
             td.A = Aeff;
             td.B = Beff;
             td.C = Cptr;
@@ -716,7 +742,7 @@ tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *
         changed_from = k;
     }
     if (L.view[OP_C].copied) {
-        s = launch_copy<T>(p, OP_C, L.view[OP_C], base[OP_C], Cptr, true, st);
+        s = launch_copy(p, OP_C, L.view[OP_C], base[OP_C], Cptr, true, st);
         if (s != TC_SUCCESS) return s;
     }
     return TC_SUCCESS;
@@ -892,9 +918,10 @@ tc_status ensure_device_resources(Plan &p, size_t workspace_bytes) {
 
 tc_status exec_nest(Plan &p, const Algorithm &alg, const void *alpha, const void *A,
                     const void *B, const void *beta, void *C, void *stream, const Probe *probe) {
-    if (p.dtype != TC_F64 && p.dtype != TC_F32)
+    if (p.dtype != TC_F64 && p.dtype != TC_F32 && alg.kernel != TC_KERNEL_GEMM)
         return fail(TC_ERROR_UNSUPPORTED_DTYPE,
-                    "the loop-nest algorithms run in FP64 or FP32; use GETT (id 0) for tensor-core dtypes");
+                    "at tensor-core dtypes only the gemm loop nests (on the tensor cores) and the GETT run; "
+                    "dot / axpy / gemv / ger nests run in FP64 or FP32");
     tc_status s = ensure_device_resources(p, nest_workspace_bytes(p, alg));
     if (s != TC_SUCCESS) return s;
     p.last_stream = stream;

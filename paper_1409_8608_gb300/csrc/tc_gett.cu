@@ -2134,6 +2134,83 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     }
 }
 
+// ------------------------------------------------------------ gemm nests
+// One phase of a gemm loop nest at a tensor dtype: the GETT kernel on its
+// global-load path, M and N one mode each, the nest's concurrent loops as
+// batch modes, its in-task contracted loops and kernel index as K (nest
+// order).  Split-BF16 keeps the GETT's accuracy settings (split
+// accumulators past K = 64, compensation past the chunk).
+tc_status gett_launch_nest(Plan &p, const NestGemm &g, double frac, void *stream) {
+    GettDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.nm = d.nn = 1;
+    d.m_ext[0] = g.m.ext;
+    d.m_sA[0] = g.m.sA;
+    d.m_sC[0] = g.m.sC;
+    d.n_ext[0] = g.n.ext;
+    d.n_sB[0] = g.n.sB;
+    d.n_sC[0] = g.n.sC;
+    d.n_chain = 1;
+    d.M = g.m.ext;
+    d.N = g.n.ext;
+    d.nk = g.nk;
+    d.K = 1;
+    for (int m = 0; m < g.nk; ++m) {
+        d.k_ext[m] = g.k[m].ext;
+        d.k_sA[m] = g.k[m].sA;
+        d.k_sB[m] = g.k[m].sB;
+        d.K *= g.k[m].ext;
+    }
+    d.nb = g.nt;
+    for (int m = 0; m < g.nt; ++m) {
+        d.b_ext[m] = g.t[m].ext;
+        d.b_sA[m] = g.t[m].sA;
+        d.b_sB[m] = g.t[m].sB;
+        d.b_sC[m] = g.t[m].sC;
+    }
+    const int in_bytes = (p.dtype == TC_BF16 || p.dtype == TC_F16) ? 2 : 4;
+    const int vec = 16 / in_bytes, chunk = p.dtype == TC_TF32 ? 4 : 8;
+    int bn = d.N >= 256 ? 256 : 128;
+    int64_t comp_k = 0;
+    if (p.dtype == TC_BF16X3) comp_k = p.comp_chunk < 0 ? kCompChunkK : p.comp_chunk;
+    const bool comp = comp_k > 0 && d.K > comp_k;
+    if (comp) {
+        bn = 128;
+        d.chunk_stages = (int)(comp_k / kBK);
+    }
+    auto pick = [&](const void *base, int rows, int nrow, const int64_t *rext, const int64_t *rs,
+                    const int64_t *ks) {
+        if (vec_ok(base, vec, nrow, rs, d.nk, d.k_ext, ks)) return 2;
+        int64_t s0 = sectors_for(0, rows, chunk, in_bytes, nrow, rext, rs, d.nk, d.k_ext, ks);
+        int64_t s1 = sectors_for(1, rows, chunk, in_bytes, nrow, rext, rs, d.nk, d.k_ext, ks);
+        return s1 < s0 ? 1 : 0;
+    };
+    d.a_map = pick(g.A, kBM, d.nm, d.m_ext, d.m_sA, d.k_sA);
+    d.b_map = pick(g.B, bn, d.nn, d.n_ext, d.n_sB, d.k_sB);
+    d.A = g.A;
+    d.B = g.B;
+    d.C = (float *)g.C;
+    d.alpha = g.alpha;
+    d.beta = g.beta;
+    d.init = g.init;
+    d.nprod = p.split_products;
+    d.status = p.dev_status;
+    d.tiles_m = (d.M + kBM - 1) / kBM;
+    d.tile_frac = frac;
+    const bool want_split = p.gett_split > 0 || (p.gett_split < 0 && d.K >= 65);
+    d.split = (p.dtype == TC_BF16X3 && !comp && want_split) ? 1 : 0;
+    CUtensorMap none;
+    std::memset(&none, 0, sizeof(none));
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (p.dtype) {
+    case TC_BF16X3: return launch_kind<GK_BF16X3>(d, bn, false, comp, false, none, none, st);
+    case TC_BF16: return launch_kind<GK_BF16>(d, bn, false, false, false, none, none, st);
+    case TC_F16: return launch_kind<GK_F16>(d, bn, false, false, false, none, none, st);
+    case TC_TF32: return launch_kind<GK_TF32>(d, bn, false, false, false, none, none, st);
+    default: return fail(TC_ERROR_UNSUPPORTED_DTYPE, "dtype has no tensor-core gemm");
+    }
+}
+
 // ------------------------------------------------------------ batched form
 size_t gett_desc_bytes() { return sizeof(GettDesc); }
 

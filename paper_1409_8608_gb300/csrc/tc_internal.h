@@ -118,6 +118,28 @@ size_t gett_workspace_bytes(const Plan &p);
 void gett_release(Plan &p);
 tc_status ensure_device_resources(Plan &p, size_t workspace_bytes);
 
+// One phase of a gemm loop nest on the tensor cores (tensor dtypes): the
+// kernel's free index of A (m: sA, sC) and of B (n: sB, sC), its K modes
+// (the in-task contracted loops outermost first, the kernel's contracted
+// index last: sA, sB), and the concurrent free loops as tasks (t: sA, sB,
+// sC, first fastest).  init 2: C = alpha*acc; 1: C = alpha*acc + beta*C.
+struct NestGemmMode {
+    int64_t ext, sA, sB, sC;
+};
+struct NestGemm {
+    NestGemmMode m, n;
+    int nk;
+    NestGemmMode k[kMaxModes];
+    int nt;
+    NestGemmMode t[kMaxModes];
+    const void *A;
+    const void *B;
+    void *C;
+    float alpha, beta;
+    int init;
+};
+tc_status gett_launch_nest(Plan &p, const NestGemm &g, double frac, void *stream);
+
 // Batched SIMT GETT (FP64 / FP32; the serving form's batches): one
 // descriptor per problem (simt_desc_bytes each) holding its modes, strides
 // and operands with alpha = 1, beta = 0; simt_fill_desc returns the

@@ -154,13 +154,63 @@ def test_gett_alpha_beta(tcmod, dtype):
         assert np.array_equal(got, alpha * S + beta * C0), (alpha, beta)
 
 
-def test_nest_algorithms_refuse_tensor_dtypes(tcmod):
+def test_nest_kernels_other_than_gemm_refuse_tensor_dtypes(tcmod):
+    # at tensor-core dtypes the gemm nests run on the tensor cores; dot,
+    # axpy, gemv and ger nests are FP64 / FP32 only
     plan = tcmod.Plan("abc=ai,ibc", [8, 8, 8, 4], dtype="bf16x3")
-    plan.select(1)
+    algs = plan.algorithms()
     d = torch.zeros(512, device="cuda:0")
-    with pytest.raises(tcmod.TcError) as e:
-        plan.execute(d, d, d)
-    assert tcmod.STATUS_NAMES[e.value.status] == "TC_ERROR_UNSUPPORTED_DTYPE"
+    for a in algs[1:]:
+        if a["kernel"] == "gemm":
+            continue
+        plan.select(a["id"])
+        with pytest.raises(tcmod.TcError) as e:
+            plan.execute(d, d, d)
+        assert tcmod.STATUS_NAMES[e.value.status] == "TC_ERROR_UNSUPPORTED_DTYPE"
+        break
+    plan.close()
+
+
+# gemm loop nests at tensor-core dtypes: each phase is one tensor-core GETT
+# launch (the nest's concurrent loops as batch modes, its in-task
+# contracted loops and kernel index as K, phases accumulated into C).
+# Exact on integer inputs; within the GETT's bounds on uniform inputs plus
+# one FP32 rounding per phase.
+NEST_TC_CASES = [
+    ("abc=iaj,jbic", [130, 40, 9, 16, 8]),   # 8 gemm algorithms, copies and phases
+    ("abc=ai,ibc", [200, 30, 20, 40]),       # 2 gemm algorithms, no copies
+    ("habc=hai,hibc", [3, 150, 20, 13, 24]),  # a batch index among the loops
+]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("spec,ext", NEST_TC_CASES)
+def test_gemm_nests_on_tensor_cores(tcmod, spec, ext, dtype):
+    plan = tcmod.Plan(spec, ext, dtype=dtype)
+    gemms = [a for a in plan.algorithms() if a["kernel"] == "gemm"]
+    assert gemms
+    n = synth.dense_sizes(spec, ext)[0]
+    K = ksize(spec, ext)
+    for integer in (True, False):
+        gen = synth.integer_operands if integer else synth.uniform_operands
+        A, B, _ = gen(spec, ext, seed=4)
+        dA, dB, (Ar, Br) = device_inputs(dtype, A, B)
+        want = oc.contract(spec, ext, Ar, Br)
+        scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
+        for a in gemms:
+            plan.select(a["id"])
+            dC = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda:0")
+            plan.execute(dA, dB, dC)
+            torch.cuda.synchronize()
+            got = dC.double().cpu().numpy()
+            if integer:
+                assert np.array_equal(got, want), (a["name"], dtype)
+            else:
+                phases = a["n_phases"]
+                base = (6 * K + 4) * U32 if dtype == "bf16x3" else (K + 1) * U32
+                err = float(np.max(np.abs(got - want) / scale))
+                assert err <= base + phases * U32, (a["name"], dtype, err)
+    plan.device_status()
     plan.close()
 
 
