@@ -57,9 +57,9 @@ def set_free_extent(n):
 
 SMS = 152
 SM_MAX_MHZ = 2070.0
-TORCH_IN = {"f64": "float64", "f32": "float32", "tf32": "float32", "bf16x3": "float32",
+TORCH_IN = {"f64": "float64", "f32": "float32", "tf32": "float32", "bf16x3": "float32", "tf32x3": "float32",
             "bf16": "bfloat16", "f16": "float16"}
-TENSOR_FORMS = ("tf32", "bf16", "f16", "bf16x3")
+TENSOR_FORMS = ("tf32", "bf16", "f16", "bf16x3", "tf32x3")
 
 
 def flops_of(extents):
@@ -438,9 +438,9 @@ def measure_form(args, dtype, spec, extents, A, B, dev, stream, dist, world, tc,
     algorithmic_bytes = int(hA.numel() * hA.element_size() + hB.numel() * hB.element_size() + nC * dC.element_size())
     nkey = extents[0]
     if dtype in TENSOR_FORMS:
-        prods = products if dtype == "bf16x3" else 1
+        prods = products if dtype == "bf16x3" else (3 if dtype == "tf32x3" else 1)
         work = flops * prods
-        peak_tf = peaks["bf16_tflops"] * (0.5 if dtype == "tf32" else 1.0)
+        peak_tf = peaks["bf16_tflops"] * (0.5 if dtype in ("tf32", "tf32x3") else 1.0)
         achieved_tf = work / launch_s / 1e12
         tkey = f"gett_tc_kernel/{dtype}/{spec}/{nkey}" + (f"/p{prods}" if dtype == "bf16x3" else "")
         roofline = {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
@@ -450,7 +450,7 @@ def measure_form(args, dtype, spec, extents, A, B, dev, stream, dist, world, tc,
                     "kernel": "gett_tc_kernel" + (" + pack_kernel (timed together)" if launches_per_step == 2 else ""),
                     "work": f"{prods} slice products x 2*prod(extents) = {work / 1e9:.1f} GFLOP per step",
                     "peak_source": "MEASURED_PEAKS bf16_tflops (burst)" +
-                    (" x 0.5 (TF32 nominal ratio)" if dtype == "tf32" else "") +
+                    (" x 0.5 (TF32 nominal ratio)" if dtype in ("tf32", "tf32x3") else "") +
                     (" (fallback)" if peaks.get("fallback") else " (measured)")}
     else:
         achieved_tf = flops / launch_s / 1e12
@@ -501,6 +501,7 @@ PRECISION_WORKLOADS = (
 PRECISION_FORMS = (
     ("bf16x3 x6 (chosen)", "bf16x3", 6, None), ("bf16x3 x3", "bf16x3", 3, None),
     ("bf16x3 x9", "bf16x3", 9, None), ("bf16x3 x6 uncompensated", "bf16x3", 6, 0),
+    ("tf32x3", "tf32x3", None, None),
     ("tf32", "tf32", None, None), ("bf16", "bf16", None, None), ("f16", "f16", None, None),
     ("f32 (SIMT)", "f32", None, None), ("f64 (plain)", "f64", None, None),
 )
@@ -551,8 +552,9 @@ def run_precision(tc, dev, stream, points=3000, reps=5):
                     row["hbm_frac"] = (nA + nB) * dA.element_size() / t / 1e9 / peaks["hbm_gbs"] + \
                         nC * esz / t / 1e9 / peaks["hbm_gbs"]
                     if dtype in TENSOR_FORMS:
-                        work = flops * (prods or 1)
-                        pk = peaks["bf16_tflops"] * (0.5 if dtype == "tf32" else 1.0)
+                        # tensor work: slice products x F (3 TF32 products for 3xTF32)
+                        work = flops * (prods or (3 if dtype == "tf32x3" else 1))
+                        pk = peaks["bf16_tflops"] * (0.5 if dtype in ("tf32", "tf32x3") else 1.0)
                         row["tensor_frac"] = work / t / 1e12 / pk
                 else:
                     run1()
@@ -666,7 +668,7 @@ def run_gpu(args):
         forms = {}
         samples = {}
         if not args.quick:
-            for dt in ("f32", "bf16x3"):
+            for dt in ("f32", "bf16x3", "tf32x3"):
                 forms[dt], samples[dt] = measure_form(
                     args, dt, SPEC, EXTENTS, A, B, dev, stream, dist, world, tc, min(args.steps, 10),
                     e2e=(dt == "bf16x3"), sample_lin=lin, clocks=(dt == "bf16x3"))
@@ -707,6 +709,8 @@ def run_gpu(args):
             forms["bf16x3"]["form"] = "chosen: split-BF16 x6 slice products on tcgen05, FP32 I/O"
             forms["bf16x3"]["speedup_vs_f64"] = forms["bf16x3"]["value"] / head["value"]
             forms["f32"]["form"] = "FP32 SIMT (FFMA tiles)"
+            forms["tf32x3"]["form"] = "3xTF32: hi.hi + hi.lo + lo.hi on tcgen05 kind::tf32, FP32 I/O"
+            forms["tf32x3"]["speedup_vs_f64"] = forms["tf32x3"]["value"] / head["value"]
             line["forms"] = forms
         if extras:
             if not args.no_cpu:

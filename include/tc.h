@@ -31,6 +31,10 @@
  *              TC_TF32     A, B, C float (tensor cores, TF32 products)
  *              TC_BF16X3   A, B, C float (each input split in three BF16
  *                          slices on the tensor cores; see tc_plan_set_split)
+ *              TC_TF32X3   A, B, C float (each input split in two TF32
+ *                          words, hi = tf32(x), lo = tf32(x - hi); the
+ *                          products hi.hi, hi.lo and lo.hi on the tensor
+ *                          cores)
  *              TC_BF16     A, B __nv_bfloat16; C float
  *              TC_F16      A, B __half; C float
  *   alpha,   host pointers to one double (TC_F64) or one float (all other
@@ -76,7 +80,8 @@ typedef enum {
     TC_TF32 = 2,
     TC_BF16 = 3,
     TC_F16 = 4,
-    TC_BF16X3 = 5
+    TC_BF16X3 = 5,
+    TC_TF32X3 = 6
 } tc_dtype;
 
 /* Kernels of Section 2 (BLAS-1: dot, axpy; BLAS-2: gemv, ger; BLAS-3:
@@ -252,8 +257,8 @@ tc_status tc_plan_set_gett_pack(tc_plan plan, int32_t mode);
  * same bits either way.  Other values give TC_ERROR_INVALID_ARGUMENT. */
 tc_status tc_plan_set_gett_pair(tc_plan plan, int32_t enable);
 
-/* TC_BF16X3, tensor-core GETT without compensation: split accumulators.
- * With 1 the weight-1 slice product (0,0) accumulates in one tensor-memory
+/* TC_BF16X3 and TC_TF32X3, tensor-core GETT without compensation: split
+ * accumulators.  With 1 the weight-1 slice product (0,0) accumulates in one tensor-memory
  * accumulator and the smaller products in a second one, added once in the
  * epilogue: only K/16 FP32 roundings then act on the magnitude of the whole
  * sum instead of 6K/16, at the cost of not double-buffering the
@@ -271,7 +276,7 @@ tc_status tc_plan_set_split_accumulators(tc_plan plan, int32_t enable);
  * for a limit out of range, TC_ERROR_CUDA on a launch or copy failure. */
 tc_status tc_selftest_bounded_wait(int64_t limit_ns, int32_t signal, void *stream);
 
-/* TC_BF16X3 plans, tensor-core GETT: compensated accumulation.  With a
+/* TC_BF16X3 and TC_TF32X3 plans, tensor-core GETT: compensated accumulation.  With a
  * chunk of c K elements (a positive multiple of 32) and K > c, each output
  * is summed on the tensor cores in FP32 over chunks of c contracted
  * positions, and the chunk sums are added into a float-float (hi, lo) pair

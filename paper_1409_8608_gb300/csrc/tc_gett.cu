@@ -55,7 +55,12 @@ namespace tc {
 
 namespace {
 
-enum GettKind { GK_BF16X3 = 0, GK_BF16 = 1, GK_F16 = 2, GK_TF32 = 3 };
+enum GettKind { GK_BF16X3 = 0, GK_BF16 = 1, GK_F16 = 2, GK_TF32 = 3, GK_TF32X3 = 4 };
+
+// MMA on TF32 words (kind::tf32, 4-byte operand elements)
+__host__ __device__ constexpr bool tf32_kind(int k) { return k == GK_TF32 || k == GK_TF32X3; }
+// FP32 inputs, converted (or split) by the converter warps
+__host__ __device__ constexpr bool float_input(int k) { return k == GK_BF16X3 || k == GK_TF32 || k == GK_TF32X3; }
 
 constexpr int kBM = 128;                  // accumulator rows = TMEM lanes
 constexpr int kBK = 32;                   // K elements per stage, global-load path
@@ -342,7 +347,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 template <int KIND, bool PAIR = false>
 __device__ __forceinline__ void mma_issue(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
-    if constexpr (PAIR && KIND == GK_TF32) {
+    if constexpr (PAIR && tf32_kind(KIND)) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.u32 p, %4, 0;\n\t"
@@ -356,7 +361,7 @@ __device__ __forceinline__ void mma_issue(uint32_t dtmem, uint64_t adesc, uint64
             "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
             : "memory");
-    } else if constexpr (KIND == GK_TF32) {
+    } else if constexpr (tf32_kind(KIND)) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.u32 p, %4, 0;\n\t"
@@ -465,12 +470,12 @@ __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
 // ------------------------------------------------------------------ layout
 template <int KIND, int BK>
 struct KindTraits {
-    static constexpr int kElemBytes = KIND == GK_TF32 ? 4 : 2;  // smem operand element
-    static constexpr int kSlices = KIND == GK_BF16X3 ? 3 : 1;
+    static constexpr int kElemBytes = tf32_kind(KIND) ? 4 : 2;  // smem operand element
+    static constexpr int kSlices = KIND == GK_BF16X3 ? 3 : (KIND == GK_TF32X3 ? 2 : 1);
     static constexpr int kChunk = 16 / kElemBytes;              // K elements per 16-byte row
     static constexpr int kKc = BK / kChunk;                     // core matrices along K per stage
     static constexpr int kKsteps = BK * kElemBytes / 32;        // MMA instructions along K per stage
-    static constexpr uint32_t kFmt = KIND == GK_TF32 ? 2u : (KIND == GK_F16 ? 0u : 1u);
+    static constexpr uint32_t kFmt = tf32_kind(KIND) ? 2u : (KIND == GK_F16 ? 0u : 1u);
     using In = typename std::conditional<KIND == GK_BF16, __nv_bfloat16,
                                          typename std::conditional<KIND == GK_F16, __half, float>::type>::type;
     static constexpr int kInBytes = sizeof(In);
@@ -568,6 +573,15 @@ __device__ __forceinline__ void store_converted(const float (&x)[N], char *dst, 
             *(uint2 *)(dst + slice_stride) = make_uint2(w1[0], w1[1]);
             *(uint2 *)(dst + 2 * slice_stride) = make_uint2(w2[0], w2[1]);
         }
+    } else if constexpr (KIND == GK_TF32X3) {  // N == 4: x = hi + lo (+ at most 2^-22 |x|)
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            h[e] = f32_to_tf32(x[e]);
+            l[e] = f32_to_tf32(x[e] - __uint_as_float(h[e]));  // the difference is exact
+        }
+        *(uint4 *)(dst) = make_uint4(h[0], h[1], h[2], h[3]);
+        *(uint4 *)(dst + slice_stride) = make_uint4(l[0], l[1], l[2], l[3]);
     } else {  // TF32: N == 4
         *(uint4 *)(dst) = make_uint4(f32_to_tf32(x[0]), f32_to_tf32(x[1]), f32_to_tf32(x[2]),
                                      f32_to_tf32(x[3]));
@@ -585,7 +599,7 @@ __device__ __forceinline__ void produce_operand(const typename KindTraits<KIND, 
                                                 int slice_stride, int pt) {
     using T = KindTraits<KIND, BK>;
     constexpr int KC = T::kKc, CH = T::kChunk;
-    constexpr bool kFloatIn = KIND == GK_BF16X3 || KIND == GK_TF32;
+    constexpr bool kFloatIn = float_input(KIND);
     if constexpr (MAP == 2) {
         constexpr int UPR = BK / T::kVec;  // 16-byte loads per row per stage
         constexpr int NU = ROWS * UPR / NT;
@@ -669,7 +683,7 @@ __device__ __forceinline__ void convert_staged(const char *stg, int srow, const 
     constexpr int KC = T::kKc, CH = T::kChunk;
     constexpr int NC = ROWS * KC / NT;  // NT threads share the box
     static_assert(NC * NT == ROWS * KC, "even split");
-    constexpr bool kFloatIn = KIND == GK_BF16X3 || KIND == GK_TF32;
+    constexpr bool kFloatIn = float_input(KIND);
     const In *s = (const In *)stg;
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
@@ -1271,7 +1285,8 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             // slice pairs in product order (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
             // (1,2) (2,1) (2,2), one nibble per product
             constexpr uint64_t kPa = 0x221210100ull, kPb = 0x212012010ull;
-            const int nprod = KIND == GK_BF16X3 ? d.nprod : 1;
+            // slice products: split-BF16 3 / 6 / 9; 3xTF32 hi.hi, hi.lo, lo.hi
+            const int nprod = KIND == GK_BF16X3 ? d.nprod : (KIND == GK_TF32X3 ? 3 : 1);
             const uint32_t base = smem_u32(ops);
             int64_t g = 0;
             int64_t u = 0;  // accumulation units (tiles, or K chunks of tiles)
@@ -1644,6 +1659,18 @@ tc_status launch_kind(GettDesc &d, int bn, bool tma, bool comp, bool pair, const
             return launch_gett<KIND, 128, 4, kBK, 0, true>(d, ta, tb, st);
         }
     }
+    if constexpr (KIND == GK_TF32X3) {  // two 4-byte slices per operand: 192 KB of rings
+        if (comp) {
+            if (tma) return launch_gett<KIND, 128, 3, kBKT, 3, true>(d, ta, tb, st);
+            return launch_gett<KIND, 128, 3, kBK, 0, true>(d, ta, tb, st);
+        }
+        if (tma) {
+            if (bn == 128) return launch_gett<KIND, 128, 3, kBKT, 3>(d, ta, tb, st);
+            return launch_gett<KIND, 256, 2, kBKT, 2>(d, ta, tb, st);
+        }
+        if (bn == 256) return launch_gett<KIND, 256, 2, kBK, 0>(d, ta, tb, st);
+        return launch_gett<KIND, 128, 3, kBK, 0>(d, ta, tb, st);
+    } else {
     if (tma) {  // 16-K stages, staged input boxes
         if (bn == 128) {
             if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 128, 3, kBKT, 3>(d, ta, tb, st);
@@ -1664,6 +1691,7 @@ tc_status launch_kind(GettDesc &d, int bn, bool tma, bool comp, bool pair, const
     if constexpr (KIND == GK_BF16X3) return launch_gett<KIND, 128, 4, kBK, 0>(d, ta, tb, st);
     else if constexpr (KIND == GK_TF32) return launch_gett<KIND, 128, 6, kBK, 0>(d, ta, tb, st);
     else return launch_gett<KIND, 128, 8, kBK, 0>(d, ta, tb, st);
+    }  // not TF32X3
 }
 
 // Distinct 32-byte sectors one warp touches on its first load under a
@@ -1845,11 +1873,17 @@ bool plan_tma_operand(const Plan &p, int opnd, const void *base, int in_bytes, i
 
 }  // namespace
 
+// bytes of a pre-converted input element: TF32 word, three BF16 slices, or
+// two TF32 words
+int image_bytes(tc_dtype dt) { return dt == TC_TF32 ? 4 : (dt == TC_TF32X3 ? 8 : 6); }
+
 // Pre-conversion choice for the tensor-core GETT (0 none, 1 A, 2 B: the
 // input with fewer elements) and a bound on its stage images' bytes.
 int pack_choice(const Plan &p, int64_t &bound) {
     bound = 0;
-    if ((p.dtype != TC_BF16X3 && p.dtype != TC_TF32) || p.gett_pack == 0 || !p.batch.empty()) return 0;
+    if ((p.dtype != TC_BF16X3 && p.dtype != TC_TF32 && p.dtype != TC_TF32X3) || p.gett_pack == 0 ||
+        !p.batch.empty())
+        return 0;
     int64_t M = 1, N = 1, K = 1;
     for (int id : p.freeA) M *= p.ext[id];
     for (int id : p.freeB) N *= p.ext[id];
@@ -1867,7 +1901,7 @@ int pack_choice(const Plan &p, int64_t &bound) {
     const int us = unit_index(a_small ? OP_A : OP_B), ub = unit_index(a_small ? OP_B : OP_A);
     const bool permuted = us >= 0 && p.cls[us] == CLS_CONTRACTED && us != ub;
     // rows rounded up to a 256-row tile, K to a 32-position stage
-    const int64_t b = (R + 255) * (K + kBK - 1) * (p.dtype == TC_TF32 ? 4 : 6);
+    const int64_t b = (R + 255) * (K + kBK - 1) * image_bytes(p.dtype);
     if (b > kPackMaxBytes) return 0;
     if (p.gett_pack == 1 && (!permuted || (a_small ? M : N) * kPackRatio > (a_small ? N : M))) return 0;
     bound = b;
@@ -2003,11 +2037,11 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     if (s != TC_SUCCESS) return s;
     const int in_bytes = (p.dtype == TC_BF16 || p.dtype == TC_F16) ? 2 : 4;
     const int vec = 16 / in_bytes;
-    const int chunk = p.dtype == TC_TF32 ? 4 : 8;
+    const int chunk = (p.dtype == TC_TF32 || p.dtype == TC_TF32X3) ? 4 : 8;
     int bn = p.gett_bn == 128 || p.gett_bn == 256 ? p.gett_bn : (d.N >= 256 ? 256 : 128);
     // compensated accumulation (split-BF16 only): K chunks of comp_k elements
     int64_t comp_k = 0;
-    if (p.dtype == TC_BF16X3) comp_k = p.comp_chunk < 0 ? kCompChunkK : p.comp_chunk;
+    if (p.dtype == TC_BF16X3 || p.dtype == TC_TF32X3) comp_k = p.comp_chunk < 0 ? kCompChunkK : p.comp_chunk;
     const bool comp = comp_k > 0 && d.K > comp_k;
     if (comp) bn = 128;
     // TMA staging for each operand TMA can describe (tiles of 128 x bn, or
@@ -2098,7 +2132,7 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     // accumulator reach the 1e-6 level
     constexpr int64_t kSplitMinK = 65;
     const bool want_split = p.gett_split > 0 || (p.gett_split < 0 && d.K >= kSplitMinK);
-    d.split = (p.dtype == TC_BF16X3 && !comp && want_split) ? 1 : 0;
+    d.split = ((p.dtype == TC_BF16X3 || p.dtype == TC_TF32X3) && !comp && want_split) ? 1 : 0;
     cudaStream_t st = (cudaStream_t)stream;
     if (pk) {
         // the smaller input's stage images, for the stage depth the launch
@@ -2107,7 +2141,7 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
         const int rows = pk == 1 ? kBM : (pair ? bn / 2 : bn);
         const int64_t R = pk == 1 ? d.M : d.N;
         const int64_t nktp = (d.K + bkp - 1) / bkp;
-        const int64_t stage_bytes = (int64_t)rows * bkp * (p.dtype == TC_TF32 ? 4 : 6);
+        const int64_t stage_bytes = (int64_t)rows * bkp * image_bytes(p.dtype);
         const int64_t rtiles = pair ? 2 * ((R + 2 * rows - 1) / (2 * rows)) : (R + rows - 1) / rows;
         const int64_t bytes = rtiles * nktp * stage_bytes;
         // bytes <= pk_bound: rows round up by less than 256, K by less than 32
@@ -2116,10 +2150,12 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
         d.pk = pk;
         d.pk_base = (const char *)p.workspace;
         d.pk_tile_bytes = nktp * stage_bytes;
-        const int64_t chunks = bytes / 16 / (p.dtype == TC_TF32 ? 1 : 3);  // one per 16-byte row of slice 0
+        const int64_t chunks = bytes / 16 / (p.dtype == TC_TF32 ? 1 : (p.dtype == TC_TF32X3 ? 2 : 3));  // one per 16-byte row of slice 0
         const unsigned grid = (unsigned)std::min<int64_t>((chunks + 127) / 128, 152 * 16);
         if (p.dtype == TC_TF32)
             pack_kernel<GK_TF32><<<grid, 128, 0, st>>>(d, pk - 1, rows, bkp, rtiles, (char *)p.workspace);
+        else if (p.dtype == TC_TF32X3)
+            pack_kernel<GK_TF32X3><<<grid, 128, 0, st>>>(d, pk - 1, rows, bkp, rtiles, (char *)p.workspace);
         else
             pack_kernel<GK_BF16X3><<<grid, 128, 0, st>>>(d, pk - 1, rows, bkp, rtiles, (char *)p.workspace);
         cudaError_t e = cudaGetLastError();
@@ -2130,6 +2166,7 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     case TC_BF16: return launch_kind<GK_BF16>(d, bn, tma, comp, false, tmA, tmB, st);
     case TC_F16: return launch_kind<GK_F16>(d, bn, tma, comp, false, tmA, tmB, st);
     case TC_TF32: return launch_kind<GK_TF32>(d, bn, tma, comp, pair, tmA, tmB, st);
+    case TC_TF32X3: return launch_kind<GK_TF32X3>(d, bn, tma, comp, false, tmA, tmB, st);
     default: return fail(TC_ERROR_UNSUPPORTED_DTYPE, "dtype has no tensor-core GETT");
     }
 }
@@ -2169,10 +2206,10 @@ tc_status gett_launch_nest(Plan &p, const NestGemm &g, double frac, void *stream
         d.b_sC[m] = g.t[m].sC;
     }
     const int in_bytes = (p.dtype == TC_BF16 || p.dtype == TC_F16) ? 2 : 4;
-    const int vec = 16 / in_bytes, chunk = p.dtype == TC_TF32 ? 4 : 8;
+    const int vec = 16 / in_bytes, chunk = (p.dtype == TC_TF32 || p.dtype == TC_TF32X3) ? 4 : 8;
     int bn = d.N >= 256 ? 256 : 128;
     int64_t comp_k = 0;
-    if (p.dtype == TC_BF16X3) comp_k = p.comp_chunk < 0 ? kCompChunkK : p.comp_chunk;
+    if (p.dtype == TC_BF16X3 || p.dtype == TC_TF32X3) comp_k = p.comp_chunk < 0 ? kCompChunkK : p.comp_chunk;
     const bool comp = comp_k > 0 && d.K > comp_k;
     if (comp) {
         bn = 128;
@@ -2198,7 +2235,7 @@ tc_status gett_launch_nest(Plan &p, const NestGemm &g, double frac, void *stream
     d.tiles_m = (d.M + kBM - 1) / kBM;
     d.tile_frac = frac;
     const bool want_split = p.gett_split > 0 || (p.gett_split < 0 && d.K >= 65);
-    d.split = (p.dtype == TC_BF16X3 && !comp && want_split) ? 1 : 0;
+    d.split = ((p.dtype == TC_BF16X3 || p.dtype == TC_TF32X3) && !comp && want_split) ? 1 : 0;
     CUtensorMap none;
     std::memset(&none, 0, sizeof(none));
     cudaStream_t st = (cudaStream_t)stream;
@@ -2207,6 +2244,7 @@ tc_status gett_launch_nest(Plan &p, const NestGemm &g, double frac, void *stream
     case TC_BF16: return launch_kind<GK_BF16>(d, bn, false, false, false, none, none, st);
     case TC_F16: return launch_kind<GK_F16>(d, bn, false, false, false, none, none, st);
     case TC_TF32: return launch_kind<GK_TF32>(d, bn, false, false, false, none, none, st);
+    case TC_TF32X3: return launch_kind<GK_TF32X3>(d, bn, false, comp, false, none, none, st);
     default: return fail(TC_ERROR_UNSUPPORTED_DTYPE, "dtype has no tensor-core gemm");
     }
 }
@@ -2253,7 +2291,7 @@ int64_t gett_fill_plan_desc(const Plan &p, int bn, const void *A, const void *B,
     std::memset(&d, 0, sizeof(d));
     if (describe_modes(p, 0, d) != TC_SUCCESS) return -1;
     const int in_bytes = (p.dtype == TC_BF16 || p.dtype == TC_F16) ? 2 : 4;
-    const int vec = 16 / in_bytes, chunk = p.dtype == TC_TF32 ? 4 : 8;
+    const int vec = 16 / in_bytes, chunk = (p.dtype == TC_TF32 || p.dtype == TC_TF32X3) ? 4 : 8;
     auto pick = [&](const void *base, int rows, int nrow, const int64_t *rext, const int64_t *rs,
                     const int64_t *ks) {
         if (vec_ok(base, vec, nrow, rs, d.nk, d.k_ext, ks)) return 2;

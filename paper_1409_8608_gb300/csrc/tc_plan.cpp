@@ -146,7 +146,7 @@ tc_status build_plan(Plan &p, const char *spec, const int64_t *extents, const in
                      bool enumerate) {
     if (!spec) return fail(TC_ERROR_INVALID_ARGUMENT, "spec is NULL");
     if (!extents) return fail(TC_ERROR_INVALID_ARGUMENT, "extents is NULL");
-    if (dtype < TC_F64 || dtype > TC_BF16X3)
+    if (dtype < TC_F64 || dtype > TC_TF32X3)
         return fail(TC_ERROR_UNSUPPORTED_DTYPE, "unknown dtype");
     std::string s(spec);
     size_t eq = s.find('='), comma = s.find(',');

@@ -96,7 +96,23 @@ CASES = [
     ("abh=aih,ibh", [130, 300, 3, 40]),       # batched matrix product, batch last
     ("hab=ha,hb", [5, 140, 260]),             # Hadamard outer product, no contracted index
 ]
-DTYPES = ["bf16", "f16", "tf32", "bf16x3"]
+DTYPES = ["bf16", "f16", "tf32", "bf16x3", "tf32x3"]
+
+
+def sum_bound(dtype, K, extra=0):
+    """Componentwise bound (relative to |A||B|) of a length-K contraction in
+    the form's arithmetic, the inputs as the kernel sees them.  Split-BF16:
+    6K slice products into FP32, the dropped products and split remainders
+    at most 3u per term.  3xTF32: the lo words round the remainder x - hi
+    (at most 2^-22 |x|, per input) and lo.lo is dropped (2^-22): at most
+    3 * 2^-22 per term, plus 3K products into FP32.  Otherwise a length-K
+    FMA chain, gamma(K + 1).  `extra` counts further roundings (beta, phases)."""
+    if dtype == "bf16x3":
+        return (6 * K + 4 + extra) * U32
+    if dtype == "tf32x3":
+        return 3 * 2.0 ** -22 + (3 * K + 4 + extra) * U32
+    n = K + 1 + extra
+    return n * U32 / (1 - n * U32)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -118,7 +134,7 @@ def test_gett_within_bound_on_uniform(tcmod, spec, ext, dtype):
     want = oc.contract(spec, ext, Ar, Br)
     scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
     K = ksize(spec, ext)
-    bound = (6 * K + 4) * U32 if dtype == "bf16x3" else (K + 1) * U32 / (1 - (K + 1) * U32)
+    bound = sum_bound(dtype, K)
     got = run_gett(tcmod, spec, ext, dtype, dA, dB)
     err = float(np.max(np.abs(got - want) / scale))
     assert err <= bound, (dtype, err, bound)
@@ -207,7 +223,7 @@ def test_gemm_nests_on_tensor_cores(tcmod, spec, ext, dtype):
                 assert np.array_equal(got, want), (a["name"], dtype)
             else:
                 phases = a["n_phases"]
-                base = (6 * K + 4) * U32 if dtype == "bf16x3" else (K + 1) * U32
+                base = sum_bound(dtype, K)
                 err = float(np.max(np.abs(got - want) / scale))
                 assert err <= base + phases * U32, (a["name"], dtype, err)
     plan.device_status()
@@ -226,13 +242,15 @@ CHOSEN_CASES = [
 ]
 
 
+@pytest.mark.parametrize("form", ["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("dist", ["uniform", "lognormal"])
 @pytest.mark.parametrize("spec,ext", CHOSEN_CASES)
-def test_chosen_form_full_size_meets_1e6(tcmod, spec, ext, dist):
+def test_chosen_form_full_size_meets_1e6(tcmod, spec, ext, dist, form):
+    # the split forms (split-BF16, the chosen one, and 3xTF32) at FP32 level
     gen = synth.uniform_operands if dist == "uniform" else synth.lognormal_slice_operands
     A, B, _ = gen(spec, ext, seed=0 if dist == "uniform" else 1)
-    dA, dB, (Ar, Br) = device_inputs("bf16x3", A, B)
-    got = run_gett(tcmod, spec, ext, "bf16x3", dA, dB)
+    dA, dB, (Ar, Br) = device_inputs(form, A, B)
+    got = run_gett(tcmod, spec, ext, form, dA, dB)
     c_modes = oc.parse_spec(spec)[0]
     e = dict(zip(oc.index_order(spec), ext))
     rng = np.random.default_rng(1)
@@ -246,7 +264,7 @@ def test_chosen_form_full_size_meets_1e6(tcmod, spec, ext, dist):
         mul *= e[m]
     err = float(np.max(np.abs(got[lin] - want) / scale))
     assert err <= 1e-6, err
-    assert err <= (6 * ksize(spec, ext) + 4) * U32, err
+    assert err <= sum_bound(form, ksize(spec, ext)), err
     assert np.isfinite(got).all()
 
 
@@ -278,7 +296,7 @@ def test_tma_staging_matches_global_loads_bitwise(tcmod, spec, ext, dtype):
     want = oc.contract(spec, ext, Ar, Br)
     scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
     K = ksize(spec, ext)
-    bound = (6 * K + 4) * U32 if dtype == "bf16x3" else (K + 1) * U32 / (1 - (K + 1) * U32)
+    bound = sum_bound(dtype, K)
     assert float(np.max(np.abs(outs[0] - want) / scale)) <= bound
 
 
@@ -403,7 +421,7 @@ def test_gett_output_layouts(tcmod, spec, ext, strides, dtype):
     scale = 0.5 * oc.contract(spec, ext, np.abs(Ar), np.abs(Br), strides=strides,
                               C=np.zeros(nc)) + 2.0 * np.abs(C0f)
     K = ksize(spec, ext)
-    bound = (6 * K + 8) * U32 if dtype == "bf16x3" else (K + 3) * U32 / (1 - (K + 3) * U32)
+    bound = sum_bound(dtype, K, extra=2)
     err = np.abs(got - want) / np.maximum(scale, 1e-300)
     assert float(np.max(err)) <= bound, (float(np.max(err)), bound)
 
@@ -440,7 +458,7 @@ def test_pack_modes_within_bound_and_paths_bitwise(tcmod, spec, ext, dtype):
     scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
     n = synth.dense_sizes(spec, ext)[0]
     K = ksize(spec, ext)
-    bound = (6 * K + 4) * U32 if dtype == "bf16x3" else (K + 1) * U32 / (1 - (K + 1) * U32)
+    bound = sum_bound(dtype, K)
     outs = {}
     for pack, tma in ((0, 1), (2, 1), (2, 0)):
         plan = tcmod.Plan(spec, ext, dtype=dtype)
