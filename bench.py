@@ -662,6 +662,13 @@ def run_gpu(args):
 
     A, B, _ = synth.uniform_operands(SPEC, EXTENTS, seed=rank)
     pts, lin = sample_points(SPEC, EXTENTS, 4000, seed=11)
+    if args.only:  # one form alone (for profiler captures)
+        with torch.cuda.stream(stream):
+            one, _ = measure_form(args, args.only, SPEC, EXTENTS, A, B, dev, stream, dist, world, tc,
+                                  args.steps, e2e=False, clocks=False)
+        if rank == 0:
+            print(json.dumps(dict(one, metric=METRIC, config={"workload": WORKLOAD, "only": args.only})), flush=True)
+        return 0
     with torch.cuda.stream(stream):
         head, head_samples = measure_form(args, "f64", SPEC, EXTENTS, A, B, dev, stream, dist, world, tc,
                                           args.steps, sample_lin=lin)
@@ -772,6 +779,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="the headline form only (no other forms or workloads)")
+    ap.add_argument("--only", default=None, choices=["f64", "f32", "bf16x3", "tf32x3"],
+                    help="profiling captures: one form of the headline workload alone, its line only")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--impl", default="tc", choices=["tc", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
