@@ -359,18 +359,29 @@ tc_status tc_predict(tc_plan plan, const int32_t *alg_ids, int32_t n, const void
 tc_status tc_plan_select_best(tc_plan plan, int32_t *best);
 
 /* Autotuner for the tensor-core GETT: predicts every tile configuration
- * (tile width 128 or 256, TMA staging on or off) with the same
- * micro-benchmark and keeps the fastest in the plan, reporting it in
- * *width and *tma (either may be NULL).  Results are cached per (spec,
+ * -- tile width 128 or 256, TMA staging on or off, one or two CTAs per
+ * tile (tc_plan_set_gett_pair), the smaller input pre-converted or not
+ * (tc_plan_set_gett_pack 0 or 2); every one gives the same bits -- with
+ * the same micro-benchmark, and keeps the fastest in the plan, reporting
+ * the width in *width and TMA in *tma (either may be NULL;
+ * tc_plan_get_gett_config reads all four).  Results are cached per (spec,
  * extents, strides, dtype, split products, device); a cached plan key is
  * answered without running anything.  FP64/FP32 plans have nothing to tune
  * (width 0, tma 1).  Clears the plan's stored predictions. */
 tc_status tc_autotune(tc_plan plan, const void *A, const void *B, void *C, void *stream,
                       int32_t *width, int32_t *tma);
 
-/* Writes / merges the process-wide tuning cache as JSON lines
- * ({"key": ..., "gett_tile": ..., "gett_tma": ...}), so that re-planning
- * in a later process is free. */
+/* The plan's tensor-core GETT settings: tile width (0: by N), TMA staging,
+ * CTA pairs, pre-conversion mode; any pointer may be NULL. */
+tc_status tc_plan_get_gett_config(tc_plan plan, int32_t *width, int32_t *tma, int32_t *pair,
+                                  int32_t *pack);
+
+/* Writes / merges the process-wide tuning cache as JSON lines, one per
+ * key with its named integer choices ({"key": ..., "gett_tile": ...,
+ * "gett_tma": ..., "gett_pair": ..., "gett_pack": ...} for plans,
+ * {"key": ..., "batch_k_chunk": ..., "batch_tile_m": ...} for batch shape
+ * classes), so that re-planning in a later process is free.  Loading keeps
+ * every "name": integer pair; the tuners check the values they read. */
 tc_status tc_tuning_cache_save(const char *path);
 tc_status tc_tuning_cache_load(const char *path);
 
@@ -392,11 +403,15 @@ tc_status tc_batch_create(tc_batch *out, const char *spec, int32_t count,
                           const int64_t *extents, tc_dtype dtype);
 tc_status tc_batch_destroy(tc_batch batch);
 
-/* Tile policy: 1 (default) picks 64x64, 32x128 or 16x256 tiles per problem
- * to waste the fewest padded rows; 0 uses 64x64 for every problem.  For
- * TC_BF16X3 the tiles are 128 x w with one w for the batch: policy 1 takes
- * the w in {128, 256} with the fewest padded columns plus 64 per tile,
- * policy 0 takes 256. */
+/* Tile policy.  TC_F32 / TC_F64 tiles hold 4096 outputs, (8 << s) rows x
+ * (512 >> s) columns for s = 0..4, and K runs in chunks of 8, 16 or 32:
+ * 0 (fixed) 64 x 64 with chunks of 16; 1 (rule, the default) the smallest
+ * tile height that covers the problem's M, with the largest chunk that
+ * fits; 2 (autotuned) the choice of tc_batch_autotune for the problem's
+ * shape class.  TC_BF16X3 tiles are 128 x w with one w for the batch: 256
+ * (fixed), the w in {128, 256} with the fewest padded columns plus 64 per
+ * tile (rule), or the autotuner's.  Policy 2 before tc_batch_autotune is
+ * TC_ERROR_INVALID_ARGUMENT. */
 tc_status tc_batch_set_tiles(tc_batch batch, int32_t policy);
 
 /* Host arrays of count device pointers, in the caller's problem order. */
@@ -418,6 +433,41 @@ tc_status tc_batch_execute(tc_batch batch, const void *alpha, const void *beta,
 /* Total flops (2 M N K summed), tiles of the current policy and compulsory
  * bytes (A, B, C once each, beta = 0); any pointer may be NULL. */
 tc_status tc_batch_info(tc_batch batch, double *flops, int64_t *tiles, int64_t *bytes);
+
+/* One shape class of the batch autotuner (TC_F32 / TC_F64: problems with
+ * the same ceil(log2 M), ceil(log2 K) and N bucket -- 0: N <= 256, 1:
+ * N <= 2048, 2: larger; TC_BF16X3: the whole batch, classes -1). */
+typedef struct {
+    int32_t m_log2, k_log2, n_class;
+    int32_t problems;     /* problems in the class */
+    int32_t candidates;   /* configurations timed (0: answered from the tuning cache) */
+    int32_t tile_m, tile_n, k_chunk;  /* the fastest configuration */
+    double seconds_best;  /* the class alone at that configuration (median; -1 if cached) */
+    double seconds_rule;  /* ... at policy 1's configuration (-1 if cached) */
+    double seconds_fixed; /* ... at policy 0's configuration (-1 if cached) */
+} tc_batch_tuning;
+
+/* Autotuner of the batched form (needs the operands).  TC_F32 / TC_F64:
+ * for every shape class, times every (tile shape, K chunk) candidate on
+ * the class's problems alone (one warm-up, median of reps launches on
+ * stream), keeps the fastest, then times the whole batch with 2 and 3
+ * pipeline stages; the class choices go to the tuning cache, and a class
+ * found there is not timed.  TC_BF16X3: times the whole batch at tile
+ * widths 128 and 256.  Leaves policy 2 selected.  Every timed launch runs
+ * with alpha = 1, beta = 0, so each C_q holds A_q.B_q afterwards.  Writes
+ * up to capacity class rows to classes and the number of classes to
+ * *n_classes (may be NULL).  Blocks until the timings are done. */
+tc_status tc_batch_autotune(tc_batch batch, void *stream, int32_t reps, tc_batch_tuning *classes,
+                            int32_t capacity, int32_t *n_classes);
+
+/* The current policy, SIMT pipeline stages (TC_BF16X3: 0) and split-BF16
+ * tile width (SIMT: 0); any pointer may be NULL. */
+tc_status tc_batch_config(tc_batch batch, int32_t *policy, int32_t *stages, int32_t *tile_n);
+
+/* Tile rows, columns and K chunk of problem `problem` (caller's order)
+ * under the current policy. */
+tc_status tc_batch_problem_tiles(tc_batch batch, int32_t problem, int32_t *tile_m,
+                                 int32_t *tile_n, int32_t *k_chunk);
 
 /* TC_BF16X3 batches: waits for the stream of the last execute, then reads
  * and clears the batch's device status word: TC_SUCCESS, or

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cstddef>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -159,13 +160,23 @@ struct BatchProblem {
     const void *B;
     void *C;
     int64_t tile0;    // first tile of this problem in the flattened list
-    int32_t shape;    // SIMT tiles 0: 64x64, 1: 32x128, 2: 16x256
+    int32_t shape;    // SIMT tiles (8 << shape) x (512 >> shape), shape 0..4
     int32_t tiles_m;
+    int32_t bk;       // SIMT K chunk per pipeline stage (8, 16 or 32)
+    int32_t flags;    // SIMT copy paths (kBatchVecA | kBatchVecB | kBatchStagedC)
 };
+constexpr int32_t kBatchVecA = 1;     // A copied in 16-byte pieces (m contiguous, aligned)
+constexpr int32_t kBatchVecB = 2;     // B copied in 16-byte pieces (k contiguous, aligned)
+constexpr int32_t kBatchStagedC = 4;  // a tile's C is one contiguous run (staged epilogue)
 
 // Batched split-BF16 on the tensor-core GETT kernel: one device descriptor
 // per problem (gett_desc_bytes each, filled by gett_fill_batch_desc for
 // 128 x bn tiles), then one launch over tiles [t_begin, t_end).
+// Process-wide tuning cache (tc_tuning_cache_save / _load): named integer
+// choices per key.
+bool tuning_get(const std::string &key, std::map<std::string, int> &out);
+void tuning_put(const std::string &key, const std::map<std::string, int> &v);
+
 size_t gett_desc_bytes();
 void gett_fill_batch_desc(const BatchProblem &P, int bn, void *out);
 // one_stage: every problem's K fits one 32-element stage (the converter

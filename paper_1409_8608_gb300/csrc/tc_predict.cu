@@ -267,7 +267,9 @@ tc_status predict_one(Plan &p, int alg_id, const Operands &ops, unsigned *sink, 
 
 // ---------------------------------------------------------------- tuning cache
 std::mutex g_cache_mu;
-std::map<std::string, std::pair<int, int>> g_cache;  // key -> (GETT tile width, TMA)
+// key -> named choices ("gett_tile", "gett_tma", "gett_pair", "gett_pack"
+// for plans; "batch_tile_m", "batch_k_chunk" for batch shape classes)
+std::map<std::string, std::map<std::string, int>> g_cache;
 
 std::string plan_key(const Plan &p) {
     std::ostringstream k;
@@ -285,6 +287,20 @@ std::string plan_key(const Plan &p) {
 }
 
 }  // namespace
+
+bool tuning_get(const std::string &key, std::map<std::string, int> &out) {
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    auto it = g_cache.find(key);
+    if (it == g_cache.end()) return false;
+    out = it->second;
+    return true;
+}
+
+void tuning_put(const std::string &key, const std::map<std::string, int> &v) {
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    g_cache[key] = v;
+}
+
 }  // namespace tc
 
 using namespace tc;
@@ -359,53 +375,73 @@ tc_status tc_autotune(tc_plan plan, const void *A, const void *B, void *C, void 
     if (!plan) return fail(TC_ERROR_INVALID_ARGUMENT, "plan is NULL");
     Plan &p = plan->p;
     const std::string key = plan_key(p);
-    {
-        std::lock_guard<std::mutex> g(g_cache_mu);
-        auto it = g_cache.find(key);
-        if (it != g_cache.end()) {
-            p.gett_bn = it->second.first;
-            p.gett_tma = it->second.second;
-            if (width) *width = p.gett_bn;
-            if (tma) *tma = p.gett_tma;
-            return TC_SUCCESS;
+    auto report = [&]() {
+        if (width) *width = p.gett_bn;
+        if (tma) *tma = p.gett_tma;
+        return TC_SUCCESS;
+    };
+    std::map<std::string, int> c;
+    if (tuning_get(key, c) && c.count("gett_tile") && c.count("gett_tma")) {
+        const int bn = c["gett_tile"], tm = c["gett_tma"];
+        const int pair = c.count("gett_pair") ? c["gett_pair"] : 0, pack = c.count("gett_pack") ? c["gett_pack"] : 1;
+        if ((bn == 0 || bn == 128 || bn == 256) && (tm == 0 || tm == 1) && (pair == 0 || pair == 1) &&
+            pack >= 0 && pack <= 2) {
+            p.gett_bn = bn;
+            p.gett_tma = tm;
+            p.gett_pair = pair;
+            p.gett_pack = pack;
+            return report();
         }
     }
     const bool tensor = p.dtype != TC_F64 && p.dtype != TC_F32;
-    int best_bn = 0, best_tma = 1;
+    int best_bn = 0, best_tma = 1, best_pair = 0, best_pack = 1;
     if (tensor) {
-        // the candidates' cost: the GETT micro-benchmark (a few waves of
-        // real tiles, median of ten), as in tc_predict
+        // candidates: tile width, TMA staging, one or two CTAs per tile and
+        // the pre-conversion of the smaller input -- all give the same bits
+        // -- each costed by the GETT micro-benchmark (a few waves of real
+        // tiles, median of ten), as in tc_predict
         double best_t = -1;
-        const int saved_bn = p.gett_bn, saved_tma = p.gett_tma;
+        const int saved[4] = {p.gett_bn, p.gett_tma, p.gett_pair, p.gett_pack};
         for (int bn : {128, 256}) {
             for (int tm : {0, 1}) {
                 if (tm == 1 && bn != 256) continue;  // the TMA path runs 128 x 256 tiles
-                p.gett_bn = bn;
-                p.gett_tma = tm;
-                int32_t id = 0;
-                double t = -1;
-                tc_status s = tc_predict(plan, &id, 1, A, B, C, &t, stream);
-                if (s != TC_SUCCESS) {
-                    p.gett_bn = saved_bn;
-                    p.gett_tma = saved_tma;
-                    return s;
-                }
-                if (t > 0 && (best_t < 0 || t < best_t)) {
-                    best_t = t;
-                    best_bn = bn;
-                    best_tma = tm;
+                for (int pair : {0, 1}) {
+                    for (int pack : {0, 2}) {
+                        p.gett_bn = bn;
+                        p.gett_tma = tm;
+                        p.gett_pair = pair;
+                        p.gett_pack = pack;
+                        int32_t id = 0;
+                        double t = -1;
+                        tc_status s = tc_predict(plan, &id, 1, A, B, C, &t, stream);
+                        if (s != TC_SUCCESS) {
+                            p.gett_bn = saved[0], p.gett_tma = saved[1], p.gett_pair = saved[2], p.gett_pack = saved[3];
+                            return s;
+                        }
+                        if (t > 0 && (best_t < 0 || t < best_t)) {
+                            best_t = t;
+                            best_bn = bn, best_tma = tm, best_pair = pair, best_pack = pack;
+                        }
+                    }
                 }
             }
         }
     }
     p.gett_bn = best_bn;
     p.gett_tma = best_tma;
-    {
-        std::lock_guard<std::mutex> g(g_cache_mu);
-        g_cache[key] = {best_bn, best_tma};
-    }
-    if (width) *width = best_bn;
-    if (tma) *tma = best_tma;
+    p.gett_pair = best_pair;
+    p.gett_pack = best_pack;
+    tuning_put(key, {{"gett_tile", best_bn}, {"gett_tma", best_tma}, {"gett_pair", best_pair}, {"gett_pack", best_pack}});
+    return report();
+}
+
+tc_status tc_plan_get_gett_config(tc_plan plan, int32_t *width, int32_t *tma, int32_t *pair, int32_t *pack) {
+    if (!plan) return fail(TC_ERROR_INVALID_ARGUMENT, "plan is NULL");
+    const Plan &p = plan->p;
+    if (width) *width = p.gett_bn;
+    if (tma) *tma = p.gett_tma;
+    if (pair) *pair = p.gett_pair;
+    if (pack) *pack = p.gett_pack;
     return TC_SUCCESS;
 }
 
@@ -420,8 +456,9 @@ tc_status tc_tuning_cache_save(const char *path) {
             if (ch == '"' || ch == '\\') k.push_back('\\');
             k.push_back(ch);
         }
-        f << "{\"key\": \"" << k << "\", \"gett_tile\": " << kv.second.first << ", \"gett_tma\": "
-          << kv.second.second << "}\n";
+        f << "{\"key\": \"" << k << "\"";
+        for (auto &fv : kv.second) f << ", \"" << fv.first << "\": " << fv.second;
+        f << "}\n";
     }
     return f ? TC_SUCCESS : fail(TC_ERROR_INVALID_ARGUMENT, "write failed");
 }
@@ -442,13 +479,23 @@ tc_status tc_tuning_cache_load(const char *path) {
             if (line[i] == '\\' && i + 1 < line.size()) ++i;
             key.push_back(line[i]);
         }
-        int bn = 0, tm = 1;
-        size_t a = line.find("\"gett_tile\": ", i), b = line.find("\"gett_tma\": ", i);
-        if (a == std::string::npos || b == std::string::npos) continue;
-        bn = std::atoi(line.c_str() + a + 13);
-        tm = std::atoi(line.c_str() + b + 12);
-        if ((bn != 0 && bn != 128 && bn != 256) || (tm != 0 && tm != 1)) continue;
-        g_cache[key] = {bn, tm};
+        // the remaining "name": integer pairs (names of [a-z_] only); the
+        // users of an entry check its values
+        std::map<std::string, int> v;
+        while (true) {
+            size_t q0 = line.find('"', i + 1);
+            if (q0 == std::string::npos) break;
+            size_t q1 = line.find('"', q0 + 1);
+            if (q1 == std::string::npos) break;
+            std::string name = line.substr(q0 + 1, q1 - q0 - 1);
+            size_t colon = line.find(':', q1);
+            if (colon == std::string::npos) break;
+            bool ok = !name.empty();
+            for (char ch : name) ok = ok && ((ch >= 'a' && ch <= 'z') || ch == '_');
+            if (ok) v[name] = std::atoi(line.c_str() + colon + 1);
+            i = colon;
+        }
+        if (!v.empty()) g_cache[key] = v;
     }
     return TC_SUCCESS;
 }

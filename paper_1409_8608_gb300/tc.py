@@ -57,6 +57,13 @@ class tc_setup_item(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("operand", ctypes.c_int32), ("size", ctypes.c_int64)]
 
 
+class tc_batch_tuning(ctypes.Structure):
+    _fields_ = [("m_log2", ctypes.c_int32), ("k_log2", ctypes.c_int32), ("n_class", ctypes.c_int32),
+                ("problems", ctypes.c_int32), ("candidates", ctypes.c_int32), ("tile_m", ctypes.c_int32),
+                ("tile_n", ctypes.c_int32), ("k_chunk", ctypes.c_int32), ("seconds_best", ctypes.c_double),
+                ("seconds_rule", ctypes.c_double), ("seconds_fixed", ctypes.c_double)]
+
+
 class tc_server_report(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("admission_stalls", ctypes.c_int64), ("peak_inflight", ctypes.c_int64),
@@ -101,6 +108,7 @@ SIGNATURES = {
                                   ctypes.POINTER(ctypes.c_double), _VP]),
     "tc_plan_select_best": (ctypes.c_int, [_VP, _I32P]),
     "tc_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I32P, _I32P]),
+    "tc_plan_get_gett_config": (ctypes.c_int, [_VP, _I32P, _I32P, _I32P, _I32P]),
     "tc_tuning_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
     "tc_tuning_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
     "tc_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_char_p, ctypes.c_int32, _I64P, ctypes.c_int]),
@@ -111,6 +119,10 @@ SIGNATURES = {
     "tc_batch_execute": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, _VP]),
     "tc_batch_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), _I64P, _I64P]),
     "tc_batch_device_status": (ctypes.c_int, [_VP]),
+    "tc_batch_autotune": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.POINTER(tc_batch_tuning), ctypes.c_int32,
+                                         _I32P]),
+    "tc_batch_config": (ctypes.c_int, [_VP, _I32P, _I32P, _I32P]),
+    "tc_batch_problem_tiles": (ctypes.c_int, [_VP, ctypes.c_int32, _I32P, _I32P, _I32P]),
     "tc_server_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]),
     "tc_server_submit": (ctypes.c_int, [_VP, ctypes.c_char_p, _I64P, ctypes.c_int, _VP, _VP, _VP, _I64P]),
     "tc_server_poll": (ctypes.c_int, [_VP, ctypes.c_int64, _I32P, ctypes.POINTER(ctypes.c_double)]),
@@ -392,6 +404,27 @@ class Batch:
     def device_status(self):
         _check(load().tc_batch_device_status(self.handle), "tc_batch_device_status")
 
+    def autotune(self, stream=None, reps=5):
+        """Per shape class: the fastest (tile shape, K chunk) by timing; leaves policy 2 selected."""
+        cap = 9 * 8 * 3  # ceil(log2 M) <= 8, ceil(log2 K) <= 7, three N buckets
+        buf = (tc_batch_tuning * cap)()
+        n = ctypes.c_int32()
+        _check(load().tc_batch_autotune(self.handle, _stream(stream), int(reps), buf, cap, ctypes.byref(n)),
+               "tc_batch_autotune")
+        return [{f: getattr(buf[i], f) for f, _ in tc_batch_tuning._fields_} for i in range(min(n.value, cap))]
+
+    def config(self):
+        p, s, w = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().tc_batch_config(self.handle, ctypes.byref(p), ctypes.byref(s), ctypes.byref(w)),
+               "tc_batch_config")
+        return {"policy": p.value, "stages": s.value, "tile_n": w.value}
+
+    def problem_tiles(self, q):
+        m, n, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().tc_batch_problem_tiles(self.handle, int(q), ctypes.byref(m), ctypes.byref(n), ctypes.byref(k)),
+               "tc_batch_problem_tiles")
+        return m.value, n.value, k.value
+
     def close(self):
         if self.handle is not None and _lib is not None:
             load().tc_batch_destroy(self.handle)
@@ -506,6 +539,12 @@ class Plan:
 
     def autotune(self, A=None, B=None, C=None, stream=None):
         return tc_autotune(self.handle, A, B, C, stream)
+
+    def gett_config(self):
+        v = [ctypes.c_int32() for _ in range(4)]
+        _check(load().tc_plan_get_gett_config(self.handle, *[ctypes.byref(x) for x in v]),
+               "tc_plan_get_gett_config")
+        return {"width": v[0].value, "tma": v[1].value, "pair": v[2].value, "pack": v[3].value}
 
     def device_status(self):
         tc_plan_device_status(self.handle)

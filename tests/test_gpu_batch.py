@@ -109,6 +109,118 @@ def test_batch_alpha_beta(tcmod):
     batch.close()
 
 
+def class_of(M, N, K):
+    # the autotuner's shape class: ceil(log2 M), ceil(log2 K), N bucket
+    cl = lambda x: int(np.ceil(np.log2(x))) if x > 1 else 0
+    return min(cl(M), 8), min(cl(K), 7), 0 if N <= 256 else (1 if N <= 2048 else 2)
+
+
+def merged(spec, ext):
+    c, a, b = oc.parse_spec(spec)
+    e = dict(zip(oc.index_order(spec), ext))
+    M = int(np.prod([e[x] for x in a if x in c]))
+    N = int(np.prod([e[x] for x in b if x in c]))
+    K = int(np.prod([e[x] for x in a if x in b and x not in c]))
+    return M, N, K
+
+
+def chunk_useful(bk, kmax):
+    return bk == 8 or kmax > bk // 2
+
+
+def stage_fits(s, bk):
+    pitch = 4 * (((bk + 3) >> 2) | 1)
+    return bk * (8 << s) + (512 >> s) * pitch <= 6400
+
+
+# every (tile shape, K chunk) the SIMT kernel runs
+SHAPE_CHUNKS = [(s, bk) for s in range(5) for bk in (8, 16, 32) if stage_fits(s, bk)]
+
+# layouts: the benchmark's (16-byte copies of B, staged C), k-contiguous A
+# (element copies of A), n-contiguous B (element copies of B), C with n
+# fastest (direct stores); extents with odd K, K over several chunks,
+# M over 128 (several row tiles)
+LAYOUT_CASES = [
+    ("abc=ai,ibc", [[8, 3, 5, 4], [13, 7, 9, 12], [37, 5, 11, 5], [70, 9, 2, 40], [128, 4, 33, 32],
+                    [200, 3, 6, 7], [1, 64, 2, 70], [9, 1, 1, 1]]),
+    ("abc=ia,ibc", [[8, 3, 5, 4], [13, 7, 9, 12], [37, 5, 11, 5], [70, 9, 2, 40], [130, 4, 3, 33]]),
+    ("abc=ai,bci", [[8, 3, 5, 4], [13, 7, 9, 12], [37, 5, 11, 5], [70, 9, 2, 40], [130, 4, 3, 33]]),
+    ("bca=ai,ibc", [[8, 3, 5, 4], [13, 7, 9, 12], [37, 5, 11, 5], [70, 9, 2, 40], [130, 4, 3, 33]]),
+]
+
+
+def forced_cache(tmp_path, spec, dtype_code, rows, s, bk):
+    # tuning-cache entries forcing (tile shape s, chunk bk) on every class of
+    # the rows; keys follow the library's "batch|spec|dtype|class|device"
+    name = torch.cuda.get_device_name()
+    lines = []
+    for ext in rows:
+        M, N, K = merged(spec, ext)
+        m, k, n = class_of(M, N, K)
+        kb = bk if chunk_useful(bk, 1 << k) else 8
+        key = f"batch|{spec}|{dtype_code}|m{m}k{k}n{n}|{name}"
+        lines.append('{"key": "%s", "batch_k_chunk": %d, "batch_tile_m": %d}' % (key, kb, 8 << s))
+    path = tmp_path / f"force_{s}_{bk}.jsonl"
+    path.write_text("\n".join(lines) + "\n")
+    return path
+
+
+def operands_offset(spec, ext, dtype, seed, offset, integer=True):
+    # device copies starting `offset` elements into their allocation (an
+    # offset of 1 defeats every 16-byte copy and shifts the staged C)
+    tdt = {"f32": torch.float32, "f64": torch.float64}[dtype]
+    gen = synth.integer_operands if integer else synth.uniform_operands
+    A, B, _ = gen(spec, ext, seed=seed)
+    out = []
+    for X in (A, B):
+        buf = torch.zeros(X.size + offset, dtype=tdt, device="cuda")
+        buf[offset:] = torch.from_numpy(X).to(tdt).cuda()
+        out.append(buf[offset:])
+    n = synth.dense_sizes(spec, ext)[0]
+    cbuf = torch.full((n + offset,), float("nan"), dtype=tdt, device="cuda")
+    return A, B, out[0], out[1], cbuf[offset:]
+
+
+def test_batch_autotune_classes_and_bits(tcmod):
+    rows = problems(400, 8, 128, seed=8)
+    As, Bs, Cs, host = make(rows, "f32", 80)
+    spec = SPEC
+    batch = tcmod.Batch(spec, rows, "f32")
+    batch.set_operands(As, Bs, Cs)
+    batch.execute()  # rule tiles
+    torch.cuda.synchronize()
+    ref = [c.clone() for c in Cs]
+    table = batch.autotune(reps=3)
+    classes = {class_of(*merged(spec, e)) for e in rows}
+    assert len(table) == len(classes)
+    assert {(r["m_log2"], r["k_log2"], r["n_class"]) for r in table} == classes
+    assert sum(r["problems"] for r in table) == len(rows)
+    for r in table:
+        if r["candidates"] == 0:  # answered from the cache of an earlier test
+            continue
+        assert r["seconds_best"] > 0 and r["seconds_best"] <= r["seconds_rule"] and \
+            r["seconds_best"] <= r["seconds_fixed"], r
+        assert (r["tile_m"], r["tile_n"]) in [(8 << s, 512 >> s) for s in range(5)]
+        assert r["k_chunk"] in (8, 16, 32)
+    cfg = batch.config()
+    assert cfg["policy"] == 2 and cfg["stages"] in (2, 3)
+    # the autotuner's launches left C = A.B; every tiling sums K in the same
+    # order, so the tuned launch gives the rule's bits
+    assert all(torch.equal(c, r) for c, r in zip(Cs, ref))
+    for c in Cs:
+        c.fill_(float("nan"))
+    batch.execute()
+    torch.cuda.synchronize()
+    assert all(torch.equal(c, r) for c, r in zip(Cs, ref))
+    # a second run of the tuner answers every class from the cache
+    again = batch.autotune(reps=3)
+    assert all(r["candidates"] == 0 for r in again)
+    batch.set_tiles(1)
+    with pytest.raises(tcmod.TcError):
+        tcmod.Batch(spec, rows[:3], "f32").set_tiles(2)  # no tuning yet
+    batch.close()
+
+
 def test_batch_rejects_unmergeable_spec(tcmod):
     with pytest.raises(tcmod.TcError):
         tcmod.Batch("ab=aij,jib", [[4, 4, 2, 2]], "f32")
@@ -190,3 +302,55 @@ def test_batch_bf16x3_alpha_beta(tcmod):
         want = 2.0 * oc.contract(SPEC, ext, A, B) - 1.5
         assert np.array_equal(C.double().cpu().numpy(), want)
     batch.close()
+
+
+def test_batch_bf16x3_autotune(tcmod):
+    rows = problems(120, 8, 128, seed=9)
+    As, Bs, Cs, host = make(rows, "bf16x3", 90)
+    batch = tcmod.Batch(SPEC, rows, "bf16x3")
+    batch.set_operands(As, Bs, Cs)
+    table = batch.autotune(reps=2)
+    assert len(table) == 1 and table[0]["tile_n"] in (128, 256) and table[0]["problems"] == len(rows)
+    assert table[0]["seconds_best"] <= min(table[0]["seconds_rule"], table[0]["seconds_fixed"])
+    assert batch.config()["tile_n"] == table[0]["tile_n"]
+    for c in Cs:
+        c.fill_(float("nan"))
+    batch.execute()
+    torch.cuda.synchronize()
+    batch.device_status()
+    for (A, B), ext, C in zip(host[:30], rows[:30], Cs[:30]):
+        Ar, Br = A.astype(np.float32).astype(np.float64), B.astype(np.float32).astype(np.float64)
+        want = oc.contract(SPEC, ext, Ar, Br)
+        scale = oc.contract(SPEC, ext, np.abs(Ar), np.abs(Br))
+        err = np.max(np.abs(C.double().cpu().numpy() - want) / scale)
+        assert err <= 1e-6, (ext, err)
+    batch.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("spec,rows", LAYOUT_CASES)
+def test_batch_every_tile_shape_chunk_and_layout(tcmod, tmp_path, spec, rows, dtype):
+    # exact on integer inputs for every (tile shape, K chunk), copy path and
+    # epilogue path, with aligned and misaligned operands
+    for offset in (0, 1):
+        host, As, Bs, Cs = [], [], [], []
+        for q, ext in enumerate(rows):
+            A, B, dA, dB, dC = operands_offset(spec, ext, dtype, 70 + q, offset)
+            host.append((A, B))
+            As.append(dA), Bs.append(dB), Cs.append(dC)
+        want = [oc.contract(spec, ext, A, B) for ext, (A, B) in zip(rows, host)]
+        batch = tcmod.Batch(spec, rows, dtype)
+        batch.set_operands(As, Bs, Cs)
+        for s, bk in SHAPE_CHUNKS:
+            tcmod.tc_tuning_cache_load(forced_cache(tmp_path, spec, tcmod.DTYPES[dtype], rows, s, bk))
+            table = batch.autotune(reps=1)
+            assert all(r["candidates"] == 0 and r["tile_m"] == 8 << s for r in table), table
+            for q in range(len(rows)):
+                assert batch.problem_tiles(q)[:2] == (8 << s, 512 >> s)
+            for c in Cs:
+                c.fill_(float("nan"))
+            batch.execute()
+            torch.cuda.synchronize()
+            for ext, C, w in zip(rows, Cs, want):
+                assert np.array_equal(C.double().cpu().numpy(), w), (spec, ext, s, bk, offset)
+        batch.close()
