@@ -408,10 +408,14 @@ tc_status tc_batch_destroy(tc_batch batch);
  * 0 (fixed) 64 x 64 with chunks of 16; 1 (rule, the default) the smallest
  * tile height that covers the problem's M, with the largest chunk that
  * fits; 2 (autotuned) the choice of tc_batch_autotune for the problem's
- * shape class.  TC_BF16X3 tiles are 128 x w with one w for the batch: 256
- * (fixed), the w in {128, 256} with the fewest padded columns plus 64 per
- * tile (rule), or the autotuner's.  Policy 2 before tc_batch_autotune is
- * TC_ERROR_INVALID_ARGUMENT. */
+ * shape class.  TC_BF16X3: 0 (fixed) tensor-core GETT tiles of 128 x 256;
+ * 1 (rule) the split-BF16 stream kernel -- one MMA tile per 128 columns n
+ * with all of M, for batches whose every problem has A, B and C dense
+ * along m, k and m, K a multiple of 4 up to 32 and M up to 128 (with A
+ * and B 16-byte aligned at execution; otherwise GETT tiles) -- else GETT
+ * tiles 128 x w with the w in {128, 256} with the fewest padded columns
+ * plus 64 per tile; 2 the autotuner's.  Policy 2 before tc_batch_autotune
+ * is TC_ERROR_INVALID_ARGUMENT. */
 tc_status tc_batch_set_tiles(tc_batch batch, int32_t policy);
 
 /* Host arrays of count device pointers, in the caller's problem order. */
@@ -442,6 +446,7 @@ typedef struct {
     int32_t problems;     /* problems in the class */
     int32_t candidates;   /* configurations timed (0: answered from the tuning cache) */
     int32_t tile_m, tile_n, k_chunk;  /* the fastest configuration */
+    int32_t kernel;       /* its kernel: 0 SIMT, 1 tensor-core GETT tiles, 2 split-BF16 stream */
     double seconds_best;  /* the class alone at that configuration (median; -1 if cached) */
     double seconds_rule;  /* ... at policy 1's configuration (-1 if cached) */
     double seconds_fixed; /* ... at policy 0's configuration (-1 if cached) */
@@ -452,17 +457,20 @@ typedef struct {
  * the class's problems alone (one warm-up, median of reps launches on
  * stream), keeps the fastest, then times the whole batch with 2 and 3
  * pipeline stages; the class choices go to the tuning cache, and a class
- * found there is not timed.  TC_BF16X3: times the whole batch at tile
- * widths 128 and 256.  Leaves policy 2 selected.  Every timed launch runs
+ * found there is not timed.  TC_BF16X3: times the whole batch on GETT
+ * tiles of width 128 and 256 and, where every problem suits it, on the
+ * stream kernel.  Leaves policy 2 selected.  Every timed launch runs
  * with alpha = 1, beta = 0, so each C_q holds A_q.B_q afterwards.  Writes
  * up to capacity class rows to classes and the number of classes to
  * *n_classes (may be NULL).  Blocks until the timings are done. */
 tc_status tc_batch_autotune(tc_batch batch, void *stream, int32_t reps, tc_batch_tuning *classes,
                             int32_t capacity, int32_t *n_classes);
 
-/* The current policy, SIMT pipeline stages (TC_BF16X3: 0) and split-BF16
- * tile width (SIMT: 0); any pointer may be NULL. */
-tc_status tc_batch_config(tc_batch batch, int32_t *policy, int32_t *stages, int32_t *tile_n);
+/* The current policy, SIMT pipeline stages (TC_BF16X3: 0), split-BF16
+ * tile width (SIMT: 0) and kernel (0 SIMT, 1 tensor-core GETT tiles, 2
+ * split-BF16 stream); any pointer may be NULL. */
+tc_status tc_batch_config(tc_batch batch, int32_t *policy, int32_t *stages, int32_t *tile_n,
+                          int32_t *kernel);
 
 /* Tile rows, columns and K chunk of problem `problem` (caller's order)
  * under the current policy. */

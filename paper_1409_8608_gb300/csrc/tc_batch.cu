@@ -388,9 +388,13 @@ struct BatchImpl {
     int tuned_stages = 2;
     std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
     bool has_tuning = false;
-    // split-BF16 (tensor-core GETT tiles of 128 x bn)
+    // split-BF16: the stream kernel (one tile per 128 columns) or the
+    // tensor-core GETT tiles of 128 x bn
+    int bf_stream = 0;
     int bn = 128;
     int tuned_bn = 0;
+    int tuned_stream = 0;
+    bool stream_layout = false;  // every problem's strides, M and K suit the stream kernel
     int nprod = 6;
     void *ddescs = nullptr;           // one kernel descriptor per problem slot
     int *dstatus = nullptr;           // bounded-wait status word
@@ -478,9 +482,23 @@ int32_t flags_for(const BatchProblem &P, size_t esz) {
 void assign_tiles(BatchImpl &b) {
     int64_t t = 0;
     if (b.dtype == TC_BF16X3) {
-        // 128 x bn tensor-core tiles, one width for the launch: the width
-        // with the fewest padded columns plus a fixed per-tile cost of 64
-        // columns (rule), 256 (fixed), or the autotuner's
+        // the stream kernel (rule, where every problem suits it), or
+        // 128 x bn tensor-core GETT tiles with one width for the launch: the
+        // width with the fewest padded columns plus a fixed per-tile cost of
+        // 64 columns (rule otherwise), 256 (fixed); or the autotuner's choice
+        b.bf_stream = b.policy == 2 ? b.tuned_stream : (b.policy == 1 && b.stream_layout);
+        if (b.bf_stream) {
+            for (auto &P : b.probs) {
+                P.shape = 0;
+                P.bk = 32;
+                P.tiles_m = 1;
+                P.tile0 = t;
+                t += stream_tiles(P);
+            }
+            b.total_tiles = t;
+            b.dirty = true;
+            return;
+        }
         int bn = 256;
         if (b.policy == 2) {
             bn = b.tuned_bn;
@@ -728,6 +746,8 @@ tc_status tc_batch_create(tc_batch *out, const char *spec, int32_t count, const 
     std::stable_sort(b.order.begin(), b.order.end(), [&](int x, int y) { return work[x] > work[y]; });
     b.probs.resize(count);
     for (int32_t slot = 0; slot < count; ++slot) b.probs[slot] = probs[b.order[slot]];
+    b.stream_layout = dtype == TC_BF16X3;
+    for (const auto &P : b.probs) b.stream_layout = b.stream_layout && stream_eligible(P);  // no pointers yet
     assign_tiles(b);
     *out = h;
     return TC_SUCCESS;
@@ -784,6 +804,17 @@ tc_status tc_batch_prepare(tc_batch batch) {
             return fail(TC_ERROR_OUT_OF_MEMORY, cudaGetErrorString(e));
         }
         b.dirty = true;
+    }
+    if (b.dtype == TC_BF16X3 && b.bf_stream) {
+        bool ok = true;
+        for (const auto &P : b.probs) ok = ok && stream_eligible(P);
+        if (!ok) {  // an operand is not 16-byte aligned: GETT tiles instead
+            const int keep = b.policy;
+            b.policy = 1;
+            b.stream_layout = false;
+            assign_tiles(b);
+            b.policy = keep == 2 ? 1 : keep;
+        }
     }
     if (b.total_tiles >= ((int64_t)1 << 31)) return fail(TC_ERROR_INVALID_EXTENT, "2^31 tiles or more in one batch");
     if (b.total_tiles > b.dtile_cap) {
@@ -846,6 +877,7 @@ tc_status tc_batch_execute(tc_batch batch, const void *alpha, const void *beta, 
         for (const auto &P : b.probs)
             if (P.K > 32) one_stage = 0;
         auto run = [&](int64_t t0, int64_t t1) {
+            if (b.bf_stream) return stream_launch_batch(b.dprobs, b.dtile_prob, t0, t1, a, be, b.nprod, b.dstatus, stream);
             return gett_launch_batch(b.ddescs, b.dtile_prob, t0, t1, b.bn, a, be, b.nprod, b.dstatus, one_stage, 0,
                                      stream);
         };
@@ -881,15 +913,20 @@ tc_status tc_batch_autotune(tc_batch batch, void *stream, int32_t reps, tc_batch
     b.last_stream = stream;
     std::vector<tc_batch_tuning> rows;
     if (b.dtype == TC_BF16X3) {
-        // one tile width per launch: time the whole batch at each
+        // candidates for the whole batch: GETT tiles 128 x 128 and 128 x 256,
+        // and the stream kernel where every problem suits it
         const float onef = 1.0f, zerof = 0.0f;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        double tw[2] = {0, 0};
-        const int saved_policy = b.policy, saved_bn = b.tuned_bn;
-        for (int w = 0; w < 2 && s == TC_SUCCESS; ++w) {
+        bool stream_ok = b.stream_layout;
+        for (const auto &P : b.probs) stream_ok = stream_ok && stream_eligible(P);
+        const int ncand = stream_ok ? 3 : 2;
+        double tw[3] = {0, 0, 0};
+        const int saved_policy = b.policy, saved_bn = b.tuned_bn, saved_stream = b.tuned_stream;
+        for (int w = 0; w < ncand && s == TC_SUCCESS; ++w) {
             b.tuned_bn = w == 0 ? 128 : 256;
+            b.tuned_stream = w == 2;
             b.policy = 2;
             assign_tiles(b);
             s = tc_batch_prepare(batch);
@@ -919,27 +956,37 @@ tc_status tc_batch_autotune(tc_batch batch, void *stream, int32_t reps, tc_batch
         if (s != TC_SUCCESS) {
             b.policy = saved_policy;
             b.tuned_bn = saved_bn;
+            b.tuned_stream = saved_stream;
             assign_tiles(b);
             return s;
         }
-        b.tuned_bn = tw[1] < tw[0] ? 256 : 128;
+        int best = 0;
+        for (int w = 1; w < ncand; ++w)
+            if (tw[w] < tw[best]) best = w;
+        b.tuned_bn = best == 0 ? 128 : 256;
+        b.tuned_stream = best == 2;
         b.has_tuning = true;
         b.policy = 2;
         assign_tiles(b);
-        // the rule's width, for the report
-        BatchImpl probe = b;
-        probe.ddescs = nullptr, probe.dstatus = nullptr, probe.dprobs = nullptr, probe.dtile_prob = nullptr;
-        probe.policy = 1;
-        assign_tiles(probe);
         tc_batch_tuning r{};
         r.m_log2 = r.k_log2 = r.n_class = -1;
         r.problems = b.count;
-        r.candidates = 2;
+        r.candidates = ncand;
+        r.kernel = best == 2 ? 2 : 1;
         r.tile_m = 128;
-        r.tile_n = b.tuned_bn;
+        r.tile_n = best == 2 ? 128 : b.tuned_bn;
         r.k_chunk = 32;
-        r.seconds_best = std::min(tw[0], tw[1]);
-        r.seconds_rule = probe.bn == 256 ? tw[1] : tw[0];
+        r.seconds_best = tw[best];
+        // the rule: the stream kernel where possible, else the padded-column width
+        if (stream_ok) {
+            r.seconds_rule = tw[2];
+        } else {
+            BatchImpl probe = b;
+            probe.ddescs = nullptr, probe.dstatus = nullptr, probe.dprobs = nullptr, probe.dtile_prob = nullptr;
+            probe.policy = 1;
+            assign_tiles(probe);
+            r.seconds_rule = probe.bn == 256 ? tw[1] : tw[0];
+        }
         r.seconds_fixed = tw[1];
         rows.push_back(r);
     } else {
@@ -963,6 +1010,7 @@ tc_status tc_batch_autotune(tc_batch batch, void *stream, int32_t reps, tc_batch
             r.k_log2 = std::get<1>(cls);
             r.n_class = std::get<2>(cls);
             r.problems = (int32_t)g.second.size();
+            r.kernel = 0;
             std::map<std::string, int> cached;
             if (tuning_get(class_key(b, cls), cached) && cached.count("batch_tile_m") && cached.count("batch_k_chunk")) {
                 const int tm = cached["batch_tile_m"], bk = cached["batch_k_chunk"];
@@ -1031,12 +1079,14 @@ tc_status tc_batch_autotune(tc_batch batch, void *stream, int32_t reps, tc_batch
     return TC_SUCCESS;
 }
 
-tc_status tc_batch_config(tc_batch batch, int32_t *policy, int32_t *stages, int32_t *tile_n) {
+tc_status tc_batch_config(tc_batch batch, int32_t *policy, int32_t *stages, int32_t *tile_n, int32_t *kernel) {
     if (!batch) return fail(TC_ERROR_INVALID_ARGUMENT, "batch is NULL");
     const BatchImpl &b = batch->b;
+    const bool bf = b.dtype == TC_BF16X3;
     if (policy) *policy = b.policy;
-    if (stages) *stages = b.dtype == TC_BF16X3 ? 0 : b.stages;
-    if (tile_n) *tile_n = b.dtype == TC_BF16X3 ? b.bn : 0;
+    if (stages) *stages = bf ? 0 : b.stages;
+    if (tile_n) *tile_n = bf ? (b.bf_stream ? 128 : b.bn) : 0;
+    if (kernel) *kernel = bf ? (b.bf_stream ? 2 : 1) : 0;
     return TC_SUCCESS;
 }
 
@@ -1050,7 +1100,7 @@ tc_status tc_batch_problem_tiles(tc_batch batch, int32_t problem, int32_t *tile_
     const BatchProblem &P = b.probs[slot];
     const bool simt = b.dtype != TC_BF16X3;
     if (tile_m) *tile_m = simt ? shape_rows(P.shape) : 128;
-    if (tile_n) *tile_n = simt ? shape_cols(P.shape) : b.bn;
+    if (tile_n) *tile_n = simt ? shape_cols(P.shape) : (b.bf_stream ? 128 : b.bn);
     if (k_chunk) *k_chunk = P.bk;
     return TC_SUCCESS;
 }

@@ -172,6 +172,14 @@ constexpr int32_t kBatchStagedC = 4;  // a tile's C is one contiguous run (stage
 // Batched split-BF16 on the tensor-core GETT kernel: one device descriptor
 // per problem (gett_desc_bytes each, filled by gett_fill_batch_desc for
 // 128 x bn tiles), then one launch over tiles [t_begin, t_end).
+// Split-BF16 stream kernel of the batched form (tc_stream.cu): problems
+// with A, B and C dense along m, k and m, K a multiple of 4 up to 32, M up
+// to 128, 16-byte aligned A and B; one tile per 128 columns n.
+bool stream_eligible(const BatchProblem &P);
+int64_t stream_tiles(const BatchProblem &P);
+tc_status stream_launch_batch(const BatchProblem *dprobs, const int32_t *dtile_prob, int64_t t_begin, int64_t t_end,
+                              float alpha, float beta, int nprod, int *dstatus, void *stream);
+
 // Process-wide tuning cache (tc_tuning_cache_save / _load): named integer
 // choices per key.
 bool tuning_get(const std::string &key, std::map<std::string, int> &out);

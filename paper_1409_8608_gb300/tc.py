@@ -60,7 +60,8 @@ class tc_setup_item(ctypes.Structure):
 class tc_batch_tuning(ctypes.Structure):
     _fields_ = [("m_log2", ctypes.c_int32), ("k_log2", ctypes.c_int32), ("n_class", ctypes.c_int32),
                 ("problems", ctypes.c_int32), ("candidates", ctypes.c_int32), ("tile_m", ctypes.c_int32),
-                ("tile_n", ctypes.c_int32), ("k_chunk", ctypes.c_int32), ("seconds_best", ctypes.c_double),
+                ("tile_n", ctypes.c_int32), ("k_chunk", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("seconds_best", ctypes.c_double),
                 ("seconds_rule", ctypes.c_double), ("seconds_fixed", ctypes.c_double)]
 
 
@@ -121,7 +122,7 @@ SIGNATURES = {
     "tc_batch_device_status": (ctypes.c_int, [_VP]),
     "tc_batch_autotune": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.POINTER(tc_batch_tuning), ctypes.c_int32,
                                          _I32P]),
-    "tc_batch_config": (ctypes.c_int, [_VP, _I32P, _I32P, _I32P]),
+    "tc_batch_config": (ctypes.c_int, [_VP, _I32P, _I32P, _I32P, _I32P]),
     "tc_batch_problem_tiles": (ctypes.c_int, [_VP, ctypes.c_int32, _I32P, _I32P, _I32P]),
     "tc_server_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]),
     "tc_server_submit": (ctypes.c_int, [_VP, ctypes.c_char_p, _I64P, ctypes.c_int, _VP, _VP, _VP, _I64P]),
@@ -414,10 +415,10 @@ class Batch:
         return [{f: getattr(buf[i], f) for f, _ in tc_batch_tuning._fields_} for i in range(min(n.value, cap))]
 
     def config(self):
-        p, s, w = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-        _check(load().tc_batch_config(self.handle, ctypes.byref(p), ctypes.byref(s), ctypes.byref(w)),
-               "tc_batch_config")
-        return {"policy": p.value, "stages": s.value, "tile_n": w.value}
+        v = [ctypes.c_int32() for _ in range(4)]
+        _check(load().tc_batch_config(self.handle, *[ctypes.byref(x) for x in v]), "tc_batch_config")
+        return {"policy": v[0].value, "stages": v[1].value, "tile_n": v[2].value,
+                "kernel": ["simt", "gett", "stream"][v[3].value]}
 
     def problem_tiles(self, q):
         m, n, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

@@ -304,6 +304,76 @@ def test_batch_bf16x3_alpha_beta(tcmod):
     batch.close()
 
 
+# the split-BF16 stream kernel: M from 1 to 128 (MMA N 16..128), K a
+# multiple of 4 in 16- and 32-wide stages, N ragged around the 128-column
+# tile; rows are [a, b, c, i] of abc=ai,ibc (M = a, N = b c, K = i)
+STREAM_ROWS = [[1, 1, 1, 4], [7, 127, 1, 12], [16, 128, 1, 16], [17, 129, 1, 20], [100, 3, 100, 32],
+               [128, 5, 61, 8], [33, 1, 2, 28], [64, 256, 1, 24], [5, 40, 7, 4], [128, 128, 2, 32]]
+
+
+def test_batch_bf16x3_stream_exact_on_integers(tcmod):
+    As, Bs, Cs, host = make(STREAM_ROWS, "bf16x3", 100, integer=True)
+    batch = tcmod.Batch(SPEC, STREAM_ROWS, "bf16x3")
+    batch.set_operands(As, Bs, Cs)
+    batch.prepare()
+    assert batch.config()["kernel"] == "stream"
+    batch.execute()
+    torch.cuda.synchronize()
+    batch.device_status()
+    for ext, (A, B), C in zip(STREAM_ROWS, host, Cs):
+        assert np.array_equal(C.double().cpu().numpy(), oc.contract(SPEC, ext, A, B)), ext
+    # alpha, beta and one launch per problem
+    C0 = [torch.from_numpy(synth.integer_operands(SPEC, e, seed=5, with_c=True)[2]).float().cuda()
+          for e in STREAM_ROWS]
+    for c, c0 in zip(Cs, C0):
+        c.copy_(c0)
+    batch.execute(alpha=2.0, beta=-3.0, per_problem=True)
+    torch.cuda.synchronize()
+    batch.device_status()
+    for ext, (A, B), C, c0 in zip(STREAM_ROWS, host, Cs, C0):
+        want = 2.0 * oc.contract(SPEC, ext, A, B) - 3.0 * c0.double().cpu().numpy()
+        assert np.array_equal(C.double().cpu().numpy(), want), ext
+    batch.close()
+
+
+def test_batch_bf16x3_stream_bound_and_fallbacks(tcmod):
+    # uniform inputs within the FP32-level target; a misaligned operand and
+    # a K that is not a multiple of 4 take the GETT tiles instead
+    rows = STREAM_ROWS
+    As, Bs, Cs, host = make(rows, "bf16x3", 110)
+    batch = tcmod.Batch(SPEC, rows, "bf16x3")
+    batch.set_operands(As, Bs, Cs)
+    batch.execute()
+    torch.cuda.synchronize()
+    batch.device_status()
+    for (A, B), ext, C in zip(host, rows, Cs):
+        Ar, Br = A.astype(np.float32).astype(np.float64), B.astype(np.float32).astype(np.float64)
+        want = oc.contract(SPEC, ext, Ar, Br)
+        scale = oc.contract(SPEC, ext, np.abs(Ar), np.abs(Br))
+        err = np.max(np.abs(C.double().cpu().numpy() - want) / scale)
+        assert err <= 1e-6, (ext, err)
+    batch.close()
+    # B of the first problem one element into its allocation
+    buf = torch.zeros(Bs[0].numel() + 1, device="cuda")
+    buf[1:] = Bs[0]
+    batch = tcmod.Batch(SPEC, rows, "bf16x3")
+    batch.set_operands(As, [buf[1:]] + Bs[1:], Cs)
+    batch.prepare()
+    assert batch.config()["kernel"] == "gett"
+    batch.close()
+    odd = [[9, 5, 3, 6], [20, 7, 2, 4]]
+    As2, Bs2, Cs2, host2 = make(odd, "bf16x3", 120, integer=True)
+    batch = tcmod.Batch(SPEC, odd, "bf16x3")
+    batch.set_operands(As2, Bs2, Cs2)
+    batch.execute()
+    torch.cuda.synchronize()
+    batch.device_status()
+    assert batch.config()["kernel"] == "gett"
+    for ext, (A, B), C in zip(odd, host2, Cs2):
+        assert np.array_equal(C.double().cpu().numpy(), oc.contract(SPEC, ext, A, B)), ext
+    batch.close()
+
+
 def test_batch_bf16x3_autotune(tcmod):
     rows = problems(120, 8, 128, seed=9)
     As, Bs, Cs, host = make(rows, "bf16x3", 90)
@@ -311,8 +381,10 @@ def test_batch_bf16x3_autotune(tcmod):
     batch.set_operands(As, Bs, Cs)
     table = batch.autotune(reps=2)
     assert len(table) == 1 and table[0]["tile_n"] in (128, 256) and table[0]["problems"] == len(rows)
+    assert table[0]["candidates"] == 3 and table[0]["kernel"] in (1, 2)
     assert table[0]["seconds_best"] <= min(table[0]["seconds_rule"], table[0]["seconds_fixed"])
-    assert batch.config()["tile_n"] == table[0]["tile_n"]
+    cfg = batch.config()
+    assert cfg["tile_n"] == table[0]["tile_n"] and cfg["kernel"] == ["simt", "gett", "stream"][table[0]["kernel"]]
     for c in Cs:
         c.fill_(float("nan"))
     batch.execute()
