@@ -385,6 +385,70 @@ tc_status tc_plan_get_gett_config(tc_plan plan, int32_t *width, int32_t *tma, in
 tc_status tc_tuning_cache_save(const char *path);
 tc_status tc_tuning_cache_load(const char *path);
 
+/* ---- Contraction chains: several kernels in one tree --------------------
+ * Section 3.2: the access-distance method holds for trees with any
+ * combination of loops and several kernels.  A chain "D=X,Y,Z" (one letter
+ * a-z per index; extents in order of first appearance in the spec; dense
+ * operands, first index fastest) computes every entry of D as the sum,
+ * over the indices not in D, of the product of the three operands' entries;
+ * every such index must appear in at least two operands.  It runs as two
+ * pairwise contractions through an intermediate T, each a plan of this
+ * library: one variant per pair contracted first (when both steps contract
+ * an index), and for each a sliced form that loops one index of D carried
+ * by the pair (not by the third operand) around both kernels, so that T
+ * holds one slice.  T's modes: the pair's indices still needed, D's order
+ * first, then the third operand's.  Host work only at creation. */
+typedef struct tc_chain_s *tc_chain;
+
+typedef struct {
+    int32_t first[2];          /* operands contracted first (0 X, 1 Y, 2 Z) */
+    int32_t third;
+    char sliced;               /* index looped around both steps, 0: none */
+    int64_t slices;            /* its extent (1 when not sliced) */
+    int64_t workspace_bytes;   /* the intermediate (one slice) */
+    double flops;              /* both steps, every slice */
+    int32_t algorithm[2];      /* each step's selected algorithm id */
+    double predicted_seconds;  /* (step 1 + step 2 predictions) x slices; < 0: none */
+} tc_chain_variant;
+
+/* dtype TC_F64, TC_F32 or an FP32-input tensor-core dtype (TC_TF32,
+ * TC_BF16X3, TC_TF32X3; T is FP32).  Selects the variant with the fewest
+ * flops (then the fewest slices).  Rejects specs that do not read "D=X,Y,Z",
+ * indices outside a-z or repeated within an operand, an index outside D in
+ * fewer than two operands, and chains with no valid variant. */
+tc_status tc_chain_create(tc_chain *out, const char *spec, const int64_t *extents, tc_dtype dtype);
+tc_status tc_chain_destroy(tc_chain chain);
+
+/* Up to capacity variants into buf; their number into *count (may be NULL). */
+tc_status tc_chain_variants(tc_chain chain, tc_chain_variant *buf, int32_t capacity, int32_t *count);
+
+/* Largest intermediate in bytes that tc_chain_select(-1) may choose (-1: no
+ * limit). */
+tc_status tc_chain_set_workspace_limit(tc_chain chain, int64_t bytes);
+
+/* Predicts every variant: for each step, tc_predict over every algorithm
+ * (all_algorithms = 1) or over the fused GETT alone (0), keeping the
+ * fastest; then selects as tc_chain_select(-1).  Runs micro-benchmarks on
+ * stream with scratch operands; blocks until done. */
+tc_status tc_chain_predict(tc_chain chain, int32_t all_algorithms, void *stream);
+
+/* variant >= 0: that variant (TC_ERROR_INVALID_ARGUMENT if its T exceeds
+ * the limit); -1: the smallest prediction if every variant has one, else
+ * the fewest flops (then the fewest slices), among the variants within the
+ * limit. */
+tc_status tc_chain_select(tc_chain chain, int32_t variant);
+tc_status tc_chain_selected(tc_chain chain, int32_t *variant);
+
+/* D = alpha * X Y Z + beta * D on stream (device pointers; alpha/beta as
+ * for the steps' dtype).  The intermediate is allocated on first use and
+ * kept; step 1 runs with alpha 1, beta 0.  A plan's stream rule applies to
+ * the chain: one stream at a time. */
+tc_status tc_chain_execute(tc_chain chain, const void *alpha, const void *X, const void *Y,
+                           const void *Z, const void *beta, void *D, void *stream);
+
+/* Both steps' tc_plan_device_status (the selected variant). */
+tc_status tc_chain_device_status(tc_chain chain);
+
 /* ---- Batched form: many independent contractions, one launch ------------
  * No paper counterpart.  Every problem has the batch's spec and its own
  * extents, dense Fortran-ordered operands, and must reduce to a strided

@@ -65,6 +65,12 @@ class tc_batch_tuning(ctypes.Structure):
                 ("seconds_rule", ctypes.c_double), ("seconds_fixed", ctypes.c_double)]
 
 
+class tc_chain_variant(ctypes.Structure):
+    _fields_ = [("first", ctypes.c_int32 * 2), ("third", ctypes.c_int32), ("sliced", ctypes.c_char),
+                ("slices", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64), ("flops", ctypes.c_double),
+                ("algorithm", ctypes.c_int32 * 2), ("predicted_seconds", ctypes.c_double)]
+
+
 class tc_server_report(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("admission_stalls", ctypes.c_int64), ("peak_inflight", ctypes.c_int64),
@@ -124,6 +130,15 @@ SIGNATURES = {
                                          _I32P]),
     "tc_batch_config": (ctypes.c_int, [_VP, _I32P, _I32P, _I32P, _I32P]),
     "tc_batch_problem_tiles": (ctypes.c_int, [_VP, ctypes.c_int32, _I32P, _I32P, _I32P]),
+    "tc_chain_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_char_p, _I64P, ctypes.c_int]),
+    "tc_chain_destroy": (ctypes.c_int, [_VP]),
+    "tc_chain_variants": (ctypes.c_int, [_VP, ctypes.POINTER(tc_chain_variant), ctypes.c_int32, _I32P]),
+    "tc_chain_set_workspace_limit": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "tc_chain_predict": (ctypes.c_int, [_VP, ctypes.c_int32, _VP]),
+    "tc_chain_select": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "tc_chain_selected": (ctypes.c_int, [_VP, _I32P]),
+    "tc_chain_execute": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "tc_chain_device_status": (ctypes.c_int, [_VP]),
     "tc_server_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]),
     "tc_server_submit": (ctypes.c_int, [_VP, ctypes.c_char_p, _I64P, ctypes.c_int, _VP, _VP, _VP, _I64P]),
     "tc_server_poll": (ctypes.c_int, [_VP, ctypes.c_int64, _I32P, ctypes.POINTER(ctypes.c_double)]),
@@ -429,6 +444,65 @@ class Batch:
     def close(self):
         if self.handle is not None and _lib is not None:
             load().tc_batch_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Chain:
+    """Owns a tc_chain: D = X Y Z through an intermediate, order and slicing
+    chosen by flops or by prediction."""
+
+    def __init__(self, spec, extents, dtype="f64"):
+        h = ctypes.c_void_p()
+        _check(load().tc_chain_create(ctypes.byref(h), spec.encode(), _i64([int(e) for e in extents]),
+                                      DTYPES[dtype]), "tc_chain_create")
+        self.handle = h
+        self.dtype = dtype
+
+    def variants(self):
+        n = ctypes.c_int32()
+        _check(load().tc_chain_variants(self.handle, None, 0, ctypes.byref(n)), "tc_chain_variants")
+        buf = (tc_chain_variant * max(1, n.value))()
+        _check(load().tc_chain_variants(self.handle, buf, n.value, ctypes.byref(n)), "tc_chain_variants")
+        out = []
+        for v in buf[:n.value]:
+            out.append({"first": (v.first[0], v.first[1]), "third": v.third,
+                        "sliced": v.sliced.decode() if v.sliced != b"\x00" else None, "slices": v.slices,
+                        "workspace_bytes": v.workspace_bytes, "flops": v.flops,
+                        "algorithm": (v.algorithm[0], v.algorithm[1]), "predicted_seconds": v.predicted_seconds})
+        return out
+
+    def set_workspace_limit(self, nbytes):
+        _check(load().tc_chain_set_workspace_limit(self.handle, int(nbytes)), "tc_chain_set_workspace_limit")
+
+    def predict(self, all_algorithms=False, stream=None):
+        _check(load().tc_chain_predict(self.handle, 1 if all_algorithms else 0, _stream(stream)), "tc_chain_predict")
+
+    def select(self, variant=-1):
+        _check(load().tc_chain_select(self.handle, int(variant)), "tc_chain_select")
+
+    def selected(self):
+        v = ctypes.c_int32()
+        _check(load().tc_chain_selected(self.handle, ctypes.byref(v)), "tc_chain_selected")
+        return v.value
+
+    def execute(self, X, Y, Z, D, alpha=1.0, beta=0.0, stream=None):
+        sd = "f64" if self.dtype == "f64" else "f32"
+        a, b = _scalar(alpha, sd), _scalar(beta, sd)
+        _check(load().tc_chain_execute(self.handle, ctypes.addressof(a), _ptr(X), _ptr(Y), _ptr(Z),
+                                       ctypes.addressof(b), _ptr(D), _stream(stream)), "tc_chain_execute")
+
+    def device_status(self):
+        _check(load().tc_chain_device_status(self.handle), "tc_chain_device_status")
+
+    def close(self):
+        if self.handle is not None and _lib is not None:
+            load().tc_chain_destroy(self.handle)
         self.handle = None
 
     def __del__(self):
