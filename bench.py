@@ -13,6 +13,8 @@ measured error, and one object per other workload of the study:
   ranking    abc=iaj,jbic n=128 i=j=16 FP64: predicted vs measured, all 177
   precision  abc=ai,ibc 512^3 i=64 and ab=aij,jib 4096^2 i=j=64: every
              precision form, time, roofline, error (uniform and lognormal)
+  chain      abc=ai,ij,jbc a=b=c=512 i=j=16 FP64: every order / slicing of a
+             three-operand chain, predicted vs measured
   batched    4096 x abc=ai,ibc (a,b,c log-uniform [8,128], i in {4,...,32})
   serving    Poisson request stream, 10 s after 1 s of warm-up, rate sweep
 
@@ -493,6 +495,55 @@ def run_ranking(tc, n=128, dtype="f64"):
             "prediction_s": r["prediction_seconds"], "measurement_s": r["measurement_seconds"]}
 
 
+CHAIN_WORKLOAD = ("abc=ai,ij,jbc", [512, 512, 512, 16, 16])  # a, b, c, i, j: the headline's shape as a chain
+
+
+def run_chain(tc, dev, reps=3):
+    """Section 3.2's several-kernel trees: every variant of a three-operand
+    chain (pair order, sliced or not) predicted from its two steps'
+    micro-benchmarks and measured whole, FP64."""
+    import torch
+    spec, ext = CHAIN_WORKLOAD
+    from paper_1409_8608_gb300 import synth
+    letters = []
+    for ch in spec.replace("=", "").replace(",", ""):
+        if ch not in letters:
+            letters.append(ch)
+    e = dict(zip(letters, ext))
+    d, ops = spec.split("=")[0], spec.split("=")[1].split(",")
+    size = lambda modes: int(np.prod([e[m] for m in modes]))
+    g = torch.Generator(device=dev).manual_seed(0)
+    X, Y, Z = (torch.rand(size(o), dtype=torch.float64, device=dev, generator=g) * 2 - 1 for o in ops)
+    D = torch.empty(size(d), dtype=torch.float64, device=dev)
+    ch = tc.Chain(spec, ext, "f64")
+    t0 = time.perf_counter()
+    ch.predict(all_algorithms=False)
+    t_pred = time.perf_counter() - t0
+    rows = []
+    for i, v in enumerate(ch.variants()):
+        ch.select(i)
+        ch.execute(X, Y, Z, D)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            ch.execute(X, Y, Z, D)
+            a1.record()
+            a1.synchronize()
+            ts.append(a0.elapsed_time(a1) * 1e-3)
+        rows.append({"first": list(v["first"]), "sliced": v["sliced"], "slices": v["slices"],
+                     "workspace_mb": v["workspace_bytes"] / 2**20, "gflop": v["flops"] / 1e9,
+                     "predicted_ms": v["predicted_seconds"] * 1e3, "measured_ms": statistics.median(ts) * 1e3})
+    ch.device_status()
+    ch.select(-1)
+    sel = ch.selected()
+    best = min(r["measured_ms"] for r in rows)
+    ch.close()
+    return {"workload": f"{spec} a=b=c=512 i=j=16 FP64 (X: ai, Y: ij, Z: jbc)", "variants": rows,
+            "selected": sel, "top1_regret": rows[sel]["measured_ms"] / best - 1.0, "prediction_s": t_pred}
+
+
 PRECISION_WORKLOADS = (
     ("abc=ai,ibc", [512, 512, 512, 64], "hbm"),
     ("ab=aij,jib", [4096, 4096, 64, 64], "tensor"),
@@ -690,6 +741,7 @@ def run_gpu(args):
         with torch.cuda.stream(stream):
             extras["small"] = run_small(tc)
             extras["ranking"] = run_ranking(tc)
+            extras["chain"] = run_chain(tc, dev)
             prec = run_precision(tc, dev, stream)
         torch.cuda.synchronize()
         extras["batched"] = run_batched(args)
