@@ -156,6 +156,72 @@ __global__ void __launch_bounds__(256) elementwise_kernel(const PhaseDesc d) {
     }
 }
 
+// Cooperative reduction (a phase with few outputs whose innermost contracted
+// index has unit stride in an input): a group of G lanes (a power of two,
+// 4..32) per kernel output splits that index (red's last mode), so the
+// group's loads are contiguous; each lane sums its share over every in-task
+// contracted loop, then the group adds the lanes' partial sums with a fixed
+// butterfly (the same order every run).
+template <typename T, int G>
+__global__ void __launch_bounds__(256) coop_reduce_kernel(const PhaseDesc d) {
+    const T *__restrict__ A = (const T *)d.A;
+    const T *__restrict__ B = (const T *)d.B;
+    T *__restrict__ C = (T *)d.C;
+    const int gl = threadIdx.x % G;  // lane within the group
+    const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
+    const int nr = d.red.n;
+    const int64_t kext = d.red.ext[nr - 1], ksA = d.red.sA[nr - 1], ksB = d.red.sB[nr - 1];
+    // every lane of a warp runs the same number of rounds (shuffles need the
+    // whole warp): the round's output is e = warp's first + the group's
+    const int64_t first = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    for (int64_t base = first - (threadIdx.x % 32) / G; base < d.total; base += groups) {
+        const int64_t e = base + (threadIdx.x % 32) / G;
+        const bool live = e < d.total;
+        int64_t r = live ? e : 0, oA = 0, oB = 0, oC = 0;
+        for (int m = 0; m < d.out.n; ++m) {
+            const int64_t x = r % d.out.ext[m];
+            r /= d.out.ext[m];
+            oA += x * d.out.sA[m];
+            oB += x * d.out.sB[m];
+            oC += x * d.out.sC[m];
+        }
+        for (int m = d.task.n - 1; m >= 0; --m) {
+            const int64_t x = r % d.task.ext[m];
+            r /= d.task.ext[m];
+            oA += x * d.task.sA[m];
+            oB += x * d.task.sB[m];
+            oC += x * d.task.sC[m];
+        }
+        T acc = T(0);
+        int64_t idx[kMaxModes];
+        for (int m = 0; m < nr - 1; ++m) idx[m] = 0;
+        for (;;) {
+            int64_t pa = oA, pb = oB;
+            for (int m = 0; m < nr - 1; ++m) {
+                pa += idx[m] * d.red.sA[m];
+                pb += idx[m] * d.red.sB[m];
+            }
+            if (live)
+                for (int64_t k = gl; k < kext; k += G) acc = fma_t<T>(A[pa + k * ksA], B[pb + k * ksB], acc);
+            int m = nr - 2;
+            while (m >= 0) {
+                if (++idx[m] < d.red.ext[m]) break;
+                idx[m] = 0;
+                --m;
+            }
+            if (m < 0) break;
+        }
+#pragma unroll
+        for (int off = G / 2; off > 0; off /= 2) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (live && gl == 0) {
+            T v = d.alpha_one ? acc : (T)d.alpha * acc;
+            if (d.init == 0) v += C[oC];
+            else if (d.init == 1) v = fma_t<T>((T)d.beta, C[oC], v);
+            C[oC] = v;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- gemm / SIMT GETT
 // One CTA computes a BM x BN tile of one task's C slice; K runs over the
 // linearised contracted space in chunks of BK staged through shared memory.
@@ -435,6 +501,17 @@ int sm_count() {
     return g_sm_count;
 }
 
+int device_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
 int64_t grid_for(int64_t total, int per_block) {
     int64_t blocks = (total + per_block - 1) / per_block;
     int64_t cap = (int64_t)sm_count() * 32;
@@ -587,6 +664,7 @@ tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *
 
     PhaseDesc pd;
     TileDesc td;
+    int coop_g = 0;  // lanes per output of coop_reduce_kernel (0: elementwise_kernel)
     std::memset(&pd, 0, sizeof(pd));
     std::memset(&td, 0, sizeof(td));
     int64_t ntasks = 1;
@@ -619,6 +697,30 @@ tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *
         pd.alpha = alpha;
         pd.beta = beta;
         pd.alpha_one = alpha_one;
+        // Access pattern per kernel (Table 1 rows 1-4): one thread per
+        // kernel output with consecutive threads along the output mode that
+        // is contiguous in C (elementwise_kernel; ger's two output modes are
+        // ordered so) -- axpy's vector and gemv's matrix with its free index
+        // contiguous are then read coalesced; dot and gemv sum their own
+        // contracted index in that thread.  When a phase has fewer outputs
+        // than the device holds threads in one wave and its innermost
+        // contracted index has unit stride in an input, a group of lanes per
+        // output splits that index instead (coop_reduce_kernel, loads
+        // contiguous across the group): the reduction, not the output count,
+        // then sets the parallelism.
+        const int kr = pd.red.n - 1;
+        if (alg.kernel == TC_KERNEL_GER && pd.out.n == 2 && pd.out.sC[1] < pd.out.sC[0]) {
+            std::swap(pd.out.ext[0], pd.out.ext[1]);
+            std::swap(pd.out.sA[0], pd.out.sA[1]);
+            std::swap(pd.out.sB[0], pd.out.sB[1]);
+            std::swap(pd.out.sC[0], pd.out.sC[1]);
+        }
+        const bool k_unit = kr >= 0 && (pd.red.sA[kr] == 1 || pd.red.sB[kr] == 1);
+        if (k_unit && pd.red.ext[kr] > 1 && pd.total < (int64_t)device_sms() * 1024) coop_g = 1;
+        if (coop_g) {
+            const int64_t kext = pd.red.ext[kr];
+            coop_g = kext <= 4 ? 4 : (kext <= 8 ? 8 : (kext <= 16 ? 16 : 32));
+        }
     }
 
     // C copy (reading for a C slice without a unit-stride mode): gather once,
@@ -710,8 +812,18 @@ tc_status run_nest(Plan &p, const Algorithm &alg, T alpha, const T *A, const T *
             q.C = Cptr;
             q.init = init;
             q.total = cut(pd.total);
-            int64_t grid = grid_for(q.total, 256);
-            elementwise_kernel<T><<<(unsigned)grid, 256, 0, st>>>(q);
+            if (coop_g) {
+                const int64_t grid = grid_for(q.total * coop_g, 256);
+                switch (coop_g) {
+                    case 4: coop_reduce_kernel<T, 4><<<(unsigned)grid, 256, 0, st>>>(q); break;
+                    case 8: coop_reduce_kernel<T, 8><<<(unsigned)grid, 256, 0, st>>>(q); break;
+                    case 16: coop_reduce_kernel<T, 16><<<(unsigned)grid, 256, 0, st>>>(q); break;
+                    default: coop_reduce_kernel<T, 32><<<(unsigned)grid, 256, 0, st>>>(q); break;
+                }
+            } else {
+                int64_t grid = grid_for(q.total, 256);
+                elementwise_kernel<T><<<(unsigned)grid, 256, 0, st>>>(q);
+            }
         }
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? TC_SUCCESS : fail(TC_ERROR_CUDA, cudaGetErrorString(e));

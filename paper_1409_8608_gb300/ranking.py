@@ -2,7 +2,7 @@
 contraction (the experiments of Sections 3-4, on the device).
 
     python -m paper_1409_8608_gb300.ranking --spec abc=iaj,jbic \\
-        --extents 256,256,256,16,16 --dtype f64 [--json out.json]
+        --extents 256,256,256,16,16 --dtype f64 [--json out.json] [--classes]
 
 Reports per algorithm the predicted and the measured seconds, and over all
 of them Spearman's rho and Kendall's tau of the two rankings, the top-1
@@ -117,6 +117,47 @@ def study(spec, extents, dtype="f64", seed=0, reps=5, cap=2.0, ids=None):
     }
 
 
+def class_study(spec, extents, dtype="f32", seed=0, reps=5, top=3, hbm_gbs=None):
+    """Per kernel class (Table 1: dot, axpy, gemv, ger, gemm): predict every
+    algorithm of the class, measure the `top` best predicted, and report the
+    class's best measured time with its compulsory traffic (A, B, C read
+    once, C written once) as GB/s -- the classes' own access patterns at a
+    size past L2."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tdt = {"f64": torch.float64, "f32": torch.float32}[dtype]
+    esz = 8 if dtype == "f64" else 4
+    A, B, _ = synth.uniform_operands(spec, extents, seed=seed)
+    nC, nA, nB = synth.dense_sizes(spec, extents)
+    dA = torch.from_numpy(A).to(tdt).to(dev)
+    dB = torch.from_numpy(B).to(tdt).to(dev)
+    dC = torch.zeros(nC, dtype=tdt, device=dev)
+    plan = tc.Plan(spec, extents, dtype=dtype)
+    algs = plan.algorithms()
+    flops = 2.0 * float(np.prod([float(e) for e in extents]))
+    nbytes = (nA + nB + 2 * nC) * esz
+    flush = torch.empty(int(256 << 20) // 4, dtype=torch.float32, device=dev)
+    out = {}
+    for kind in ("dot", "axpy", "gemv", "ger", "gemm"):
+        ids = [a["id"] for a in algs if a["kernel"] == kind]
+        if not ids:
+            continue
+        pred = plan.predict(ids, dA, dB, dC)
+        order = [i for _, i in sorted(zip(pred, ids)) if _ > 0][:top]
+        meas, _ = measure(plan, order, dA, dB, dC, flush, reps=reps, cap=5.0)
+        j = int(np.argmin(meas))
+        t = meas[j]
+        row = {"algorithms": len(ids), "measured": len(order), "best": algs[order[j]]["name"],
+               "ms": t * 1e3, "gflops": flops / t / 1e9, "compulsory_gbs": nbytes / t / 1e9,
+               "top_predicted": algs[order[0]]["name"], "top_predicted_ms": meas[0] * 1e3}
+        if hbm_gbs:
+            row["hbm_frac"] = row["compulsory_gbs"] / hbm_gbs
+        out[kind] = row
+    plan.close()
+    return {"spec": spec, "extents": list(extents), "dtype": dtype, "gflop": flops / 1e9,
+            "compulsory_gb": nbytes / 1e9, "classes": out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--spec", default="abc=iaj,jbic")
@@ -125,8 +166,12 @@ def main():
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--cap", type=float, default=2.0)
     ap.add_argument("--json", default=None)
+    ap.add_argument("--classes", action="store_true", help="per-kernel-class study instead")
     args = ap.parse_args()
     ext = [int(x) for x in args.extents.split(",")]
+    if args.classes:
+        print(json.dumps(class_study(args.spec, ext, args.dtype, reps=args.reps)))
+        return
     r = study(args.spec, ext, args.dtype, reps=args.reps, cap=args.cap)
     summary = {k: v for k, v in r.items() if k != "algorithms"}
     print(json.dumps(summary))
