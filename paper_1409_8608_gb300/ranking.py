@@ -3,6 +3,7 @@ contraction (the experiments of Sections 3-4, on the device).
 
     python -m paper_1409_8608_gb300.ranking --spec abc=iaj,jbic \\
         --extents 256,256,256,16,16 --dtype f64 [--json out.json] [--classes]
+        [--execute name,name,...]
 
 Reports per algorithm the predicted and the measured seconds, and over all
 of them Spearman's rho and Kendall's tau of the two rankings, the top-1
@@ -158,6 +159,24 @@ def class_study(spec, extents, dtype="f32", seed=0, reps=5, top=3, hbm_gbs=None)
             "compulsory_gb": nbytes / 1e9, "classes": out}
 
 
+def execute_named(spec, extents, dtype, names, runs=2):
+    """Runs the named algorithms `runs` times each on uniform inputs."""
+    import torch
+    tdt = {"f64": torch.float64, "f32": torch.float32}[dtype]
+    A, B, _ = synth.uniform_operands(spec, extents, seed=0)
+    dA, dB = torch.from_numpy(A).to(tdt).cuda(), torch.from_numpy(B).to(tdt).cuda()
+    dC = torch.zeros(synth.dense_sizes(spec, extents)[0], dtype=tdt, device="cuda")
+    plan = tc.Plan(spec, extents, dtype=dtype)
+    ids = {a["name"]: a["id"] for a in plan.algorithms()}
+    for n in names:
+        plan.select(ids[n])
+        for _ in range(runs):
+            plan.execute(dA, dB, dC)
+        torch.cuda.synchronize()
+    plan.device_status()
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--spec", default="abc=iaj,jbic")
@@ -167,8 +186,13 @@ def main():
     ap.add_argument("--cap", type=float, default=2.0)
     ap.add_argument("--json", default=None)
     ap.add_argument("--classes", action="store_true", help="per-kernel-class study instead")
+    ap.add_argument("--execute", default=None,
+                    help="comma-separated algorithm names: run each twice, nothing else (profiler captures)")
     args = ap.parse_args()
     ext = [int(x) for x in args.extents.split(",")]
+    if args.execute:
+        execute_named(args.spec, ext, args.dtype, args.execute.split(","))
+        return
     if args.classes:
         print(json.dumps(class_study(args.spec, ext, args.dtype, reps=args.reps)))
         return
