@@ -516,20 +516,21 @@ def run_chain(tc, dev, reps=3):
     X, Y, Z = (torch.rand(size(o), dtype=torch.float64, device=dev, generator=g) * 2 - 1 for o in ops)
     D = torch.empty(size(d), dtype=torch.float64, device=dev)
     ch = tc.Chain(spec, ext, "f64")
+    st = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    ch.predict(all_algorithms=False)
+    ch.predict(all_algorithms=False, stream=st)
     t_pred = time.perf_counter() - t0
     rows = []
     for i, v in enumerate(ch.variants()):
         ch.select(i)
-        ch.execute(X, Y, Z, D)
+        ch.execute(X, Y, Z, D, stream=st)
         torch.cuda.synchronize()
         ts = []
         for _ in range(reps):
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a0.record()
-            ch.execute(X, Y, Z, D)
-            a1.record()
+            a0.record(st)
+            ch.execute(X, Y, Z, D, stream=st)
+            a1.record(st)
             a1.synchronize()
             ts.append(a0.elapsed_time(a1) * 1e-3)
         rows.append({"first": list(v["first"]), "sliced": v["sliced"], "slices": v["slices"],
