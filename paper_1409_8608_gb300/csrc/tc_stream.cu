@@ -9,20 +9,28 @@
 // 16, K = 16 or 32), so that no row of the MMA is padding except past N.
 // The persistent kernel (one CTA per SM) is warp-specialised:
 //
-//   producer warp 0      one 1-D bulk copy of the tile's B run (128 x K
+//   producer warp 0      fetches the problem records of 32 tiles at a time
+//                        (one per lane, so their latency is paid once per 32
+//                        tiles) into a ring of tile records the other roles
+//                        read from shared memory; then one 1-D bulk copy of the tile's B run (128 x K
 //                        contiguous FP32) and one of the problem's A (M x K)
-//                        into a ring of raw slots, counted in bytes on an
-//                        mbarrier;
+//                        into a byte ring that packs tiles by their actual
+//                        size (about nine in flight: the copies take a few
+//                        microseconds to land), counted in bytes on an
+//                        mbarrier per tile;
 //   converter warps 2-5  split each FP32 value into three BF16 slices
 //                        x = h0 + h1 + h2 and store both operands in the
 //                        no-swizzle K-major core-matrix layout (zeros past K);
 //   MMA warp 1           one thread issues the six slice products
 //                        (0,0) (0,1) (1,0) (0,2) (1,1) (2,0) per 16-K step
 //                        into one of four tensor-memory accumulators;
-//   epilogue warps 6-9   tcgen05.ld 32 columns at a time, transpose them
-//                        through a per-warp buffer and store each tile row's
-//                        contiguous run of C (m fastest) with whole-warp
-//                        coalesced stores, alpha and beta applied.
+//   epilogue warps 6-13  two groups of four taking alternate tiles (the
+//                        epilogue is the slowest role: one group left the MMA
+//                        waiting on accumulators): tcgen05.ld 32 columns at a
+//                        time, transpose them through a per-warp buffer and
+//                        store each tile row's contiguous run of C (m
+//                        fastest) with whole-warp coalesced stores, alpha and
+//                        beta applied.
 //
 // Every mbarrier wait is bounded; on expiry the kernel records
 // TC_ERROR_TIMEOUT in the status word, stops, waits for its own copies and
@@ -46,19 +54,22 @@ using namespace dev;
 constexpr int kRows = 128;                      // tile columns n = MMA rows = TMEM lanes
 constexpr int kMaxM = 128;                      // problem rows m (MMA N <= 128)
 constexpr int kMaxK = 32;
-constexpr int kRawSlots = 3;                    // raw FP32 ring
+constexpr int kRawSlots = 12;                   // tiles in the raw ring at most
+constexpr int kRawBytes = 94 * 1024;            // raw FP32 ring: each tile's B run and A, packed
+constexpr int kRecs = 32;                       // tile records in shared memory (the producer's lead)
 constexpr int kConvSlots = 2;                   // converted operand ring
 constexpr int kAccs = 4;                        // TMEM accumulators of kMaxM columns
-constexpr int kRawB = kRows * kMaxK * 4;        // 16 KB: the tile's B run
-constexpr int kRawA = kMaxM * kMaxK * 4;        // 16 KB: the problem's A
-constexpr int kRawSlot = kRawB + kRawA;
+constexpr int kMaxRawTile = kRows * kMaxK * 4 + kMaxM * kMaxK * 4;  // B run + A, at most
 constexpr int kOpA = 3 * kRows * kMaxK * 2;     // three slices of the 128 x Kpad B tile
 constexpr int kOpB = 3 * kMaxM * kMaxK * 2;     // three slices of the Mpad x Kpad A
 constexpr int kConvSlot = kOpA + kOpB;
 constexpr int kStgFloats = 32 * 33;             // per epilogue warp: 32 x 32 transpose, pitch 33
-constexpr int kWProducer = 0, kWMma = 1, kWConv = 2, kConvWarps = 4, kWEpi = 6, kEpiWarps = 4;
+constexpr int kWProducer = 0, kWMma = 1, kWConv = 2, kConvWarps = 4, kWEpi = 6;
+constexpr int kEpiGroups = 2;                   // epilogue groups of four warps, taking alternate tiles
+constexpr int kEpiWarps = 4 * kEpiGroups;
 constexpr int kStreamThreads = (kWEpi + kEpiWarps) * 32;
-constexpr int kStreamSmem = kRawSlots * kRawSlot + kConvSlots * kConvSlot + kEpiWarps * kStgFloats * 4 + 128;
+constexpr int kStreamSmem = kRawBytes + kConvSlots * kConvSlot + kEpiWarps * kStgFloats * 4 + 128;
+static_assert(kMaxRawTile <= kRawBytes, "a tile fits the raw ring");
 static_assert(kStreamSmem <= 232448, "shared memory budget");
 
 struct StreamArgs {
@@ -108,9 +119,12 @@ __device__ __forceinline__ void split8_store(const float (&x)[8], char *dst, int
 __global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     char *raw = (char *)smem;
-    char *conv = raw + kRawSlots * kRawSlot;
+    char *conv = raw + kRawBytes;
     float *stg_all = (float *)(conv + kConvSlots * kConvSlot);
     __shared__ __align__(8) uint64_t raw_full[kRawSlots], raw_empty[kRawSlots];
+    __shared__ int raw_off[kRawSlots];  // byte offset of each raw tile in the ring
+    __shared__ STile recs[kRecs];       // tile i's record at i % kRecs
+    __shared__ __align__(8) uint64_t rec_full[kRecs], rec_empty[kRecs];
     __shared__ __align__(8) uint64_t conv_full[kConvSlots], conv_empty[kConvSlots];
     __shared__ __align__(8) uint64_t acc_full[kAccs], acc_empty[kAccs], drain;
     __shared__ uint32_t tmem_slot;
@@ -119,7 +133,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamA
     if (threadIdx.x == 0) {
         for (int i = 0; i < kRawSlots; ++i) mbar_init(&raw_full[i], 1), mbar_init(&raw_empty[i], kConvWarps);
         for (int i = 0; i < kConvSlots; ++i) mbar_init(&conv_full[i], kConvWarps), mbar_init(&conv_empty[i], 1);
-        for (int i = 0; i < kAccs; ++i) mbar_init(&acc_full[i], 1), mbar_init(&acc_empty[i], kEpiWarps);
+        for (int i = 0; i < kAccs; ++i) mbar_init(&acc_full[i], 1), mbar_init(&acc_empty[i], 4);
+        for (int i = 0; i < kRecs; ++i) mbar_init(&rec_full[i], 1), mbar_init(&rec_empty[i], 4);
         mbar_init(&drain, 1);
         abort_flag = 0;
         fence_mbar_init();
@@ -137,35 +152,70 @@ __global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamA
 
     if (warp == kWProducer) {
         // ------------------------------------------------------------ producer
-        if (lane == 0) {
-            int64_t i = 0;
-            STile nxt = first < a.t_end ? stream_tile(a, first) : STile{};
-            for (int64_t t = first; t < a.t_end; t += step, ++i) {
-                const STile s = nxt;
-                if (t + step < a.t_end) nxt = stream_tile(a, t + step);  // in flight during the wait
-                const int r = (int)(i % kRawSlots);
-                if (abort_flag || (i >= kRawSlots && !mbar_wait(&raw_empty[r], (uint32_t)(((i / kRawSlots) - 1) & 1)))) {
-                    give_up();
-                    break;
+        // byte ring: tiles take [pos, pos + size) in order, none wrapping the
+        // end; released in order by the converters (lane 0 keeps the books)
+        int64_t head = 0, tail = 0, oldest = 0, i = 0;
+        int64_t ends[kRawSlots];  // ring end of each tile in flight
+        bool stop = false;
+        for (int64_t base = 0; !stop; base += 32) {
+            const int64_t tl = first + (base + lane) * step;  // lane l: tile base + l
+            const STile mine = tl < a.t_end ? stream_tile(a, tl) : STile{};
+            const int64_t left = (a.t_end - first + step - 1) / step - base;  // tiles of this CTA left
+            if (left <= 0) break;
+            const int nb = left < 32 ? (int)left : 32;
+            for (int jj = 0; jj < nb; ++jj, ++i) {
+                STile s;
+                s.A = (const float *)__shfl_sync(0xffffffffu, (unsigned long long)mine.A, jj);
+                s.B = (const float *)__shfl_sync(0xffffffffu, (unsigned long long)mine.B, jj);
+                s.C = (float *)__shfl_sync(0xffffffffu, (unsigned long long)mine.C, jj);
+                s.n0 = __shfl_sync(0xffffffffu, mine.n0, jj);
+                s.M = __shfl_sync(0xffffffffu, mine.M, jj);
+                s.K = __shfl_sync(0xffffffffu, mine.K, jj);
+                s.nvalid = __shfl_sync(0xffffffffu, mine.nvalid, jj);
+                if (lane == 0) {
+                    const uint32_t bytesB = (uint32_t)(s.nvalid * s.K * 4), bytesA = (uint32_t)(s.M * s.K * 4);
+                    const int64_t offA = (bytesB + 127) & ~127, size = offA + ((bytesA + 127) & ~127);
+                    int64_t pos = head % kRawBytes;
+                    if (pos + size > kRawBytes) {  // skip the ring's end
+                        head += kRawBytes - pos;
+                        pos = 0;
+                    }
+                    while (!stop && (head + size - tail > kRawBytes || i - oldest >= kRawSlots)) {
+                        const int o = (int)(oldest % kRawSlots);
+                        if (abort_flag || !mbar_wait(&raw_empty[o], (uint32_t)((oldest / kRawSlots) & 1))) stop = true;
+                        else tail = ends[o], ++oldest;
+                    }
+                    // the record slot: its previous tile's epilogue has read it
+                    const int q = (int)(i % kRecs);
+                    if (!stop && i >= kRecs && !mbar_wait(&rec_empty[q], (uint32_t)(((i / kRecs) - 1) & 1)))
+                        stop = true;
+                    if (stop || abort_flag) {
+                        stop = true;
+                        give_up();
+                    } else {
+                        recs[q] = s;
+                        mbar_arrive(&rec_full[q]);  // releases recs[q] to the epilogue
+                        const int r = (int)(i % kRawSlots);
+                        raw_off[r] = (int)pos;
+                        ends[r] = head + size;
+                        head += size;
+                        mbar_arrive_expect_tx(&raw_full[r], bytesB + bytesA);  // releases raw_off[r], recs[q]
+                        bulk_load(raw + pos, s.B + s.n0 * s.K, bytesB, &raw_full[r]);
+                        bulk_load(raw + pos + offA, s.A, bytesA, &raw_full[r]);
+                    }
                 }
-                const uint32_t bytesB = (uint32_t)(s.nvalid * s.K * 4), bytesA = (uint32_t)(s.M * s.K * 4);
-                char *slot = raw + r * kRawSlot;
-                mbar_arrive_expect_tx(&raw_full[r], bytesB + bytesA);
-                bulk_load(slot, s.B + s.n0 * s.K, bytesB, &raw_full[r]);
-                bulk_load(slot + kRawB, s.A, bytesA, &raw_full[r]);
+                stop = __shfl_sync(0xffffffffu, stop, 0);
+                if (stop) break;
             }
-            // nothing may still be copying into shared memory at exit
-            for (int64_t j = i > kRawSlots ? i - kRawSlots : 0; j < i; ++j)
-                mbar_wait(&raw_full[j % kRawSlots], (uint32_t)((j / kRawSlots) & 1));
         }
+        // nothing may still be copying into shared memory at exit
+        if (lane == 0)
+            for (int64_t jj = oldest; jj < i; ++jj) mbar_wait(&raw_full[jj % kRawSlots], (uint32_t)((jj / kRawSlots) & 1));
     } else if (warp >= kWConv && warp < kWConv + kConvWarps) {
         // ----------------------------------------------------------- converters
         const int ct = threadIdx.x - kWConv * 32;  // 0..127: tile row n, and row m of A
         int64_t i = 0;
-        STile nxt = first < a.t_end ? stream_tile(a, first) : STile{};
         for (int64_t t = first; t < a.t_end; t += step, ++i) {
-            const STile s = nxt;
-            if (t + step < a.t_end) nxt = stream_tile(a, t + step);
             const int r = (int)(i % kRawSlots), c = (int)(i % kConvSlots);
             bool ok = !abort_flag && mbar_wait(&raw_full[r], (uint32_t)((i / kRawSlots) & 1));
             if (ok && i >= kConvSlots) ok = mbar_wait(&conv_empty[c], (uint32_t)(((i / kConvSlots) - 1) & 1));
@@ -173,9 +223,10 @@ __global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamA
                 if (lane == 0) give_up();
                 break;
             }
+            const STile s = recs[i % kRecs];  // written before raw_full[r] was armed
             const int K = s.K, M = s.M, Kp = K <= 16 ? 16 : 32, Mp = (M + 15) & ~15;
-            const float *rawB = (const float *)(raw + r * kRawSlot);
-            const float *rawA = (const float *)(raw + r * kRawSlot + kRawB);
+            const float *rawB = (const float *)(raw + raw_off[r]);
+            const float *rawA = (const float *)(raw + raw_off[r] + ((s.nvalid * K * 4 + 127) & ~127));
             char *opA = conv + c * kConvSlot, *opB = opA + kOpA;
             // B tile -> the MMA's A operand: row n = ct (rows past nvalid keep
             // whatever they held: they only reach accumulator rows never stored)
@@ -228,10 +279,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamA
             constexpr uint32_t kPa = 0x210100u, kPb = 0x012010u;
             bool issued = false;
             int64_t i = 0;
-            STile nxt = first < a.t_end ? stream_tile(a, first) : STile{};
             for (int64_t t = first; t < a.t_end; t += step, ++i) {
-                const STile s = nxt;
-                if (t + step < a.t_end) nxt = stream_tile(a, t + step);
                 const int c = (int)(i % kConvSlots), b = (int)(i % kAccs);
                 bool ok = !abort_flag && mbar_wait(&conv_full[c], (uint32_t)((i / kConvSlots) & 1));
                 if (ok && i >= kAccs) ok = mbar_wait(&acc_empty[b], (uint32_t)(((i / kAccs) - 1) & 1));
@@ -240,6 +288,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamA
                     break;
                 }
                 tc_fence_after();
+                const STile s = recs[i % kRecs];  // visible through the converters' arrival
                 const int Kp = s.K <= 16 ? 16 : 32, Mp = (s.M + 15) & ~15;
                 const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Mp >> 3) << 17) |
                                        ((uint32_t)(kRows >> 4) << 24);
@@ -267,14 +316,20 @@ __global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamA
     } else if (warp >= kWEpi) {
         // ------------------------------------------------------------- epilogue
         const int qd = warp % 4;  // this warp's TMEM lane quadrant = tile rows 32 qd ...
+        const int grp = (warp - kWEpi) / 4;  // tiles grp, grp + kEpiGroups, ...
         float *stg = stg_all + (warp - kWEpi) * kStgFloats;
-        int64_t i = 0;
-        STile nxt = first < a.t_end ? stream_tile(a, first) : STile{};
-        for (int64_t t = first; t < a.t_end; t += step, ++i) {
-            const STile s = nxt;
-            if (t + step < a.t_end) nxt = stream_tile(a, t + step);
-            const int b = (int)(i % kAccs);
-            bool ok = !abort_flag && mbar_wait(&acc_full[b], (uint32_t)((i / kAccs) & 1));
+        int64_t i = grp;
+        const int64_t t1 = first + grp * step, gstep = kEpiGroups * step;
+        for (int64_t t = t1; t < a.t_end; t += gstep, i += kEpiGroups) {
+            const int b = (int)(i % kAccs), q = (int)(i % kRecs);
+            bool ok = !abort_flag && mbar_wait(&rec_full[q], (uint32_t)((i / kRecs) & 1));
+            STile s{};
+            if (ok) s = recs[q];
+            ok = ok && mbar_wait(&acc_full[b], (uint32_t)((i / kAccs) & 1));
+            // the tile's MMAs are done, so the converters and the MMA warp
+            // have read the record too: its slot may take tile i + kRecs
+            __syncwarp();
+            if (lane == 0 && ok) mbar_arrive(&rec_empty[q]);
             if (!__all_sync(0xffffffffu, ok)) {
                 if (lane == 0) give_up();
                 break;
@@ -302,11 +357,9 @@ __global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamA
                 if (lane < mv) {
                     float *Crow = s.C + (s.n0 + nbase) * M + c0 + lane;
                     if (a.init == 1) {
-                        float o[32];
 #pragma unroll
-                        for (int rr = 0; rr < 32; ++rr) o[rr] = rr < rows ? Crow[(int64_t)rr * M] : 0.0f;
-#pragma unroll
-                        for (int rr = 0; rr < 32; ++rr) x[rr] = fmaf(a.beta, o[rr], x[rr]);
+                        for (int rr = 0; rr < 32; ++rr)
+                            if (rr < rows) x[rr] = fmaf(a.beta, Crow[(int64_t)rr * M], x[rr]);
                     }
 #pragma unroll
                     for (int rr = 0; rr < 32; ++rr)
