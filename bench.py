@@ -60,8 +60,8 @@ def set_free_extent(n):
 SMS = 152
 SM_MAX_MHZ = 2070.0
 TORCH_IN = {"f64": "float64", "f32": "float32", "tf32": "float32", "bf16x3": "float32", "tf32x3": "float32",
-            "bf16": "bfloat16", "f16": "float16"}
-TENSOR_FORMS = ("tf32", "bf16", "f16", "bf16x3", "tf32x3")
+            "bf16": "bfloat16", "f16": "float16", "e4m3": "float32"}
+TENSOR_FORMS = ("tf32", "bf16", "f16", "bf16x3", "tf32x3", "e4m3")
 
 
 def flops_of(extents):
@@ -555,6 +555,7 @@ PRECISION_FORMS = (
     ("bf16x3 x9", "bf16x3", 9, None), ("bf16x3 x6 uncompensated", "bf16x3", 6, 0),
     ("tf32x3", "tf32x3", None, None),
     ("tf32", "tf32", None, None), ("bf16", "bf16", None, None), ("f16", "f16", None, None),
+    ("fp8 e4m3 (power-of-two input scales)", "e4m3", None, None),
     ("f32 (SIMT)", "f32", None, None), ("f64 (plain)", "f64", None, None),
 )
 
@@ -606,7 +607,9 @@ def run_precision(tc, dev, stream, points=3000, reps=5):
                     if dtype in TENSOR_FORMS:
                         # tensor work: slice products x F (3 TF32 products for 3xTF32)
                         work = flops * (prods or (3 if dtype == "tf32x3" else 1))
-                        pk = peaks["bf16_tflops"] * (0.5 if dtype in ("tf32", "tf32x3") else 1.0)
+                        # nominal ratios to the measured BF16 peak: TF32 0.5, FP8 2
+                        pk = peaks["bf16_tflops"] * (0.5 if dtype in ("tf32", "tf32x3") else
+                                                     (2.0 if dtype == "e4m3" else 1.0))
                         row["tensor_frac"] = work / t / 1e12 / pk
                 else:
                     run1()

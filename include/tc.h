@@ -35,6 +35,11 @@
  *                          words, hi = tf32(x), lo = tf32(x - hi); the
  *                          products hi.hi, hi.lo and lo.hi on the tensor
  *                          cores)
+ *              TC_E4M3     A, B, C float (each input divided by a power
+ *                          of two that brings its largest magnitude to at
+ *                          most 448, rounded to FP8 E4M3, products on the
+ *                          tensor cores (kind::f8f6f4), FP32 accumulation;
+ *                          the fused GETT only, global-load path)
  *              TC_BF16     A, B __nv_bfloat16; C float
  *              TC_F16      A, B __half; C float
  *   alpha,   host pointers to one double (TC_F64) or one float (all other
@@ -81,7 +86,8 @@ typedef enum {
     TC_BF16 = 3,
     TC_F16 = 4,
     TC_BF16X3 = 5,
-    TC_TF32X3 = 6
+    TC_TF32X3 = 6,
+    TC_E4M3 = 7
 } tc_dtype;
 
 /* Kernels of Section 2 (BLAS-1: dot, axpy; BLAS-2: gemv, ger; BLAS-3:
@@ -588,7 +594,8 @@ tc_status tc_server_create(tc_server *out, int64_t budget_bytes, int32_t slots,
  * lets the copies run asynchronously.  C: host output or NULL to keep the
  * result only on the device until the request completes.  The caller keeps
  * the buffers alive until the request is done.  A request larger than the
- * whole budget is refused with TC_ERROR_ADMISSION. */
+ * whole budget is refused with TC_ERROR_ADMISSION; TC_E4M3 with
+ * TC_ERROR_UNSUPPORTED_DTYPE. */
 tc_status tc_server_submit(tc_server server, const char *spec, const int64_t *extents,
                            tc_dtype dtype, const void *A, const void *B, void *C,
                            int64_t *request_id);

@@ -1034,6 +1034,8 @@ tc_status exec_nest(Plan &p, const Algorithm &alg, const void *alpha, const void
         return fail(TC_ERROR_UNSUPPORTED_DTYPE,
                     "at tensor-core dtypes only the gemm loop nests (on the tensor cores) and the GETT run; "
                     "dot / axpy / gemv / ger nests run in FP64 or FP32");
+    if (p.dtype == TC_E4M3)
+        return fail(TC_ERROR_UNSUPPORTED_DTYPE, "TC_E4M3 runs the fused GETT (algorithm 0) only");
     tc_status s = ensure_device_resources(p, nest_workspace_bytes(p, alg));
     if (s != TC_SUCCESS) return s;
     p.last_stream = stream;

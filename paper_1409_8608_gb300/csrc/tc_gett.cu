@@ -42,6 +42,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,12 +59,14 @@ namespace {
 
 using namespace dev;
 
-enum GettKind { GK_BF16X3 = 0, GK_BF16 = 1, GK_F16 = 2, GK_TF32 = 3, GK_TF32X3 = 4 };
+enum GettKind { GK_BF16X3 = 0, GK_BF16 = 1, GK_F16 = 2, GK_TF32 = 3, GK_TF32X3 = 4, GK_E4M3 = 5 };
 
 // MMA on TF32 words (kind::tf32, 4-byte operand elements)
 __host__ __device__ constexpr bool tf32_kind(int k) { return k == GK_TF32 || k == GK_TF32X3; }
 // FP32 inputs, converted (or split) by the converter warps
-__host__ __device__ constexpr bool float_input(int k) { return k == GK_BF16X3 || k == GK_TF32 || k == GK_TF32X3; }
+__host__ __device__ constexpr bool float_input(int k) {
+    return k == GK_BF16X3 || k == GK_TF32 || k == GK_TF32X3 || k == GK_E4M3;
+}
 
 constexpr int kBM = 128;                  // accumulator rows = TMEM lanes
 constexpr int kBK = 32;                   // K elements per stage, global-load path
@@ -121,6 +124,7 @@ struct GettDesc {
     double tile_frac;    // micro-benchmark: run this fraction of the tiles
     int chunk_stages;    // compensated form: K stages per TMEM chunk
     int split;           // split-BF16: (0,0) products in their own accumulator
+    const float *qscale; // E4M3: the scales of A and B (powers of two, device memory)
     // batched form: per-problem descriptors (num_tiles, status, nprod,
     // alpha, beta and init are the batch's, in this descriptor), the
     // problem of each tile, and each problem's first tile
@@ -260,6 +264,13 @@ __device__ __forceinline__ void mma_issue(uint32_t dtmem, uint64_t adesc, uint64
             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
             : "memory");
+    } else if constexpr (KIND == GK_E4M3) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.u32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
     } else {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -341,12 +352,14 @@ __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
 // ------------------------------------------------------------------ layout
 template <int KIND, int BK>
 struct KindTraits {
-    static constexpr int kElemBytes = tf32_kind(KIND) ? 4 : 2;  // smem operand element
+    static constexpr int kElemBytes = tf32_kind(KIND) ? 4 : (KIND == GK_E4M3 ? 1 : 2);  // smem operand element
     static constexpr int kSlices = KIND == GK_BF16X3 ? 3 : (KIND == GK_TF32X3 ? 2 : 1);
     static constexpr int kChunk = 16 / kElemBytes;              // K elements per 16-byte row
     static constexpr int kKc = BK / kChunk;                     // core matrices along K per stage
     static constexpr int kKsteps = BK * kElemBytes / 32;        // MMA instructions along K per stage
-    static constexpr uint32_t kFmt = tf32_kind(KIND) ? 2u : (KIND == GK_F16 ? 0u : 1u);
+    // instruction-descriptor operand format: kind::tf32 TF32 = 2; kind::f16
+    // F16 = 0, BF16 = 1; kind::f8f6f4 E4M3 = 0
+    static constexpr uint32_t kFmt = tf32_kind(KIND) ? 2u : ((KIND == GK_F16 || KIND == GK_E4M3) ? 0u : 1u);
     using In = typename std::conditional<KIND == GK_BF16, __nv_bfloat16,
                                          typename std::conditional<KIND == GK_F16, __half, float>::type>::type;
     static constexpr int kInBytes = sizeof(In);
@@ -412,8 +425,9 @@ __device__ __forceinline__ void decode(int64_t x, int n, const int64_t *ext, con
 
 // Converts N (4 or 8) FP32 values into the 16-bit slices or TF32 words
 // and stores them at dst (one slice after another, slice_stride apart).
+// qs: E4M3 only, the operand's inverse scale (a power of two).
 template <int KIND, int N>
-__device__ __forceinline__ void store_converted(const float (&x)[N], char *dst, int slice_stride) {
+__device__ __forceinline__ void store_converted(const float (&x)[N], char *dst, int slice_stride, float qs = 1.0f) {
     if constexpr (KIND == GK_BF16X3) {
         uint32_t w0[N / 2], w1[N / 2], w2[N / 2];
 #pragma unroll
@@ -436,6 +450,18 @@ __device__ __forceinline__ void store_converted(const float (&x)[N], char *dst, 
         }
         *(uint4 *)(dst) = make_uint4(h[0], h[1], h[2], h[3]);
         *(uint4 *)(dst + slice_stride) = make_uint4(l[0], l[1], l[2], l[3]);
+    } else if constexpr (KIND == GK_E4M3) {  // N == 4 or 16: x * qs rounded to E4M3, saturating
+        (void)slice_stride;
+        uint32_t w[N / 4];
+#pragma unroll
+        for (int e = 0; e < N; e += 4) {
+            const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(x[e] * qs, x[e + 1] * qs), __NV_SATFINITE, __NV_E4M3);
+            const uint32_t hi =
+                __nv_cvt_float2_to_fp8x2(make_float2(x[e + 2] * qs, x[e + 3] * qs), __NV_SATFINITE, __NV_E4M3);
+            w[e / 4] = lo | (hi << 16);
+        }
+        if constexpr (N == 16) *(uint4 *)(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+        else *(uint32_t *)(dst) = w[0];
     } else {  // TF32: N == 4
         *(uint4 *)(dst) = make_uint4(f32_to_tf32(x[0]), f32_to_tf32(x[1]), f32_to_tf32(x[2]),
                                      f32_to_tf32(x[3]));
@@ -450,7 +476,7 @@ __device__ __forceinline__ void store_converted(const float (&x)[N], char *dst, 
 template <int KIND, int BK, int ROWS, int MAP, int NT = kProducerThreads>
 __device__ __forceinline__ void produce_operand(const typename KindTraits<KIND, BK>::In *__restrict__ src,
                                                 const int64_t *rowoff, const int64_t *koff, char *tile,
-                                                int slice_stride, int pt) {
+                                                int slice_stride, int pt, float qs = 1.0f) {
     using T = KindTraits<KIND, BK>;
     constexpr int KC = T::kKc, CH = T::kChunk;
     constexpr bool kFloatIn = float_input(KIND);
@@ -475,7 +501,7 @@ __device__ __forceinline__ void produce_operand(const typename KindTraits<KIND, 
             if constexpr (kFloatIn) {
                 float x[4] = {__uint_as_float(v[i].x), __uint_as_float(v[i].y), __uint_as_float(v[i].z),
                               __uint_as_float(v[i].w)};
-                store_converted<KIND, 4>(x, dst, slice_stride);
+                store_converted<KIND, 4>(x, dst, slice_stride, qs);
             } else {
                 *(uint4 *)(dst) = v[i];
             }
@@ -505,7 +531,7 @@ __device__ __forceinline__ void produce_operand(const typename KindTraits<KIND, 
             const int kc = MAP == 1 ? c % KC : c / ROWS;
             char *dst = tile + (kc * (ROWS / 8) + row / 8) * 128 + (row % 8) * 16;
             if constexpr (kFloatIn) {
-                store_converted<KIND, CH>(x[i], dst, slice_stride);
+                store_converted<KIND, CH>(x[i], dst, slice_stride, qs);
             } else {
                 uint32_t w[CH / 2];
 #pragma unroll
@@ -519,10 +545,10 @@ __device__ __forceinline__ void produce_operand(const typename KindTraits<KIND, 
 template <int KIND, int BK, int ROWS, int NT = kProducerThreads>
 __device__ __forceinline__ void produce_any(const typename KindTraits<KIND, BK>::In *__restrict__ src,
                                             const int64_t *rowoff, const int64_t *koff, char *tile,
-                                            int slice_stride, int map, int pt) {
-    if (map == 2) produce_operand<KIND, BK, ROWS, 2, NT>(src, rowoff, koff, tile, slice_stride, pt);
-    else if (map == 1) produce_operand<KIND, BK, ROWS, 1, NT>(src, rowoff, koff, tile, slice_stride, pt);
-    else produce_operand<KIND, BK, ROWS, 0, NT>(src, rowoff, koff, tile, slice_stride, pt);
+                                            int slice_stride, int map, int pt, float qs = 1.0f) {
+    if (map == 2) produce_operand<KIND, BK, ROWS, 2, NT>(src, rowoff, koff, tile, slice_stride, pt, qs);
+    else if (map == 1) produce_operand<KIND, BK, ROWS, 1, NT>(src, rowoff, koff, tile, slice_stride, pt, qs);
+    else produce_operand<KIND, BK, ROWS, 0, NT>(src, rowoff, koff, tile, slice_stride, pt, qs);
 }
 
 // TMA path: converts one operand's staged box (ROWS rows x BK K positions,
@@ -783,6 +809,12 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     if (warp >= kEpiWarps && warp < kMmaWarp) {
         // ---------------------------------------------------------- converters
         const int pt = threadIdx.x - kEpiThreads;
+        // E4M3: each input divided by its scale (a power of two, exact)
+        float qa = 1.0f, qb = 1.0f;
+        if constexpr (KIND == GK_E4M3) {
+            qa = 1.0f / d.qscale[0];
+            qb = 1.0f / d.qscale[1];
+        }
         // with a pre-converted input the kernel is launched as a programmatic
         // dependent of the pre-pass: its other roles start at once (the TMA
         // warp streams the other input), the converters wait here until the
@@ -1032,14 +1064,14 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                         convert_staged<KIND, BK, kBM>(stg + ss * (boxA + boxB), d.srow[0], d.sk[0] + half * BK,
                                                       d.sk_vec4[0], stage, SP::kATile, pt);
                     else
-                        produce_any<KIND, BK, kBM>(Ap, rA, kA + s * BK, stage, SP::kATile, P.a_map, pt);
+                        produce_any<KIND, BK, kBM>(Ap, rA, kA + s * BK, stage, SP::kATile, P.a_map, pt, qa);
                 }
                 if (pk != 2) {
                     if (TMA && d.tma[1])
                         convert_staged<KIND, BK, BN>(stg + ss * (boxA + boxB) + boxA, d.srow[1],
                                                      d.sk[1] + half * BK, d.sk_vec4[1], bstage, SP::kBTile, pt);
                     else
-                        produce_any<KIND, BK, BN>(Bp, rB, kB + s * BK, bstage, SP::kBTile, P.b_map, pt);
+                        produce_any<KIND, BK, BN>(Bp, rB, kB + s * BK, bstage, SP::kBTile, P.b_map, pt, qb);
                 }
                 if (pk) cp_async_wait_all();
                 // each lane publishes its stores to the async proxy; the warp's
@@ -1203,6 +1235,9 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
     } else {
         // ---------------------------------------------------------- epilogue
         const int et = threadIdx.x;  // 0..127 = accumulator row = TMEM lane
+        // E4M3: the products carry both inputs' scales
+        float alpha_e = d.alpha;
+        if constexpr (KIND == GK_E4M3) alpha_e = d.alpha * d.qscale[0] * d.qscale[1];
         int it = 0;
         int64_t u = 0;
         for (int64_t tile = d.tile_begin + slot0; tile < d.num_tiles; tile += nslots, ++it) {
@@ -1289,14 +1324,14 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                         for (int c0 = 0; c0 < BN; c0 += 32) {
                             uint32_t r[32];
                             tmem_ld32_sum(acc + (uint32_t)c0, acc + (uint32_t)(BN + c0), r);
-                            store_cols<32>(r, C, om, c0, lin, on0, nval, cn, d.alpha, d.beta, d.init);
+                            store_cols<32>(r, C, om, c0, lin, on0, nval, cn, alpha_e, d.beta, d.init);
                         }
                     } else {
 #pragma unroll 1
                         for (int c0 = 0; c0 < BN; c0 += 64) {
                             uint32_t r[64];
                             tmem_ld64(acc + (uint32_t)c0, r);
-                            store_cols<64>(r, C, om, c0, lin, on0, nval, cn, d.alpha, d.beta, d.init);
+                            store_cols<64>(r, C, om, c0, lin, on0, nval, cn, alpha_e, d.beta, d.init);
                         }
                     }
                 } else {
@@ -1343,7 +1378,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                                 }
                             }
                         }
-                        store_cols<32>(r, C, om, c0, lin, on0, nval, cn, d.alpha, d.beta, d.init);
+                        store_cols<32>(r, C, om, c0, lin, on0, nval, cn, alpha_e, d.beta, d.init);
                     }
                 }
                 tc_fence_before();
@@ -1430,6 +1465,45 @@ __global__ void __launch_bounds__(128) pack_kernel(const GettDesc d, int op, int
     }
 }
 
+// E4M3 scales: the largest magnitude of each input over its modes, then the
+// power of two s with max / s <= 448 (E4M3's largest finite value), so that
+// dividing by s is exact and no input saturates.
+struct AbsmaxDesc {
+    int n;            // modes (0: the operand is dense, read [0, total) linearly)
+    int64_t ext[kMaxModes], stride[kMaxModes];
+    int64_t total;
+    const float *src;
+    unsigned *out;    // the maximum as float bits (non-negative: ordered as integers)
+};
+
+__global__ void __launch_bounds__(256) absmax_kernel(const AbsmaxDesc a) {
+    float m = 0.0f;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.total; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t off = e;
+        if (a.n) {
+            int64_t r = e;
+            off = 0;
+            for (int k = 0; k < a.n; ++k) {
+                const int64_t x = r % a.ext[k];
+                r /= a.ext[k];
+                off += x * a.stride[k];
+            }
+        }
+        m = fmaxf(m, fabsf(a.src[off]));  // a NaN input is passed over
+    }
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(a.out, __float_as_uint(m));
+}
+
+__global__ void e4m3_scale_kernel(const unsigned *mx, float *scale) {
+    if (threadIdx.x < 2) {
+        const float m = __uint_as_float(mx[threadIdx.x]);
+        float sc = 1.0f;
+        if (m > 0.0f && isfinite(m)) sc = ldexpf(1.0f, (int)ceilf(log2f(m / 448.0f)));
+        scale[threadIdx.x] = sc;
+    }
+}
+
 // ------------------------------------------------------------------ host side
 int g_gett_sms = 0;
 
@@ -1513,7 +1587,10 @@ tc_status launch_kind(GettDesc &d, int bn, bool tma, bool comp, bool pair, const
             return launch_gett<KIND, 128, 4, kBK, 0, true>(d, ta, tb, st);
         }
     }
-    if constexpr (KIND == GK_TF32X3) {  // two 4-byte slices per operand: 192 KB of rings
+    if constexpr (KIND == GK_E4M3) {  // global-load path only: 32-K stages of 1-byte elements
+        if (bn == 256) return launch_gett<KIND, 256, 6, kBK, 0>(d, ta, tb, st);
+        return launch_gett<KIND, 128, 8, kBK, 0>(d, ta, tb, st);
+    } else if constexpr (KIND == GK_TF32X3) {  // two 4-byte slices per operand: 192 KB of rings
         if (comp) {
             if (tma) return launch_gett<KIND, 128, 3, kBKT, 3, true>(d, ta, tb, st);
             return launch_gett<KIND, 128, 3, kBK, 0, true>(d, ta, tb, st);
@@ -1891,7 +1968,7 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     if (s != TC_SUCCESS) return s;
     const int in_bytes = (p.dtype == TC_BF16 || p.dtype == TC_F16) ? 2 : 4;
     const int vec = 16 / in_bytes;
-    const int chunk = (p.dtype == TC_TF32 || p.dtype == TC_TF32X3) ? 4 : 8;
+    const int chunk = (p.dtype == TC_TF32 || p.dtype == TC_TF32X3) ? 4 : (p.dtype == TC_E4M3 ? 16 : 8);
     int bn = p.gett_bn == 128 || p.gett_bn == 256 ? p.gett_bn : (d.N >= 256 ? 256 : 128);
     // compensated accumulation (split-BF16 only): K chunks of comp_k elements
     int64_t comp_k = 0;
@@ -1943,7 +2020,8 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     bool pair = false;
     // batch indices: the global-load path (the TMA warp and the
     // pre-converted images walk M and N tiles only)
-    if (p.gett_tma && d.nb == 0 && d.K < (int64_t(1) << 31)) {  // 32-bit K positions in the TMA warp
+    // (E4M3: the global-load path only)
+    if (p.gett_tma && p.dtype != TC_E4M3 && d.nb == 0 && d.K < (int64_t(1) << 31)) {  // 32-bit K positions in the TMA warp
         if (p.gett_pair && (p.dtype == TC_BF16X3 || p.dtype == TC_TF32) && !comp && bn == 256 && d.M > kBM) {
             GettDesc dp = d;
             CUtensorMap pa, pb;
@@ -2014,6 +2092,42 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
             pack_kernel<GK_BF16X3><<<grid, 128, 0, st>>>(d, pk - 1, rows, bkp, rtiles, (char *)p.workspace);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+    }
+    if (p.dtype == TC_E4M3) {
+        // the inputs' scales, written before the GETT reads them (stream order)
+        if (!p.qbuf) {
+            cudaError_t e = cudaMalloc(&p.qbuf, 16);
+            if (e != cudaSuccess) {
+                p.qbuf = nullptr;
+                return fail(TC_ERROR_OUT_OF_MEMORY, cudaGetErrorString(e));
+            }
+        }
+        unsigned *mx = (unsigned *)p.qbuf;
+        float *scale = (float *)((char *)p.qbuf + 8);
+        cudaMemsetAsync(mx, 0, 8, st);
+        for (int o = 0; o < 2; ++o) {
+            const Layout &L = p.op[o == 0 ? OP_A : OP_B];
+            AbsmaxDesc a;
+            std::memset(&a, 0, sizeof(a));
+            int64_t total = 1, span = 1;
+            for (int m = 0; m < L.n; ++m) {
+                a.ext[m] = p.ext[L.idx[m]];
+                a.stride[m] = L.stride[m];
+                total *= a.ext[m];
+                span += (a.ext[m] - 1) * a.stride[m];
+            }
+            a.n = span == total ? 0 : L.n;
+            a.total = total;
+            a.src = (const float *)(o == 0 ? A : B);
+            a.out = mx + o;
+            const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 8));
+            absmax_kernel<<<(unsigned)grid, 256, 0, st>>>(a);
+        }
+        e4m3_scale_kernel<<<1, 32, 0, st>>>(mx, scale);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+        d.qscale = scale;
+        return launch_kind<GK_E4M3>(d, bn, false, false, false, tmA, tmB, st);
     }
     switch (p.dtype) {
     case TC_BF16X3: return launch_kind<GK_BF16X3>(d, bn, tma, comp, pair, tmA, tmB, st);

@@ -76,6 +76,7 @@ struct Plan {
     void *host_dev[3] = {nullptr, nullptr, nullptr};  // tc_execute_host: device copies of A, B, C
     size_t host_dev_bytes[3] = {0, 0, 0};
     void *gett_state = nullptr;     // owned by the GETT executor
+    void *qbuf = nullptr;           // TC_E4M3: the inputs' maxima and scales (16 bytes)
     void *flush_buf = nullptr;      // predictor: remote regions / L2 flush
     size_t flush_bytes = 0;
     std::vector<double> predicted;  // last tc_predict result per algorithm (< 0: none)

@@ -146,7 +146,7 @@ tc_status build_plan(Plan &p, const char *spec, const int64_t *extents, const in
                      bool enumerate) {
     if (!spec) return fail(TC_ERROR_INVALID_ARGUMENT, "spec is NULL");
     if (!extents) return fail(TC_ERROR_INVALID_ARGUMENT, "extents is NULL");
-    if (dtype < TC_F64 || dtype > TC_TF32X3)
+    if (dtype < TC_F64 || dtype > TC_E4M3)
         return fail(TC_ERROR_UNSUPPORTED_DTYPE, "unknown dtype");
     std::string s(spec);
     size_t eq = s.find('='), comma = s.find(',');
@@ -346,6 +346,7 @@ tc_status tc_plan_destroy(tc_plan plan) {
         if (p.workspace) cudaFree(p.workspace);
         if (p.dev_status) cudaFree(p.dev_status);
         if (p.flush_buf) cudaFree(p.flush_buf);
+        if (p.qbuf) cudaFree(p.qbuf);
         if (p.busy_event) cudaEventDestroy((cudaEvent_t)p.busy_event);
         for (void *d : p.host_dev)
             if (d) cudaFree(d);

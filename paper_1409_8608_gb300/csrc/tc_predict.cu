@@ -212,8 +212,9 @@ double probe_fraction(int64_t items, bool tiled, int gett_tc) {
 tc_status predict_one(Plan &p, int alg_id, const Operands &ops, unsigned *sink, cudaStream_t st, double *out) {
     const Algorithm &alg = p.algs[alg_id];
     const bool tensor = p.dtype != TC_F64 && p.dtype != TC_F32;
-    if (alg.kernel != TC_KERNEL_GETT && alg.kernel != TC_KERNEL_GEMM && tensor) {
-        *out = -1.0;  // at tensor dtypes only the gemm nests and the GETT run
+    if ((alg.kernel != TC_KERNEL_GETT && alg.kernel != TC_KERNEL_GEMM && tensor) ||
+        (alg.kernel != TC_KERNEL_GETT && p.dtype == TC_E4M3)) {
+        *out = -1.0;  // at tensor dtypes only the gemm nests and the GETT run (E4M3: the GETT)
         return TC_SUCCESS;
     }
     device_props();

@@ -487,6 +487,7 @@ tc_status tc_server_submit(tc_server server, const char *spec, const int64_t *ex
                            const void *A, const void *B, void *C, int64_t *request_id) {
     if (!server || !spec || !extents || !A || !B || !request_id)
         return fail(TC_ERROR_INVALID_ARGUMENT, "NULL argument");
+    if (dtype == TC_E4M3) return fail(TC_ERROR_UNSUPPORTED_DTYPE, "the serving loop does not run TC_E4M3");
     ServerImpl &S = server->s;
     // validate and size the request: spec, classes and layouts only (the
     // request runs the GETT; its plan has no other algorithm)

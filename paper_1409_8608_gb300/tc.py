@@ -22,7 +22,7 @@ STATUS_NAMES = {
     7: "TC_ERROR_CUDA", 8: "TC_ERROR_TIMEOUT", 9: "TC_ERROR_INVALID_ARGUMENT",
     10: "TC_ERROR_ADMISSION",
 }
-DTYPES = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3, "f16": 4, "bf16x3": 5, "tf32x3": 6}
+DTYPES = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3, "f16": 4, "bf16x3": 5, "tf32x3": 6, "e4m3": 7}
 KERNELS = ("dot", "axpy", "gemv", "ger", "gemm", "gett")
 
 

@@ -492,3 +492,61 @@ def test_pack_integers_exact(tcmod, spec, ext):
         plan.device_status()
         plan.close()
         assert np.array_equal(dC.double().cpu().numpy(), 2.0 * S + 0.5 * C0), dtype
+
+
+# FP8 E4M3 (the fused GETT only): each FP32 input divided by a power of two
+# that brings its largest magnitude to at most 448, rounded to E4M3 (four
+# significant bits: unit roundoff 2^-4), products on kind::f8f6f4 into FP32.
+E4M3_U = 2.0 ** -4
+
+
+def e4m3_bound(K):
+    # per term (2u + u^2)|a||b| for inputs in E4M3's normal range, plus the
+    # subnormal slack (2^-10 of each input's scale: about 2^-14 of the sum
+    # for these inputs) and the FP32 accumulation
+    return 2 * E4M3_U + E4M3_U ** 2 + 2.0 ** -14 + (K + 2) * U32
+
+
+@pytest.mark.parametrize("spec,ext", CASES)
+def test_e4m3_exact_on_integers(tcmod, spec, ext):
+    # integers in [-8, 8] scale by 32 onto E4M3 values exactly; every product
+    # and partial sum is an integer below 2^24
+    A, B, _ = synth.integer_operands(spec, ext, seed=1)
+    want = oc.contract(spec, ext, A, B)
+    dA, dB, _ = device_inputs("e4m3", A, B)
+    got = run_gett(tcmod, spec, ext, "e4m3", dA, dB)
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, (bad[:5], got[bad[:5]], want[bad[:5]])
+
+
+@pytest.mark.parametrize("spec,ext", CASES[:4])
+@pytest.mark.parametrize("mag", [1.0, 1e-6, 3e5])
+def test_e4m3_within_bound_at_any_magnitude(tcmod, spec, ext, mag):
+    # the power-of-two scales make the bound hold whatever the inputs' size
+    A, B, _ = synth.uniform_operands(spec, ext, seed=0)
+    A, B = A * mag, B / mag ** 0.5
+    dA, dB, (Ar, Br) = device_inputs("e4m3", A, B)
+    want = oc.contract(spec, ext, Ar, Br)
+    scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
+    got = run_gett(tcmod, spec, ext, "e4m3", dA, dB)
+    err = float(np.max(np.abs(got - want) / scale))
+    assert err <= e4m3_bound(ksize(spec, ext)), (err, mag)
+    assert err > 1e-4  # the form is FP8: far coarser than FP32
+
+
+def test_e4m3_alpha_beta_and_refused_nests(tcmod):
+    spec, ext = "abc=ai,ibc", [64, 40, 30, 16]
+    A, B, C0 = synth.integer_operands(spec, ext, seed=4, with_c=True)
+    S = oc.contract(spec, ext, A, B)
+    dA, dB, _ = device_inputs("e4m3", A, B)
+    got = run_gett(tcmod, spec, ext, "e4m3", dA, dB, C0=C0, alpha=2.0, beta=-0.5)
+    assert np.array_equal(got, 2.0 * S - 0.5 * C0)
+    plan = tcmod.Plan(spec, ext, dtype="e4m3")
+    d = torch.zeros(synth.dense_sizes(spec, ext)[0], device="cuda:0")
+    pred = plan.predict(None)
+    assert pred[0] > 0 and all(t < 0 for t in pred[1:])
+    plan.select(1)
+    with pytest.raises(tcmod.TcError) as e:
+        plan.execute(d, d, d)
+    assert tcmod.STATUS_NAMES[e.value.status] == "TC_ERROR_UNSUPPORTED_DTYPE"
+    plan.close()
