@@ -550,3 +550,48 @@ def test_e4m3_alpha_beta_and_refused_nests(tcmod):
         plan.execute(d, d, d)
     assert tcmod.STATUS_NAMES[e.value.status] == "TC_ERROR_UNSUPPORTED_DTYPE"
     plan.close()
+
+
+def test_e4m3_strided_inputs_scale_from_elements_only(tcmod):
+    # A and B with gaps between their elements (strides past the extents);
+    # the gaps hold 1e6: the max-magnitude pre-pass must walk the operands'
+    # modes, or every input would be rounded against the gaps' magnitude
+    spec, ext = "abc=ai,ibc", [40, 9, 7, 12]  # a, b, c, i
+    a, b, c, i = ext
+    strides = [1, a, a * b, 2, 2 * a + 3, 1, i + 1, (i + 1) * b]  # C dense; A (a, i); B (i, b, c)
+    ext_d, sc, sa, sb = oc.operand_layout(spec, ext, strides)
+    nA = oc.required_length("ai", ext_d, sa)
+    nB = oc.required_length("ibc", ext_d, sb)
+    rng = np.random.default_rng(21)
+    A = np.full(nA, 1e6)
+    B = np.full(nB, 1e6)
+    for x in range(a):
+        for y in range(i):
+            A[x * sa["a"] + y * sa["i"]] = rng.uniform(-1, 1)
+    for y in range(i):
+        for u in range(b):
+            for v in range(c):
+                B[y * sb["i"] + u * sb["b"] + v * sb["c"]] = rng.uniform(-1, 1)
+    dA, dB, (Ar, Br) = device_inputs("e4m3", A, B)
+    want = oc.contract(spec, ext, Ar, Br, strides=strides)
+    scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br), strides=strides)
+    plan = tcmod.Plan(spec, ext, strides=strides, dtype="e4m3")
+    plan.select(0)
+    dC = torch.full((a * b * c,), float("nan"), device="cuda:0")
+    plan.execute(dA, dB, dC)
+    torch.cuda.synchronize()
+    plan.device_status()
+    plan.close()
+    err = float(np.max(np.abs(dC.double().cpu().numpy() - want) / scale))
+    assert err <= e4m3_bound(i), err
+
+
+@pytest.mark.parametrize("spec,ext", [
+    ("abc=ai,ibc", [1, 1, 1, 1]),
+    ("abc=ai,ibc", [130, 3, 70, 1]),
+    ("abc=iaj,jbic", [1, 300, 2, 1, 1]),
+])
+def test_e4m3_degenerate_extents(tcmod, spec, ext):
+    A, B, _ = synth.integer_operands(spec, ext, seed=14)
+    dA, dB, _ = device_inputs("e4m3", A, B)
+    assert np.array_equal(run_gett(tcmod, spec, ext, "e4m3", dA, dB), oc.contract(spec, ext, A, B))
