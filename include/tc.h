@@ -237,30 +237,39 @@ tc_status tc_plan_set_gett_tile(tc_plan plan, int32_t width);
  * same either way. */
 tc_status tc_plan_set_gett_tma(tc_plan plan, int32_t enable);
 
-/* Tensor-core GETT, FP32 inputs (TC_BF16X3, TC_TF32): pre-conversion of the
- * smaller input.  With it, a pre-pass kernel writes that input once into
- * the plan's workspace as the converted shared-memory images of its tiles
- * (split-BF16 slices or TF32 words in the MMA's core-matrix layout, zeros
- * past the extents), and the GETT copies them with 16-byte asynchronous
- * copies instead of loading and converting the input per tile; the K order
- * then follows the larger input alone.  mode 0: never; 1 (default): when
- * the smaller input has at most 1/8 of the larger one's elements and its
- * images fit in 64 MiB; 2: whenever its images fit in 64 MiB.  Other values
- * give TC_ERROR_INVALID_ARGUMENT.  The workspace is allocated by the first
+/* Tensor-core GETT, FP32 inputs (TC_BF16X3, TC_TF32X3, TC_TF32):
+ * pre-conversion of the smaller input, or of both.  With it, a pre-pass
+ * kernel writes the input once into the plan's workspace as the converted
+ * shared-memory images of its tiles (split-BF16 slices or TF32 words in the
+ * MMA's core-matrix layout, zeros past the extents), and the GETT copies
+ * them instead of loading and converting the input per tile; the K order
+ * then follows the larger input alone.  mode 0: never; 1 (default): both
+ * inputs for the compensated split form (K past the chunk of
+ * tc_plan_set_compensation) when their images fit in 2 GiB, else the smaller
+ * input when it has at most 1/8 of the larger one's elements and its
+ * images fit in 64 MiB; 2: the smaller input whenever its images fit in
+ * 64 MiB; 3: both inputs whenever their images fit in 2 GiB (else none),
+ * each stage's two images then reach shared memory as two 1-D bulk copies
+ * and no input is staged by TMA.  Other values give
+ * TC_ERROR_INVALID_ARGUMENT.  The workspace is allocated by the first
  * execute that needs it (tc_algorithm_workspace(plan, 0) bounds it).  The
- * K order, and so the rounding of the sums, depends on this setting but not
- * on tc_plan_set_gett_tma: both input paths give the same bits.  With
- * pre-conversion an execute launches two kernels (pre-pass, GETT). */
+ * K order, and so the rounding of the sums, depends on whether an input is
+ * pre-converted but not on which (modes 1-3 with a pre-converted input give
+ * the same bits) nor on tc_plan_set_gett_tma.  With pre-conversion an
+ * execute launches two kernels (pre-pass, GETT), three with both inputs. */
 tc_status tc_plan_set_gett_pack(tc_plan plan, int32_t mode);
 
 /* Tensor-core GETT, FP32-input kinds (TC_BF16X3, TC_TF32): CTA pairs.
  * With 1, and where the launch allows it (256-column tiles, no
  * compensated accumulation, more than 128 rows of M, every input staged by
- * TMA or pre-converted), clusters of two CTAs share each MMA
- * (tcgen05.mma.cta_group::2, M = 256): each CTA stages and converts its 128
- * rows of A and half of the tile's 256 rows of B, so a CTA moves half the
- * B bytes per MMA; 0 (default) keeps one CTA per tile.  Results are the
- * same bits either way.  Other values give TC_ERROR_INVALID_ARGUMENT. */
+ * TMA or pre-converted; or, for TC_BF16X3 with both inputs pre-converted
+ * (tc_plan_set_gett_pack), any layout with more than 128 rows of M, on
+ * 256-column tiles or compensated 128-column ones), clusters of two CTAs
+ * share each MMA (tcgen05.mma.cta_group::2, M = 256): each CTA stages and
+ * converts (or copies) its 128 rows of A and half of the tile's rows of B,
+ * so a CTA moves half the B bytes per MMA; 0 (default) keeps one CTA per
+ * tile.  Results are the same bits either way.  Other values give
+ * TC_ERROR_INVALID_ARGUMENT. */
 tc_status tc_plan_set_gett_pair(tc_plan plan, int32_t enable);
 
 /* TC_BF16X3 and TC_TF32X3, tensor-core GETT without compensation: split

@@ -76,6 +76,7 @@ constexpr int64_t kTwoStageBoxMinK = 128; // shorter K keeps one-stage boxes (fi
 constexpr int64_t kCompChunkK = 256;      // default K chunk of the compensated split-BF16 form
 constexpr int kConvGroups = 2;            // converter groups taking turns (TMA-staged operands)
 constexpr int64_t kPackMaxBytes = int64_t(64) << 20;  // largest pre-converted input
+constexpr int64_t kPackBothMaxBytes = int64_t(2) << 30;  // both inputs pre-converted: their images
 constexpr int kPackRatio = 8;             // auto: the smaller input has <= 1/8 the elements
 constexpr int kEpiWarps = 4;              // warps 0-3
 constexpr int kEpiThreads = kEpiWarps * 32;
@@ -133,12 +134,15 @@ struct GettDesc {
     int64_t tile0;
     int64_t tile_begin;  // first tile of this launch (batched form; else 0)
     int one_stage;       // batched form: every problem's K fits one stage
-    // pre-converted input (0 none, 1 A, 2 B): its stage images, laid out
-    // [row tile][K stage][slice][core-matrix image] as the converters would
-    // write them to shared memory
+    // pre-converted input (0 none, 1 A, 2 B, 3 both): its stage images,
+    // laid out [row tile][K stage][slice][core-matrix image] as the
+    // converters would write them to shared memory (3: A's at pk_base, B's
+    // at pkb_base)
     int pk;
     const char *pk_base;
     int64_t pk_tile_bytes;  // one row tile's images (every K stage)
+    const char *pkb_base;
+    int64_t pkb_tile_bytes;
 };
 
 // number of batch values of a descriptor (1 without batch indices)
@@ -690,7 +694,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
     using T = KindTraits<KIND, BK>;
     using SP = SmemPlan<KIND, BN, STAGES, BK, SSTG, BATCH, PAIR>;
-    static_assert(!(PAIR && (COMP || BATCH)), "CTA pairs: plain tensor-core GETT only");
+    // (pairs with the compensated form: both inputs pre-converted only)
+    static_assert(!(PAIR && BATCH), "CTA pairs: not in the batched form");
     constexpr bool TMA = SP::TMA;
     constexpr int SS = SP::kSstg;
     constexpr int BNL = SP::kBNL;  // B rows this CTA stages and converts
@@ -770,8 +775,9 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         // or the four of one group when the groups take turns
         const uint32_t conv_warps = grouped ? kProducerThreads / 32 / kConvGroups : kProducerThreads / 32;
         for (int s = 0; s < STAGES; ++s) {
-            // pairs: both CTAs' converters arrive on rank 0's barrier
-            mbar_init(&full[s], conv_warps * (PAIR ? 2 : 1));
+            // pairs: both CTAs' converters arrive on rank 0's barrier; with
+            // both inputs pre-converted the copying lane arms it alone
+            mbar_init(&full[s], d.pk == 3 ? (PAIR && crank == 0 ? 2u : 1u) : conv_warps * (PAIR ? 2 : 1));
             mbar_init(&empty[s], 1);
         }
         // a staging slot is free again once every stage of its box is converted
@@ -968,7 +974,7 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                 }
             }
         }
-        for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop && !grouped && !PAIR;
+        for (int64_t tile = d.tile_begin + blockIdx.x; tile < d.num_tiles && !stop && !grouped && !PAIR && d.pk != 3;
              tile += gridDim.x, ++it) {
             const GettDesc &P = tile_desc<BATCH>(d, tile);
             int64_t boA, boB, boC;
@@ -1086,7 +1092,47 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
         }
     } else if (warp == kTmaWarp) {
         // ---------------------------------------------------------- TMA issue
-        if (TMA && any_tma && lane == 0) {
+        if (!BATCH && d.pk == 3) {
+            // both inputs pre-converted: one lane copies each stage's two
+            // images (contiguous runs of the workspace) straight into the
+            // operand ring with 1-D bulk copies; the converters stay idle.
+            // Pairs: each CTA copies its 128 rows of A and its half of the
+            // tile's B rows into its own ring (images of 128-row and
+            // BN/2-row tiles, two per pair tile)
+            if (lane == 0) {
+                asm volatile("griddepcontrol.wait;" ::: "memory");  // the pre-pass grids are complete
+                constexpr uint32_t kImgA = (uint32_t)(T::kSlices * SP::kATile);
+                constexpr uint32_t kImgB = (uint32_t)(T::kSlices * SP::kBTile);
+                int64_t g = 0;
+                bool stop = false;
+                for (int64_t tile = d.tile_begin + slot0; tile < d.num_tiles && !stop; tile += nslots) {
+                    int64_t mt;
+                    const int64_t nt = divmod(tile, d.tiles_m, mt);
+                    const char *ia = d.pk_base + (PAIR ? 2 * mt + crank : mt) * d.pk_tile_bytes;
+                    const char *ib = d.pkb_base + (PAIR ? 2 * nt + crank : nt) * d.pkb_tile_bytes;
+                    for (int kt = 0; kt < nkt; ++kt, ++g) {
+                        const int s = (int)(g % STAGES);
+                        if (*abort_flag ||
+                            (g >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((g / STAGES) - 1) & 1)))) {
+                            stop = true;
+                            break;
+                        }
+                        char *stage = ops + s * SP::kStage;
+                        mbar_arrive_expect_tx(&full[s], kImgA + kImgB);
+                        bulk_load(stage, ia + kt * (int64_t)kImgA, kImgA, &full[s]);
+                        bulk_load(stage + kImgA, ib + kt * (int64_t)kImgB, kImgB, &full[s]);
+                    }
+                }
+                if (stop) {
+                    *abort_flag = 1;
+                    atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
+                    // the copies still in flight land before the CTA may
+                    // exit: each slot's last issue completes its phase
+                    for (int64_t q = g > STAGES ? g - STAGES : 0; q < g; ++q)
+                        mbar_wait(&full[q % STAGES], (uint32_t)((q / STAGES) & 1));
+                }
+            }
+        } else if (TMA && any_tma && lane == 0) {
             int64_t g = 0;
             bool stop = false;
             // box coordinates of a tile's rows, and of one of its K stages
@@ -1174,6 +1220,32 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             // slice products: split-BF16 3 / 6 / 9; 3xTF32 hi.hi, hi.lo, lo.hi
             const int nprod = KIND == GK_BF16X3 ? d.nprod : (KIND == GK_TF32X3 ? 3 : 1);
             const uint32_t base = smem_u32(ops);
+            // descriptors of stage slot 0, slice 0, first K step: every other
+            // operand tile differs only in its start address, whose field is
+            // the descriptor's low bits (address >> 4, below 2^14 for any
+            // shared-memory offset), so adding (offset >> 4) moves it.  With
+            // the products unrolled the issuing thread spends a few
+            // independent instructions per MMA (a dependent chain per MMA
+            // left the N = 128 tensor pipe idle most of the time).
+            const uint64_t ad0 = smem_desc(base, lboA, 128);
+            const uint64_t bd0 = smem_desc(base + T::kSlices * SP::kATile, lboB, 128);
+            auto issue_stage = [&](auto np, uint64_t as, uint64_t bs, uint32_t dt, bool first) {
+                constexpr int NP = decltype(np)::value;
+#pragma unroll
+                for (int ks = 0; ks < T::kKsteps; ++ks) {
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        const uint32_t qa = (uint32_t)(kPa >> (4 * q)) & 15u, qb = (uint32_t)(kPb >> (4 * q)) & 15u;
+                        const uint64_t ad = as + (uint64_t)((qa * SP::kATile + ks * 2 * lboA) >> 4);
+                        const uint64_t bd = bs + (uint64_t)((qb * SP::kBTile + ks * 2 * lboB) >> 4);
+                        // each accumulator starts from zero with its own
+                        // first product of the unit
+                        const bool fresh = first && ks == 0 && q == (split && q > 0 ? 1 : 0);
+                        const uint32_t dq = split && q > 0 ? dt + (uint32_t)BN : dt;
+                        mma_issue<KIND, PAIR>(dq, ad, bd, idesc, !fresh);
+                    }
+                }
+            };
             int64_t g = 0;
             int64_t u = 0;  // accumulation units (tiles, or K chunks of tiles)
             bool stop = false;
@@ -1201,21 +1273,15 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t sa = base + s * SP::kStage;
-                        const uint32_t sb = sa + T::kSlices * SP::kATile;
+                        const uint64_t so = (uint64_t)((s * SP::kStage) >> 4);
                         const bool first = kt == c * cstg_t;
-#pragma unroll
-                        for (int ks = 0; ks < T::kKsteps; ++ks) {
-                            for (int q = 0; q < nprod; ++q) {
-                                const uint32_t qa = (uint32_t)(kPa >> (4 * q)) & 15u, qb = (uint32_t)(kPb >> (4 * q)) & 15u;
-                                uint64_t ad = smem_desc(sa + qa * SP::kATile + ks * 2 * lboA, lboA, 128);
-                                uint64_t bd = smem_desc(sb + qb * SP::kBTile + ks * 2 * lboB, lboB, 128);
-                                // each accumulator starts from zero with its own
-                                // first product of the unit
-                                const bool fresh = first && ks == 0 && q == (split && q > 0 ? 1 : 0);
-                                const uint32_t dq = split && q > 0 ? dt + (uint32_t)BN : dt;
-                                mma_issue<KIND, PAIR>(dq, ad, bd, idesc, !fresh);
-                            }
+                        if constexpr (KIND == GK_BF16X3) {
+                            if (nprod == 6) issue_stage(std::integral_constant<int, 6>{}, ad0 + so, bd0 + so, dt, first);
+                            else if (nprod == 3) issue_stage(std::integral_constant<int, 3>{}, ad0 + so, bd0 + so, dt, first);
+                            else issue_stage(std::integral_constant<int, 9>{}, ad0 + so, bd0 + so, dt, first);
+                        } else {
+                            issue_stage(std::integral_constant<int, KIND == GK_TF32X3 ? 3 : 1>{}, ad0 + so, bd0 + so, dt,
+                                        first);
                         }
                         commit(&empty[s]);
                     }
@@ -1230,6 +1296,26 @@ gett_tc_kernel(const GettDesc d, const __grid_constant__ CUtensorMap tmA, const 
             if constexpr (PAIR) mma_commit2(drain, (uint16_t)1);
             else mma_commit(drain);
             mbar_wait(drain, 0);
+        } else if (PAIR && !BATCH && d.pk == 3 && lane == 0) {
+            // both inputs pre-converted, second CTA of a pair: its copies
+            // complete on its own stage barriers; this lane passes each
+            // completed stage on to the issuer's barrier in the first CTA
+            int64_t g = 0;
+            bool stop = false;
+            for (int64_t tile = d.tile_begin + slot0; tile < d.num_tiles && !stop; tile += nslots) {
+                for (int kt = 0; kt < nkt; ++kt, ++g) {
+                    const int s = (int)(g % STAGES);
+                    if (*abort_flag || !mbar_wait(&full[s], (uint32_t)((g / STAGES) & 1))) {
+                        stop = true;
+                        break;
+                    }
+                    mbar_arrive_remote(mapa_shared(smem_u32(&full[s]), 0u));
+                }
+            }
+            if (stop) {
+                *abort_flag = 1;
+                atomicExch(d.status, (int)TC_ERROR_TIMEOUT);
+            }
         }
         __syncwarp();
     } else {
@@ -1428,6 +1514,12 @@ __global__ void __launch_bounds__(128) pack_kernel(const GettDesc d, int op, int
     const int64_t *rs = op == 0 ? d.m_sA : d.n_sB;
     const int64_t *ks = op == 0 ? d.k_sA : d.k_sB;
     const int slice = rows * bk * T::kElemBytes;
+    // when the innermost K mode holds whole chunks (its extent a multiple
+    // of CH; then so is K), a chunk's K positions are one run of that mode:
+    // one decode per chunk, and 16-byte loads where the run is contiguous
+    // and aligned
+    const bool whole = d.nk > 0 && d.k_ext[d.nk - 1] % CH == 0;
+    const int64_t s_in = d.nk > 0 ? ks[d.nk - 1] : 0;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x) {
         // rows fastest, then K chunks, K stages, row tiles (divmod: 32-bit
         // divisions whenever the values fit)
@@ -1445,8 +1537,34 @@ __global__ void __launch_bounds__(128) pack_kernel(const GettDesc d, int op, int
             }
         }
         float x[CH];
+        if (whole) {
+            int64_t k = kt * bk + kc * CH, ko = 0;
 #pragma unroll
-        for (int e = 0; e < CH; ++e) {
+            for (int e = 0; e < CH; ++e) x[e] = 0.0f;
+            if (ro >= 0 && k < d.K) {
+                for (int m = d.nk - 1; m >= 0; --m) {
+                    int64_t v;
+                    k = divmod(k, d.k_ext[m], v);
+                    ko += v * ks[m];
+                }
+                const float *p = src + ro + ko;
+                if (s_in == 1 && ((uintptr_t)p & 15) == 0) {
+#pragma unroll
+                    for (int e = 0; e < CH; e += 4) {
+                        const float4 v4 = *reinterpret_cast<const float4 *>(p + e);
+                        x[e] = v4.x;
+                        x[e + 1] = v4.y;
+                        x[e + 2] = v4.z;
+                        x[e + 3] = v4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < CH; ++e) x[e] = p[e * s_in];
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < CH && !whole; ++e) {
             int64_t k = kt * bk + kc * CH + e;
             x[e] = 0.0f;
             if (ro >= 0 && k < d.K) {
@@ -1575,6 +1693,18 @@ tc_status launch_kind(GettDesc &d, int bn, bool tma, bool comp, bool pair, const
     d.tiles_n = (d.N + bn - 1) / bn;
     d.num_tiles = d.tiles_m * d.tiles_n * batch_count(d);
     if (d.tile_frac < 1.0) d.num_tiles = std::max<int64_t>(1, (int64_t)(d.num_tiles * d.tile_frac));
+    // CTA pairs with both inputs pre-converted (pair tiles of 256 x BN;
+    // per CTA 128 rows of A and BN/2 of B in each 32-position stage):
+    // split-BF16 256 x 256 (four stages) or compensated 256 x 128, whose
+    // two chunk accumulators and (hi, lo) take each CTA's 512 tensor-memory
+    // columns
+    if (pair && d.pk == 3) {
+        if constexpr (KIND == GK_BF16X3) {
+            if (comp) return launch_gett<KIND, 128, 5, kBK, 0, true, false, true>(d, ta, tb, st);
+            if (bn == 256) return launch_gett<KIND, 256, 4, kBK, 0, false, false, true>(d, ta, tb, st);
+        }
+        return fail(TC_ERROR_UNSUPPORTED_DTYPE, "no CTA-pair launch for this pre-converted form");
+    }
     // CTA pairs (tiles of 256 x 256): four operand stages of 128 + 128
     // rows and three staging slots of two-stage boxes
     if constexpr (KIND == GK_BF16X3 || KIND == GK_TF32) {
@@ -1809,7 +1939,7 @@ bool plan_tma_operand(const Plan &p, int opnd, const void *base, int in_bytes, i
 int image_bytes(tc_dtype dt) { return dt == TC_TF32 ? 4 : (dt == TC_TF32X3 ? 8 : 6); }
 
 // Pre-conversion choice for the tensor-core GETT (0 none, 1 A, 2 B: the
-// input with fewer elements) and a bound on its stage images' bytes.
+// input with fewer elements, 3 both) and a bound on the stage images' bytes.
 int pack_choice(const Plan &p, int64_t &bound) {
     bound = 0;
     if ((p.dtype != TC_BF16X3 && p.dtype != TC_TF32 && p.dtype != TC_TF32X3) || p.gett_pack == 0 ||
@@ -1819,6 +1949,21 @@ int pack_choice(const Plan &p, int64_t &bound) {
     for (int id : p.freeA) M *= p.ext[id];
     for (int id : p.freeB) N *= p.ext[id];
     for (int id : p.contracted) K *= p.ext[id];
+    // both inputs: on request (3), and by default for the compensated form,
+    // whose 128-column tiles would otherwise convert each input once per
+    // tile of the other; A's rows round up to a 128-row tile, B's to a
+    // 256-row one, K to a 32-position stage, plus the alignment of B's images
+    int64_t comp_k = 0;
+    if (p.dtype == TC_BF16X3 || p.dtype == TC_TF32X3) comp_k = p.comp_chunk < 0 ? kCompChunkK : p.comp_chunk;
+    const bool comp = comp_k > 0 && K > comp_k;
+    if (p.gett_pack == 3 || (p.gett_pack == 1 && comp)) {
+        const int64_t b2 = (M + N + 512) * (K + kBK - 1) * image_bytes(p.dtype) + 256;
+        if (b2 <= kPackBothMaxBytes) {
+            bound = b2;
+            return 3;
+        }
+        if (p.gett_pack == 3) return 0;
+    }
     const bool a_small = M <= N;  // the same choice as the K order's "larger input"
     const int64_t R = a_small ? M : N;
     // auto: only where the two inputs are contiguous along different
@@ -2021,7 +2166,8 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     // batch indices: the global-load path (the TMA warp and the
     // pre-converted images walk M and N tiles only)
     // (E4M3: the global-load path only)
-    if (p.gett_tma && p.dtype != TC_E4M3 && d.nb == 0 && d.K < (int64_t(1) << 31)) {  // 32-bit K positions in the TMA warp
+    // (both inputs pre-converted: no input is staged)
+    if (p.gett_tma && pk != 3 && p.dtype != TC_E4M3 && d.nb == 0 && d.K < (int64_t(1) << 31)) {  // 32-bit K positions in the TMA warp
         if (p.gett_pair && (p.dtype == TC_BF16X3 || p.dtype == TC_TF32) && !comp && bn == 256 && d.M > kBM) {
             GettDesc dp = d;
             CUtensorMap pa, pb;
@@ -2037,6 +2183,11 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
         }
         if (!pair) tma = plan_tma(d, tmA, tmB, bn);
     }
+    // CTA pairs with both inputs pre-converted: no staging, so every
+    // layout qualifies (more than one 128-row tile; split-BF16 on 256-wide
+    // tiles or compensated)
+    if (pk == 3 && p.gett_pair && d.M > kBM && d.nb == 0 && p.dtype == TC_BF16X3 && (comp || bn == 256))
+        pair = true;
     if (comp) d.chunk_stages = (int)(comp_k / (tma ? kBKT : kBK));
     // global-load mappings (used by operands without TMA staging)
     auto pick = [&](const void *base, int rows, int nrow, const int64_t *rext, const int64_t *rs,
@@ -2066,7 +2217,41 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     const bool want_split = p.gett_split > 0 || (p.gett_split < 0 && d.K >= kSplitMinK);
     d.split = ((p.dtype == TC_BF16X3 || p.dtype == TC_TF32X3) && !comp && want_split) ? 1 : 0;
     cudaStream_t st = (cudaStream_t)stream;
-    if (pk) {
+    if (pk == 3) {
+        // both inputs' stage images (128-row tiles of A, bn-row tiles of B,
+        // 32-position K stages), A's first, then B's on a 256-byte boundary;
+        // the GETT copies each stage's two images with 1-D bulk copies.
+        // Pairs: B in bn/2-row tiles, both inputs in an even number of row
+        // tiles (two per pair tile; rows past the extent are zeros)
+        const int64_t nktp = (d.K + kBK - 1) / kBK;
+        const int brows = pair ? bn / 2 : bn;
+        const int64_t stA = (int64_t)kBM * kBK * image_bytes(p.dtype), stB = (int64_t)brows * kBK * image_bytes(p.dtype);
+        const int64_t rtA = pair ? 2 * ((d.M + 2 * kBM - 1) / (2 * kBM)) : (d.M + kBM - 1) / kBM;
+        const int64_t rtB = pair ? 2 * ((d.N + bn - 1) / bn) : (d.N + bn - 1) / bn;
+        const int64_t offB = (rtA * nktp * stA + 255) / 256 * 256;
+        // offB + rtB * nktp * stB <= pk_bound (rows round up by less than
+        // 128 and bn <= 256, K by less than 32)
+        s = ensure_device_resources(p, (size_t)pk_bound);
+        if (s != TC_SUCCESS) return s;
+        d.pk = 3;
+        d.pk_base = (const char *)p.workspace;
+        d.pk_tile_bytes = nktp * stA;
+        d.pkb_base = (const char *)p.workspace + offB;
+        d.pkb_tile_bytes = nktp * stB;
+        for (int o = 0; o < 2; ++o) {
+            const int rows = o == 0 ? kBM : brows;
+            const int64_t rt = o == 0 ? rtA : rtB;
+            const int64_t bytes = rt * nktp * (o == 0 ? stA : stB);
+            const int64_t chunks = bytes / 16 / (p.dtype == TC_TF32 ? 1 : (p.dtype == TC_TF32X3 ? 2 : 3));
+            const unsigned grid = (unsigned)std::min<int64_t>((chunks + 127) / 128, 152 * 16);
+            char *out = (char *)p.workspace + (o == 0 ? 0 : offB);
+            if (p.dtype == TC_TF32) pack_kernel<GK_TF32><<<grid, 128, 0, st>>>(d, o, rows, kBK, rt, out);
+            else if (p.dtype == TC_TF32X3) pack_kernel<GK_TF32X3><<<grid, 128, 0, st>>>(d, o, rows, kBK, rt, out);
+            else pack_kernel<GK_BF16X3><<<grid, 128, 0, st>>>(d, o, rows, kBK, rt, out);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+    } else if (pk) {
         // the smaller input's stage images, for the stage depth the launch
         // uses; pairs read them as two images per pair tile (an even count)
         const int bkp = tma ? kBKT : kBK;

@@ -421,7 +421,7 @@ tc_status tc_plan_set_gett_tma(tc_plan plan, int32_t enable) {
 
 tc_status tc_plan_set_gett_pack(tc_plan plan, int32_t mode) {
     if (!plan) return fail(TC_ERROR_INVALID_ARGUMENT, "plan is NULL");
-    if (mode < 0 || mode > 2) return fail(TC_ERROR_INVALID_ARGUMENT, "pack mode must be 0, 1 or 2");
+    if (mode < 0 || mode > 3) return fail(TC_ERROR_INVALID_ARGUMENT, "pack mode must be 0, 1, 2 or 3");
     plan->p.gett_pack = mode;
     return TC_SUCCESS;
 }

@@ -135,9 +135,9 @@ def test_plan_option_validation(lib):
         plan.set_gett_tile(64)
     with pytest.raises(tc.TcError):
         plan.set_gett_tma(2)
-    for mode in (0, 1, 2):
+    for mode in (0, 1, 2, 3):
         plan.set_gett_pack(mode)
-    for mode in (-1, 3):
+    for mode in (-1, 4):
         with pytest.raises(tc.TcError) as e:
             plan.set_gett_pack(mode)
         assert tc.STATUS_NAMES[e.value.status] == "TC_ERROR_INVALID_ARGUMENT"

@@ -438,10 +438,12 @@ def test_gett_degenerate_extents(tcmod, spec, ext, dtype):
     assert np.array_equal(run_gett(tcmod, spec, ext, dtype, dA, dB), oc.contract(spec, ext, A, B))
 
 
-# Pre-converted smaller input (tc_plan_set_gett_pack): the GETT reads the
-# small input's split-BF16 / TF32 stage images written by a pre-pass, and
-# the K order follows the larger input.  Both input paths of the larger
-# input must give the same bits, and every mode stays within the bound.
+# Pre-converted inputs (tc_plan_set_gett_pack): the GETT reads the small
+# input's split-BF16 / TF32 stage images written by a pre-pass (mode 2), or
+# both inputs' images (mode 3, copied by 1-D bulk copies), and the K order
+# follows the larger input.  Both input paths of the larger input, and
+# both-inputs pre-converted, must give the same bits, and every mode stays
+# within the bound.
 PACK_CASES = [
     ("abc=iaj,jbic", [256, 512, 3, 16, 16]),  # A packed; B keeps 64-byte rows of j
     ("abc=aic,ib", [200, 100, 48, 72]),       # B packed, N = 100 < one tile, K = 72 (stage tail)
@@ -460,7 +462,7 @@ def test_pack_modes_within_bound_and_paths_bitwise(tcmod, spec, ext, dtype):
     K = ksize(spec, ext)
     bound = sum_bound(dtype, K)
     outs = {}
-    for pack, tma in ((0, 1), (2, 1), (2, 0)):
+    for pack, tma in ((0, 1), (2, 1), (2, 0), (3, 1)):
         plan = tcmod.Plan(spec, ext, dtype=dtype)
         plan.set_gett_pack(pack)
         plan.set_gett_tma(tma)
@@ -476,22 +478,92 @@ def test_pack_modes_within_bound_and_paths_bitwise(tcmod, spec, ext, dtype):
         err = float(np.max(np.abs(outs[(pack, tma)] - want) / scale))
         assert err <= bound, (pack, tma, err, bound)
     assert np.array_equal(outs[(2, 1)], outs[(2, 0)])
+    assert np.array_equal(outs[(3, 1)], outs[(2, 0)])
 
 
 @pytest.mark.parametrize("spec,ext", PACK_CASES)
 def test_pack_integers_exact(tcmod, spec, ext):
     A, B, C0 = synth.integer_operands(spec, ext, seed=13, with_c=True)
     S = oc.contract(spec, ext, A, B)
-    for dtype in ("bf16x3", "tf32"):
-        dA, dB, _ = device_inputs(dtype, A, B)
+    for dtype in ("bf16x3", "tf32", "tf32x3"):
+        for pack in (2, 3):
+            dA, dB, _ = device_inputs(dtype, A, B)
+            plan = tcmod.Plan(spec, ext, dtype=dtype)
+            plan.set_gett_pack(pack)
+            dC = torch.from_numpy(C0).float().to("cuda:0")
+            plan.execute(dA, dB, dC, alpha=2.0, beta=0.5)
+            torch.cuda.synchronize()
+            plan.device_status()
+            plan.close()
+            assert np.array_equal(dC.double().cpu().numpy(), 2.0 * S + 0.5 * C0), (dtype, pack)
+
+
+@pytest.mark.parametrize("spec,ext,dtype,comp", [
+    ("ab=aij,jib", [300, 260, 24, 20], "bf16x3", -1),   # compensated, ragged pair tiles (M = 300)
+    ("abc=iaj,jbic", [200, 96, 5, 16, 8], "bf16x3", 0),  # split accumulators, 256-wide tiles, N tail
+    ("abc=ai,ibc", [520, 64, 9, 40], "bf16x3", 0),       # K = 40: a stage tail, one split stage
+])
+def test_pack_both_pairs_bitwise(tcmod, spec, ext, dtype, comp):
+    # both inputs pre-converted, one CTA per tile or CTA pairs (cta_group::2
+    # M = 256, each CTA copying its own rows of A and half of B's): the same
+    # bits, and within the form's bound
+    A, B, _ = synth.uniform_operands(spec, ext, seed=16)
+    dA, dB, (Ar, Br) = device_inputs(dtype, A, B)
+    want = oc.contract(spec, ext, Ar, Br)
+    scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
+    n = synth.dense_sizes(spec, ext)[0]
+    outs = {}
+    for pair in (0, 1):
         plan = tcmod.Plan(spec, ext, dtype=dtype)
-        plan.set_gett_pack(2)
-        dC = torch.from_numpy(C0).float().to("cuda:0")
-        plan.execute(dA, dB, dC, alpha=2.0, beta=0.5)
+        plan.set_gett_pack(3)
+        plan.set_gett_pair(pair)
+        if comp == 0:
+            plan.set_compensation(0)
+            plan.set_gett_tile(256)
+        dC = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda:0")
+        for _ in range(2):
+            plan.execute(dA, dB, dC)
         torch.cuda.synchronize()
         plan.device_status()
         plan.close()
-        assert np.array_equal(dC.double().cpu().numpy(), 2.0 * S + 0.5 * C0), dtype
+        outs[pair] = dC.double().cpu().numpy()
+    assert np.array_equal(outs[1], outs[0])
+    err = float(np.max(np.abs(outs[1] - want) / scale))
+    bound = sum_bound(dtype, ksize(spec, ext))
+    assert err <= bound, (err, bound)
+
+
+@pytest.mark.parametrize("dtype", ["bf16x3", "tf32x3"])
+def test_pack_both_compensated_default(tcmod, dtype):
+    # the compensated form pre-converts both inputs by default (mode 1):
+    # the same bits as with no pre-conversion (this layout's K order does
+    # not depend on it), a workspace for both inputs' images, and the
+    # compensated bound
+    spec, ext = "ab=aij,jib", [300, 260, 24, 20]  # K = 480 > the 256 chunk; ragged tiles
+    A, B, _ = synth.uniform_operands(spec, ext, seed=15)
+    dA, dB, (Ar, Br) = device_inputs(dtype, A, B)
+    want = oc.contract(spec, ext, Ar, Br)
+    scale = oc.contract(spec, ext, np.abs(Ar), np.abs(Br))
+    n = synth.dense_sizes(spec, ext)[0]
+    outs = {}
+    for pack in (1, 0):
+        plan = tcmod.Plan(spec, ext, dtype=dtype)
+        plan.set_gett_pack(pack)
+        ws = plan.workspace(0)
+        if pack == 1:
+            assert ws >= (6 if dtype == "bf16x3" else 8) * (300 + 260) * 480
+        else:
+            assert ws == 0
+        dC = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda:0")
+        plan.execute(dA, dB, dC)
+        torch.cuda.synchronize()
+        plan.device_status()
+        plan.close()
+        outs[pack] = dC.double().cpu().numpy()
+    assert np.array_equal(outs[1], outs[0])
+    err = float(np.max(np.abs(outs[1] - want) / scale))
+    bound = 1e-6 if dtype == "bf16x3" else sum_bound(dtype, 480)
+    assert err <= bound, (err, bound)
 
 
 # FP8 E4M3 (the fused GETT only): each FP32 input divided by a power of two
