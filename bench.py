@@ -350,7 +350,12 @@ def measure_form(args, dtype, spec, extents, A, B, dev, stream, dist, world, tc,
     # GETT: one kernel, plus the pre-pass when the plan pre-converts its
     # smaller input (the only GETT workspace); nests: phases and copies
     if alg["kernel"] == "gett":
-        launches_per_step = 1 + int(plan.workspace(alg["id"]) > 0)
+        # with a workspace: one pre-pass (the smaller input), or two (both
+        # inputs: the default of the compensated split forms, K past the
+        # 256-element chunk)
+        K = plan.flops // (2 * nC)
+        both = dtype in ("bf16x3", "tf32x3") and K > 256
+        launches_per_step = 1 + (2 if both else 1) * int(plan.workspace(alg["id"]) > 0)
     else:
         launches_per_step = alg["n_phases"] * (1 + sum(1 for lv in alg["copy_level"] if lv != -2))
 
@@ -449,7 +454,8 @@ def measure_form(args, dtype, spec, extents, A, B, dev, stream, dist, world, tc,
                     "frac": achieved_tf / peak_tf,
                     "traffic": captured_traffic(tkey, "paper_1409_8608_gb300/csrc/tc_gett.cu"),
                     "algorithmic_bytes": algorithmic_bytes,
-                    "kernel": "gett_tc_kernel" + (" + pack_kernel (timed together)" if launches_per_step == 2 else ""),
+                    "kernel": "gett_tc_kernel" + (" + pack_kernel (timed together)" if launches_per_step == 2 else
+                                                  " + 2 x pack_kernel (timed together)" if launches_per_step == 3 else ""),
                     "work": f"{prods} slice products x 2*prod(extents) = {work / 1e9:.1f} GFLOP per step",
                     "peak_source": "MEASURED_PEAKS bf16_tflops (burst)" +
                     (" x 0.5 (TF32 nominal ratio)" if dtype in ("tf32", "tf32x3") else "") +
@@ -721,15 +727,20 @@ def run_gpu(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(device=dev)
 
-    A, B, _ = synth.uniform_operands(SPEC, EXTENTS, seed=rank)
-    pts, lin = sample_points(SPEC, EXTENTS, 4000, seed=11)
     if args.only:  # one form alone (for profiler captures)
+        spec, ext, form, wl = SPEC, EXTENTS, args.only, WORKLOAD
+        if args.only == "bf16x3_4096":  # the chosen form of the tensor-bound precision workload
+            spec, ext = PRECISION_WORKLOADS[1][:2]
+            form, wl = "bf16x3", f"{spec} {ext}"
+        A, B, _ = synth.uniform_operands(spec, ext, seed=rank)
         with torch.cuda.stream(stream):
-            one, _ = measure_form(args, args.only, SPEC, EXTENTS, A, B, dev, stream, dist, world, tc,
+            one, _ = measure_form(args, form, spec, ext, A, B, dev, stream, dist, world, tc,
                                   args.steps, e2e=False, clocks=False)
         if rank == 0:
-            print(json.dumps(dict(one, metric=METRIC, config={"workload": WORKLOAD, "only": args.only})), flush=True)
+            print(json.dumps(dict(one, metric=METRIC, config={"workload": wl, "only": args.only})), flush=True)
         return 0
+    A, B, _ = synth.uniform_operands(SPEC, EXTENTS, seed=rank)
+    pts, lin = sample_points(SPEC, EXTENTS, 4000, seed=11)
     with torch.cuda.stream(stream):
         head, head_samples = measure_form(args, "f64", SPEC, EXTENTS, A, B, dev, stream, dist, world, tc,
                                           args.steps, sample_lin=lin)
@@ -841,7 +852,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="the headline form only (no other forms or workloads)")
-    ap.add_argument("--only", default=None, choices=["f64", "f32", "bf16x3", "tf32x3"],
+    ap.add_argument("--only", default=None, choices=["f64", "f32", "bf16x3", "tf32x3", "bf16x3_4096"],
                     help="profiling captures: one form of the headline workload alone, its line only")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--impl", default="tc", choices=["tc", "reference"])

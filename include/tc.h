@@ -237,17 +237,19 @@ tc_status tc_plan_set_gett_tile(tc_plan plan, int32_t width);
  * same either way. */
 tc_status tc_plan_set_gett_tma(tc_plan plan, int32_t enable);
 
-/* Tensor-core GETT, FP32 inputs (TC_BF16X3, TC_TF32X3, TC_TF32):
- * pre-conversion of the smaller input, or of both.  With it, a pre-pass
- * kernel writes the input once into the plan's workspace as the converted
- * shared-memory images of its tiles (split-BF16 slices or TF32 words in the
+/* Tensor-core GETT, FP32 inputs (TC_BF16X3, TC_TF32X3, TC_TF32) and, for
+ * both inputs only, 16-bit ones (TC_BF16, TC_F16): pre-conversion of the
+ * smaller input, or of both.  With it, a pre-pass kernel writes the input
+ * once into the plan's workspace as the converted shared-memory images of
+ * its tiles (split-BF16 slices, TF32 words or the 16-bit values in the
  * MMA's core-matrix layout, zeros past the extents), and the GETT copies
  * them instead of loading and converting the input per tile; the K order
  * then follows the larger input alone.  mode 0: never; 1 (default): both
  * inputs for the compensated split form (K past the chunk of
- * tc_plan_set_compensation) when their images fit in 2 GiB, else the smaller
- * input when it has at most 1/8 of the larger one's elements and its
- * images fit in 64 MiB; 2: the smaller input whenever its images fit in
+ * tc_plan_set_compensation) and wherever M and N are both at least 1024,
+ * when their images fit in 2 GiB, else (FP32 inputs) the smaller input
+ * when it has at most 1/8 of the larger one's elements and its images fit
+ * in 64 MiB; 2: the smaller input (FP32 inputs) whenever its images fit in
  * 64 MiB; 3: both inputs whenever their images fit in 2 GiB (else none),
  * each stage's two images then reach shared memory as two 1-D bulk copies
  * and no input is staged by TMA.  Other values give
@@ -375,8 +377,10 @@ tc_status tc_plan_select_best(tc_plan plan, int32_t *best);
 
 /* Autotuner for the tensor-core GETT: predicts every tile configuration
  * -- tile width 128 or 256, TMA staging on or off, one or two CTAs per
- * tile (tc_plan_set_gett_pair), the smaller input pre-converted or not
- * (tc_plan_set_gett_pack 0 or 2); every one gives the same bits -- with
+ * tile (tc_plan_set_gett_pair), no input, the smaller input or both
+ * pre-converted (tc_plan_set_gett_pack 0, 2 or 3); width, staging and
+ * pairs give the same bits, pre-conversion can change the K order and so
+ * the rounding (within the form's bound) -- with
  * the same micro-benchmark, and keeps the fastest in the plan, reporting
  * the width in *width and TMA in *tma (either may be NULL;
  * tc_plan_get_gett_config reads all four).  Results are cached per (spec,

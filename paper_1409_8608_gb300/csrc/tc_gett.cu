@@ -77,6 +77,7 @@ constexpr int64_t kCompChunkK = 256;      // default K chunk of the compensated 
 constexpr int kConvGroups = 2;            // converter groups taking turns (TMA-staged operands)
 constexpr int64_t kPackMaxBytes = int64_t(64) << 20;  // largest pre-converted input
 constexpr int64_t kPackBothMaxBytes = int64_t(2) << 30;  // both inputs pre-converted: their images
+constexpr int64_t kPackBothMinMN = 1024;                   // auto: both inputs pre-converted from these M, N
 constexpr int kPackRatio = 8;             // auto: the smaller input has <= 1/8 the elements
 constexpr int kEpiWarps = 4;              // warps 0-3
 constexpr int kEpiThreads = kEpiWarps * 32;
@@ -1583,6 +1584,85 @@ __global__ void __launch_bounds__(128) pack_kernel(const GettDesc d, int op, int
     }
 }
 
+// Pre-conversion of one 16-bit input (BF16 / FP16; op 0 = A, 1 = B) for the
+// both-inputs path: its stage images in the core-matrix layout, the values
+// as they are, zeros for rows past the extent and K positions past K.  One
+// thread per 16-byte core-matrix row (8 K positions of one row).
+__global__ void __launch_bounds__(128) pack16_kernel(const GettDesc d, int op, int rows, int bk, int64_t rtiles,
+                                                     char *out) {
+    constexpr int CH = 8;
+    const int kcn = bk / CH;
+    const int64_t nkt = (d.K + bk - 1) / bk;
+    const int64_t R = op == 0 ? d.M : d.N;
+    const int64_t total = rtiles * nkt * kcn * rows;
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const uint16_t *__restrict__ src = (const uint16_t *)(op == 0 ? d.A : d.B);
+    const int nr = op == 0 ? d.nm : d.nn;
+    const int64_t *rext = op == 0 ? d.m_ext : d.n_ext;
+    const int64_t *rs = op == 0 ? d.m_sA : d.n_sB;
+    const int64_t *ks = op == 0 ? d.k_sA : d.k_sB;
+    const int64_t slice = (int64_t)rows * bk * 2;
+    const bool whole = d.nk > 0 && d.k_ext[d.nk - 1] % CH == 0;  // a chunk is one run of the innermost K mode
+    const int64_t s_in = d.nk > 0 ? ks[d.nk - 1] : 0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t row, kc, kt;
+        int64_t q = divmod(c, rows, row);
+        q = divmod(q, kcn, kc);
+        const int64_t rt = divmod(q, nkt, kt);
+        int64_t r = rt * rows + row, ro = -1;
+        if (r < R) {
+            ro = 0;
+            for (int m = 0; m < nr; ++m) {
+                int64_t v;
+                r = divmod(r, rext[m], v);
+                ro += v * rs[m];
+            }
+        }
+        uint16_t x[CH];
+#pragma unroll
+        for (int e = 0; e < CH; ++e) x[e] = 0;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        bool vec = false;
+        if (ro >= 0 && whole) {
+            int64_t k = kt * bk + kc * CH, ko = 0;
+            if (k < d.K) {
+                for (int m = d.nk - 1; m >= 0; --m) {
+                    int64_t v;
+                    k = divmod(k, d.k_ext[m], v);
+                    ko += v * ks[m];
+                }
+                const uint16_t *p = src + ro + ko;
+                if (s_in == 1 && ((uintptr_t)p & 15) == 0) {
+                    w = *reinterpret_cast<const uint4 *>(p);
+                    vec = true;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < CH; ++e) x[e] = p[e * s_in];
+                }
+            }
+        } else if (ro >= 0) {
+#pragma unroll
+            for (int e = 0; e < CH; ++e) {
+                int64_t k = kt * bk + kc * CH + e;
+                if (k < d.K) {
+                    int64_t ko = 0;
+                    for (int m = d.nk - 1; m >= 0; --m) {  // innermost K mode fastest
+                        int64_t v;
+                        k = divmod(k, d.k_ext[m], v);
+                        ko += v * ks[m];
+                    }
+                    x[e] = src[ro + ko];
+                }
+            }
+        }
+        if (!vec)
+            w = make_uint4(x[0] | ((uint32_t)x[1] << 16), x[2] | ((uint32_t)x[3] << 16), x[4] | ((uint32_t)x[5] << 16),
+                           x[6] | ((uint32_t)x[7] << 16));
+        char *dst = out + (rt * nkt + kt) * slice + (kc * (rows / 8) + row / 8) * 128 + (row % 8) * 16;
+        *(uint4 *)dst = w;
+    }
+}
+
 // E4M3 scales: the largest magnitude of each input over its modes, then the
 // power of two s with max / s <= 448 (E4M3's largest finite value), so that
 // dividing by s is exact and no input saturates.
@@ -1936,27 +2016,32 @@ bool plan_tma_operand(const Plan &p, int opnd, const void *base, int in_bytes, i
 
 // bytes of a pre-converted input element: TF32 word, three BF16 slices, or
 // two TF32 words
-int image_bytes(tc_dtype dt) { return dt == TC_TF32 ? 4 : (dt == TC_TF32X3 ? 8 : 6); }
+int image_bytes(tc_dtype dt) {
+    return dt == TC_TF32 ? 4 : (dt == TC_TF32X3 ? 8 : ((dt == TC_BF16 || dt == TC_F16) ? 2 : 6));
+}
 
 // Pre-conversion choice for the tensor-core GETT (0 none, 1 A, 2 B: the
 // input with fewer elements, 3 both) and a bound on the stage images' bytes.
 int pack_choice(const Plan &p, int64_t &bound) {
     bound = 0;
-    if ((p.dtype != TC_BF16X3 && p.dtype != TC_TF32 && p.dtype != TC_TF32X3) || p.gett_pack == 0 ||
+    const bool in16 = p.dtype == TC_BF16 || p.dtype == TC_F16;  // 16-bit inputs: both-inputs form only
+    if ((p.dtype != TC_BF16X3 && p.dtype != TC_TF32 && p.dtype != TC_TF32X3 && !in16) || p.gett_pack == 0 ||
         !p.batch.empty())
         return 0;
     int64_t M = 1, N = 1, K = 1;
     for (int id : p.freeA) M *= p.ext[id];
     for (int id : p.freeB) N *= p.ext[id];
     for (int id : p.contracted) K *= p.ext[id];
-    // both inputs: on request (3), and by default for the compensated form,
-    // whose 128-column tiles would otherwise convert each input once per
-    // tile of the other; A's rows round up to a 128-row tile, B's to a
-    // 256-row one, K to a 32-position stage, plus the alignment of B's images
+    // both inputs: on request (3), and by default for the compensated form
+    // (whose 128-column tiles would otherwise convert each input once per
+    // tile of the other) and wherever both M and N reach kPackBothMinMN (each
+    // input would be converted or re-laid out at least four times); A's
+    // rows round up to a 128-row tile, B's to a 256-row one, K to a
+    // 32-position stage, plus the alignment of B's images
     int64_t comp_k = 0;
     if (p.dtype == TC_BF16X3 || p.dtype == TC_TF32X3) comp_k = p.comp_chunk < 0 ? kCompChunkK : p.comp_chunk;
     const bool comp = comp_k > 0 && K > comp_k;
-    if (p.gett_pack == 3 || (p.gett_pack == 1 && comp)) {
+    if (p.gett_pack == 3 || (p.gett_pack == 1 && (comp || (M >= kPackBothMinMN && N >= kPackBothMinMN)))) {
         const int64_t b2 = (M + N + 512) * (K + kBK - 1) * image_bytes(p.dtype) + 256;
         if (b2 <= kPackBothMaxBytes) {
             bound = b2;
@@ -1964,6 +2049,7 @@ int pack_choice(const Plan &p, int64_t &bound) {
         }
         if (p.gett_pack == 3) return 0;
     }
+    if (in16) return 0;
     const bool a_small = M <= N;  // the same choice as the K order's "larger input"
     const int64_t R = a_small ? M : N;
     // auto: only where the two inputs are contiguous along different
@@ -2242,10 +2328,12 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
             const int rows = o == 0 ? kBM : brows;
             const int64_t rt = o == 0 ? rtA : rtB;
             const int64_t bytes = rt * nktp * (o == 0 ? stA : stB);
-            const int64_t chunks = bytes / 16 / (p.dtype == TC_TF32 ? 1 : (p.dtype == TC_TF32X3 ? 2 : 3));
+            const int64_t chunks =
+                bytes / 16 / (p.dtype == TC_TF32X3 ? 2 : (p.dtype == TC_BF16X3 ? 3 : 1));  // 16-byte rows of slice 0
             const unsigned grid = (unsigned)std::min<int64_t>((chunks + 127) / 128, 152 * 16);
             char *out = (char *)p.workspace + (o == 0 ? 0 : offB);
-            if (p.dtype == TC_TF32) pack_kernel<GK_TF32><<<grid, 128, 0, st>>>(d, o, rows, kBK, rt, out);
+            if (p.dtype == TC_BF16 || p.dtype == TC_F16) pack16_kernel<<<grid, 128, 0, st>>>(d, o, rows, kBK, rt, out);
+            else if (p.dtype == TC_TF32) pack_kernel<GK_TF32><<<grid, 128, 0, st>>>(d, o, rows, kBK, rt, out);
             else if (p.dtype == TC_TF32X3) pack_kernel<GK_TF32X3><<<grid, 128, 0, st>>>(d, o, rows, kBK, rt, out);
             else pack_kernel<GK_BF16X3><<<grid, 128, 0, st>>>(d, o, rows, kBK, rt, out);
         }

@@ -398,8 +398,10 @@ tc_status tc_autotune(tc_plan plan, const void *A, const void *B, void *C, void 
     int best_bn = 0, best_tma = 1, best_pair = 0, best_pack = 1;
     if (tensor) {
         // candidates: tile width, TMA staging, one or two CTAs per tile and
-        // the pre-conversion of the smaller input -- all give the same bits
-        // -- each costed by the GETT micro-benchmark (a few waves of real
+        // the pre-conversion of the smaller input or of both (tile width,
+        // staging and pairs give the same bits; pre-conversion can change
+        // the K order, and so the rounding, within the form's bound) --
+        // each costed by the GETT micro-benchmark (a few waves of real
         // tiles, median of ten), as in tc_predict
         double best_t = -1;
         const int saved[4] = {p.gett_bn, p.gett_tma, p.gett_pair, p.gett_pack};
@@ -407,7 +409,9 @@ tc_status tc_autotune(tc_plan plan, const void *A, const void *B, void *C, void 
             for (int tm : {0, 1}) {
                 if (tm == 1 && bn != 256) continue;  // the TMA path runs 128 x 256 tiles
                 for (int pair : {0, 1}) {
-                    for (int pack : {0, 2}) {
+                    for (int pack : {0, 2, 3}) {
+                        if (pack == 3 && tm == 0 && bn == 256) continue;  // no input is staged: once per width
+                        if (pack == 3 && p.dtype != TC_BF16X3 && p.dtype != TC_TF32X3 && p.dtype != TC_TF32) continue;
                         p.gett_bn = bn;
                         p.gett_tma = tm;
                         p.gett_pair = pair;

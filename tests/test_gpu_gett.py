@@ -533,6 +533,32 @@ def test_pack_both_pairs_bitwise(tcmod, spec, ext, dtype, comp):
     assert err <= bound, (err, bound)
 
 
+@pytest.mark.parametrize("dtype", ["bf16", "f16", "tf32"])
+@pytest.mark.parametrize("spec,ext", [("ab=aij,jib", [300, 260, 24, 20]), ("abc=ai,ibc", [130, 100, 3, 72])])
+def test_pack_both_16bit_and_tf32_bitwise(tcmod, spec, ext, dtype):
+    # both inputs pre-converted (16-bit inputs re-laid out as they are): the
+    # same bits as the converter path (these layouts' K order does not
+    # depend on pre-conversion), exact on integers
+    A, B, _ = synth.uniform_operands(spec, ext, seed=17)
+    Ai, Bi, _ = synth.integer_operands(spec, ext, seed=18)
+    n = synth.dense_sizes(spec, ext)[0]
+    for (X, Y), exact in (((A, B), False), ((Ai, Bi), True)):
+        dA, dB, _ = device_inputs(dtype, X, Y)
+        outs = {}
+        for pack in (0, 3):
+            plan = tcmod.Plan(spec, ext, dtype=dtype)
+            plan.set_gett_pack(pack)
+            dC = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda:0")
+            plan.execute(dA, dB, dC)
+            torch.cuda.synchronize()
+            plan.device_status()
+            plan.close()
+            outs[pack] = dC.double().cpu().numpy()
+        assert np.array_equal(outs[3], outs[0])
+        if exact:
+            assert np.array_equal(outs[3], oc.contract(spec, ext, Ai, Bi))
+
+
 @pytest.mark.parametrize("dtype", ["bf16x3", "tf32x3"])
 def test_pack_both_compensated_default(tcmod, dtype):
     # the compensated form pre-converts both inputs by default (mode 1):
