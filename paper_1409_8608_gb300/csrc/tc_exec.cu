@@ -311,7 +311,10 @@ __device__ __forceinline__ void tile_body(const TileDesc &d, int64_t bid) {
         }
     }
 
-    // K offsets of a stage into table buffer b (threads kk < BK)
+    // K offsets of a stage into table buffer b (threads kk < BK); the K
+    // position's digits in 32-bit arithmetic when K fits (a 64-bit division
+    // is a long dependent sequence, and the other warps wait for these
+    // tables at the stage's barrier)
     auto k_tables = [&](int64_t k0, int b) {
         for (int kk = tid; kk < BK; kk += NT) {
             int64_t k = k0 + kk;
@@ -319,11 +322,22 @@ __device__ __forceinline__ void tile_body(const TileDesc &d, int64_t bid) {
             if (k < d.K) {
                 oa = 0;
                 ob = 0;
-                for (int m = d.red.n - 1; m >= 0; --m) {
-                    int64_t x = k % d.red.ext[m];
-                    k /= d.red.ext[m];
-                    oa += x * d.red.sA[m];
-                    ob += x * d.red.sB[m];
+                if (d.K < (int64_t(1) << 31)) {
+                    uint32_t k32 = (uint32_t)k;
+                    for (int m = d.red.n - 1; m >= 0; --m) {
+                        const uint32_t e = (uint32_t)d.red.ext[m];
+                        const int64_t x = (int64_t)(k32 % e);
+                        k32 /= e;
+                        oa += x * d.red.sA[m];
+                        ob += x * d.red.sB[m];
+                    }
+                } else {
+                    for (int m = d.red.n - 1; m >= 0; --m) {
+                        int64_t x = k % d.red.ext[m];
+                        k /= d.red.ext[m];
+                        oa += x * d.red.sA[m];
+                        ob += x * d.red.sB[m];
+                    }
                 }
             }
             kA[b][kk] = oa;
@@ -387,7 +401,10 @@ __device__ __forceinline__ void tile_body(const TileDesc &d, int64_t bid) {
     // While stage s is multiplied, stage s + 1's global loads are in flight
     // and then stored to the other buffer, whose last reader (stage s - 1)
     // finished before the barrier that ended the previous iteration; one
-    // barrier per stage.
+    // barrier per stage.  Stage s + 2's K tables go to buffer s & 1 right
+    // after stage s + 1's loads have read theirs (buffer s & 1 was last read
+    // by stage s's loads, before that barrier), so that their integer work
+    // overlaps the multiplications instead of delaying the barrier.
     k_tables(0, 0);
     __syncthreads();
     load_stage(0);
@@ -398,6 +415,7 @@ __device__ __forceinline__ void tile_body(const TileDesc &d, int64_t bid) {
     for (int64_t k0 = 0; k0 < d.K; k0 += BK, sb ^= 1) {
         const bool more = k0 + BK < d.K;
         if (more) load_stage(sb ^ 1);
+        if (k0 + 2 * BK < d.K) k_tables(k0 + 2 * BK, sb);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
             T a[TM], b[TN];
@@ -429,10 +447,7 @@ __device__ __forceinline__ void tile_body(const TileDesc &d, int64_t bid) {
 #pragma unroll
                 for (int j = 0; j < TN; ++j) acc[i][j] = fma_t<T>(a[i], b[j], acc[i][j]);
         }
-        if (more) {
-            store_stage(sb ^ 1);
-            if (k0 + 2 * BK < d.K) k_tables(k0 + 2 * BK, sb);
-        }
+        if (more) store_stage(sb ^ 1);
         __syncthreads();
     }
 
