@@ -238,11 +238,12 @@ tc_status tc_plan_set_gett_tile(tc_plan plan, int32_t width);
 tc_status tc_plan_set_gett_tma(tc_plan plan, int32_t enable);
 
 /* Tensor-core GETT, FP32 inputs (TC_BF16X3, TC_TF32X3, TC_TF32) and, for
- * both inputs only, 16-bit ones (TC_BF16, TC_F16): pre-conversion of the
- * smaller input, or of both.  With it, a pre-pass kernel writes the input
- * once into the plan's workspace as the converted shared-memory images of
- * its tiles (split-BF16 slices, TF32 words or the 16-bit values in the
- * MMA's core-matrix layout, zeros past the extents), and the GETT copies
+ * both inputs only, 16-bit ones (TC_BF16, TC_F16) and TC_E4M3:
+ * pre-conversion of the smaller input, or of both.  With it, a pre-pass
+ * kernel writes the input once into the plan's workspace as the converted
+ * shared-memory images of its tiles (split-BF16 slices, TF32 words, the
+ * 16-bit values or the scaled E4M3 bytes in the MMA's core-matrix layout,
+ * zeros past the extents), and the GETT copies
  * them instead of loading and converting the input per tile; the K order
  * then follows the larger input alone.  mode 0: never; 1 (default): both
  * inputs for the compensated split form (K past the chunk of

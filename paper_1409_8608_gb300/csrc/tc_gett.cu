@@ -1521,6 +1521,10 @@ __global__ void __launch_bounds__(128) pack_kernel(const GettDesc d, int op, int
     // and aligned
     const bool whole = d.nk > 0 && d.k_ext[d.nk - 1] % CH == 0;
     const int64_t s_in = d.nk > 0 ? ks[d.nk - 1] : 0;
+    // E4M3: the input divided by its scale (a power of two, written by the
+    // scale kernel earlier in the stream)
+    float qs = 1.0f;
+    if constexpr (KIND == GK_E4M3) qs = 1.0f / d.qscale[op];
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x) {
         // rows fastest, then K chunks, K stages, row tiles (divmod: 32-bit
         // divisions whenever the values fit)
@@ -1580,7 +1584,7 @@ __global__ void __launch_bounds__(128) pack_kernel(const GettDesc d, int op, int
         }
         char *dst = out + (rt * nkt + kt) * (int64_t)(T::kSlices * slice) + (kc * (rows / 8) + row / 8) * 128 +
                     (row % 8) * 16;
-        store_converted<KIND, CH>(x, dst, slice);
+        store_converted<KIND, CH>(x, dst, slice, qs);
     }
 }
 
@@ -2017,14 +2021,15 @@ bool plan_tma_operand(const Plan &p, int opnd, const void *base, int in_bytes, i
 // bytes of a pre-converted input element: TF32 word, three BF16 slices, or
 // two TF32 words
 int image_bytes(tc_dtype dt) {
-    return dt == TC_TF32 ? 4 : (dt == TC_TF32X3 ? 8 : ((dt == TC_BF16 || dt == TC_F16) ? 2 : 6));
+    return dt == TC_TF32 ? 4 : (dt == TC_TF32X3 ? 8 : ((dt == TC_BF16 || dt == TC_F16) ? 2 : (dt == TC_E4M3 ? 1 : 6)));
 }
 
 // Pre-conversion choice for the tensor-core GETT (0 none, 1 A, 2 B: the
 // input with fewer elements, 3 both) and a bound on the stage images' bytes.
 int pack_choice(const Plan &p, int64_t &bound) {
     bound = 0;
-    const bool in16 = p.dtype == TC_BF16 || p.dtype == TC_F16;  // 16-bit inputs: both-inputs form only
+    // 16-bit and E4M3 inputs: the both-inputs form only
+    const bool in16 = p.dtype == TC_BF16 || p.dtype == TC_F16 || p.dtype == TC_E4M3;
     if ((p.dtype != TC_BF16X3 && p.dtype != TC_TF32 && p.dtype != TC_TF32X3 && !in16) || p.gett_pack == 0 ||
         !p.batch.empty())
         return 0;
@@ -2303,6 +2308,42 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
     const bool want_split = p.gett_split > 0 || (p.gett_split < 0 && d.K >= kSplitMinK);
     d.split = ((p.dtype == TC_BF16X3 || p.dtype == TC_TF32X3) && !comp && want_split) ? 1 : 0;
     cudaStream_t st = (cudaStream_t)stream;
+    if (p.dtype == TC_E4M3) {
+        // the inputs' scales, written before the pre-passes and the GETT read
+        // them (stream order)
+        if (!p.qbuf) {
+            cudaError_t e = cudaMalloc(&p.qbuf, 16);
+            if (e != cudaSuccess) {
+                p.qbuf = nullptr;
+                return fail(TC_ERROR_OUT_OF_MEMORY, cudaGetErrorString(e));
+            }
+        }
+        unsigned *mx = (unsigned *)p.qbuf;
+        float *scale = (float *)((char *)p.qbuf + 8);
+        cudaMemsetAsync(mx, 0, 8, st);
+        for (int o = 0; o < 2; ++o) {
+            const Layout &L = p.op[o == 0 ? OP_A : OP_B];
+            AbsmaxDesc a;
+            std::memset(&a, 0, sizeof(a));
+            int64_t total = 1, span = 1;
+            for (int m = 0; m < L.n; ++m) {
+                a.ext[m] = p.ext[L.idx[m]];
+                a.stride[m] = L.stride[m];
+                total *= a.ext[m];
+                span += (a.ext[m] - 1) * a.stride[m];
+            }
+            a.n = span == total ? 0 : L.n;
+            a.total = total;
+            a.src = (const float *)(o == 0 ? A : B);
+            a.out = mx + o;
+            const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 8));
+            absmax_kernel<<<(unsigned)grid, 256, 0, st>>>(a);
+        }
+        e4m3_scale_kernel<<<1, 32, 0, st>>>(mx, scale);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
+        d.qscale = scale;
+    }
     if (pk == 3) {
         // both inputs' stage images (128-row tiles of A, bn-row tiles of B,
         // 32-position K stages), A's first, then B's on a 256-byte boundary;
@@ -2333,6 +2374,7 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
             const unsigned grid = (unsigned)std::min<int64_t>((chunks + 127) / 128, 152 * 16);
             char *out = (char *)p.workspace + (o == 0 ? 0 : offB);
             if (p.dtype == TC_BF16 || p.dtype == TC_F16) pack16_kernel<<<grid, 128, 0, st>>>(d, o, rows, kBK, rt, out);
+            else if (p.dtype == TC_E4M3) pack_kernel<GK_E4M3><<<grid, 128, 0, st>>>(d, o, rows, kBK, rt, out);
             else if (p.dtype == TC_TF32) pack_kernel<GK_TF32><<<grid, 128, 0, st>>>(d, o, rows, kBK, rt, out);
             else if (p.dtype == TC_TF32X3) pack_kernel<GK_TF32X3><<<grid, 128, 0, st>>>(d, o, rows, kBK, rt, out);
             else pack_kernel<GK_BF16X3><<<grid, 128, 0, st>>>(d, o, rows, kBK, rt, out);
@@ -2366,42 +2408,7 @@ tc_status exec_gett(Plan &p, const void *alpha, const void *A, const void *B, co
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
     }
-    if (p.dtype == TC_E4M3) {
-        // the inputs' scales, written before the GETT reads them (stream order)
-        if (!p.qbuf) {
-            cudaError_t e = cudaMalloc(&p.qbuf, 16);
-            if (e != cudaSuccess) {
-                p.qbuf = nullptr;
-                return fail(TC_ERROR_OUT_OF_MEMORY, cudaGetErrorString(e));
-            }
-        }
-        unsigned *mx = (unsigned *)p.qbuf;
-        float *scale = (float *)((char *)p.qbuf + 8);
-        cudaMemsetAsync(mx, 0, 8, st);
-        for (int o = 0; o < 2; ++o) {
-            const Layout &L = p.op[o == 0 ? OP_A : OP_B];
-            AbsmaxDesc a;
-            std::memset(&a, 0, sizeof(a));
-            int64_t total = 1, span = 1;
-            for (int m = 0; m < L.n; ++m) {
-                a.ext[m] = p.ext[L.idx[m]];
-                a.stride[m] = L.stride[m];
-                total *= a.ext[m];
-                span += (a.ext[m] - 1) * a.stride[m];
-            }
-            a.n = span == total ? 0 : L.n;
-            a.total = total;
-            a.src = (const float *)(o == 0 ? A : B);
-            a.out = mx + o;
-            const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 8));
-            absmax_kernel<<<(unsigned)grid, 256, 0, st>>>(a);
-        }
-        e4m3_scale_kernel<<<1, 32, 0, st>>>(mx, scale);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return fail(TC_ERROR_CUDA, cudaGetErrorString(e));
-        d.qscale = scale;
-        return launch_kind<GK_E4M3>(d, bn, false, false, false, tmA, tmB, st);
-    }
+    if (p.dtype == TC_E4M3) return launch_kind<GK_E4M3>(d, bn, false, false, false, tmA, tmB, st);
     switch (p.dtype) {
     case TC_BF16X3: return launch_kind<GK_BF16X3>(d, bn, tma, comp, pair, tmA, tmB, st);
     case TC_BF16: return launch_kind<GK_BF16>(d, bn, tma, comp, false, tmA, tmB, st);

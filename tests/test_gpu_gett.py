@@ -533,12 +533,13 @@ def test_pack_both_pairs_bitwise(tcmod, spec, ext, dtype, comp):
     assert err <= bound, (err, bound)
 
 
-@pytest.mark.parametrize("dtype", ["bf16", "f16", "tf32"])
+@pytest.mark.parametrize("dtype", ["bf16", "f16", "tf32", "e4m3"])
 @pytest.mark.parametrize("spec,ext", [("ab=aij,jib", [300, 260, 24, 20]), ("abc=ai,ibc", [130, 100, 3, 72])])
 def test_pack_both_16bit_and_tf32_bitwise(tcmod, spec, ext, dtype):
-    # both inputs pre-converted (16-bit inputs re-laid out as they are): the
-    # same bits as the converter path (these layouts' K order does not
-    # depend on pre-conversion), exact on integers
+    # both inputs pre-converted (16-bit inputs re-laid out as they are, E4M3
+    # divided by the inputs' scales): the same bits as the converter path
+    # (these layouts' K order does not depend on pre-conversion), exact on
+    # integers
     A, B, _ = synth.uniform_operands(spec, ext, seed=17)
     Ai, Bi, _ = synth.integer_operands(spec, ext, seed=18)
     n = synth.dense_sizes(spec, ext)[0]
