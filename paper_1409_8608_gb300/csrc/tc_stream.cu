@@ -41,6 +41,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "tc_internal.h"
 #include "tc_tcgen05.cuh"
@@ -296,13 +297,25 @@ __global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamA
                 const uint32_t sliceA = kRows * Kp * 2, sliceB = Mp * Kp * 2;
                 const uint32_t lboA = kRows * 16, lboB = Mp * 16;
                 const uint32_t dt = tmem + (uint32_t)(b * kMaxM);
-                for (int ks = 0; ks < Kp / 16; ++ks)
-                    for (int q = 0; q < a.nprod; ++q) {
-                        const uint32_t qa = (kPa >> (4 * q)) & 15u, qb = (kPb >> (4 * q)) & 15u;
-                        const uint64_t ad = smem_desc(sa + qa * sliceA + ks * 2 * lboA, lboA, 128);
-                        const uint64_t bd = smem_desc(sb + qb * sliceB + ks * 2 * lboB, lboB, 128);
-                        mma_f16(dt, ad, bd, idesc, (ks == 0 && q == 0) ? 0u : 1u);
+                // descriptors of slice 0, first K step; the others differ in
+                // the address field only (address >> 4, below 2^14), moved by
+                // adding (offset >> 4); the products unrolled, so the issuing
+                // thread spends a few independent instructions per MMA
+                const uint64_t ad0 = smem_desc(sa, lboA, 128), bd0 = smem_desc(sb, lboB, 128);
+                auto issue = [&](auto np) {
+                    constexpr int NP = decltype(np)::value;
+                    for (int ks = 0; ks < Kp / 16; ++ks) {
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) {
+                            const uint32_t qa = (kPa >> (4 * q)) & 15u, qb = (kPb >> (4 * q)) & 15u;
+                            const uint64_t ad = ad0 + (uint64_t)((qa * sliceA + ks * 2 * lboA) >> 4);
+                            const uint64_t bd = bd0 + (uint64_t)((qb * sliceB + ks * 2 * lboB) >> 4);
+                            mma_f16(dt, ad, bd, idesc, (ks == 0 && q == 0) ? 0u : 1u);
+                        }
                     }
+                };
+                if (a.nprod == 6) issue(std::integral_constant<int, 6>{});
+                else issue(std::integral_constant<int, 3>{});
                 mma_commit(&conv_empty[c]);
                 mma_commit(&acc_full[b]);
                 issued = true;
