@@ -170,6 +170,44 @@ def test_gett_pack_choice(lib):
             plan.close()
 
 
+def test_gett_pack_both_choice(lib):
+    # both inputs pre-converted: by default for the compensated split forms
+    # (K past the 256-element chunk) and wherever M and N are both at least
+    # 1024; mode 3 on request.  The workspace then holds both inputs' images
+    # (6 / 8 / 4 / 2 / 1 bytes per element for split-BF16 / 3xTF32 / TF32 /
+    # BF16 and FP16 / E4M3, rows and K rounded up to whole tiles and stages)
+    img = {"bf16x3": 6, "tf32x3": 8, "tf32": 4, "bf16": 2, "f16": 2, "e4m3": 1}
+
+    def both(ws, M, N, K, b):  # within the documented bound, at least the exact images
+        return b * (M + N) * K <= ws <= b * (M + N + 512) * (K + 31) + 256
+
+    # the compensated form (K = 288 > 256): both inputs, whatever the sizes
+    for dtype in ("bf16x3", "tf32x3"):
+        plan = tc.Plan("ab=aij,jib", [300, 40, 24, 12], dtype=dtype)
+        assert both(plan.workspace(0), 300, 40, 288, img[dtype]), dtype
+        plan.set_compensation(0)  # no compensation: one small input at most
+        assert plan.workspace(0) < img[dtype] * (300 + 40) * 288, dtype
+        plan.close()
+    # M and N of 1024 and more: every tensor form with FP32, 16-bit or E4M3 inputs
+    for dtype in img:
+        plan = tc.Plan("ab=aij,jib", [1024, 1536, 8, 8], dtype=dtype)
+        assert both(plan.workspace(0), 1024, 1536, 64, img[dtype]), dtype
+        plan.set_gett_pack(0)
+        assert plan.workspace(0) == 0, dtype
+        plan.close()
+        plan = tc.Plan("ab=aij,jib", [512, 1536, 8, 8], dtype=dtype)  # M below 1024
+        assert plan.workspace(0) < img[dtype] * (512 + 1536) * 64, dtype
+        plan.set_gett_pack(3)  # on request
+        assert both(plan.workspace(0), 512, 1536, 64, img[dtype]), dtype
+        plan.close()
+    # FP64 / FP32 run the SIMT GETT: nothing to pre-convert
+    for dtype in ("f64", "f32"):
+        plan = tc.Plan("ab=aij,jib", [1024, 1536, 8, 8], dtype=dtype)
+        plan.set_gett_pack(3)
+        assert plan.workspace(0) == 0
+        plan.close()
+
+
 def test_batch_indices_are_accepted_and_never_kernel_indices(lib):
     # an index in A, B and C is a batch index: the plan accepts it, and in
     # every algorithm it is one of the sliced loops, never a kernel index
