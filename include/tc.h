@@ -443,7 +443,9 @@ tc_status tc_chain_destroy(tc_chain chain);
 tc_status tc_chain_variants(tc_chain chain, tc_chain_variant *buf, int32_t capacity, int32_t *count);
 
 /* Largest intermediate in bytes that tc_chain_select(-1) may choose (-1: no
- * limit). */
+ * limit).  The limit covers the intermediate only: with a tensor-core
+ * dtype a step's plan may also hold the pre-converted images of its inputs
+ * (tc_plan_set_gett_pack's default), allocated by its first execute. */
 tc_status tc_chain_set_workspace_limit(tc_chain chain, int64_t bytes);
 
 /* Predicts every variant: for each step, tc_predict over every algorithm
