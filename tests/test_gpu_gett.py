@@ -694,3 +694,50 @@ def test_e4m3_degenerate_extents(tcmod, spec, ext):
     A, B, _ = synth.integer_operands(spec, ext, seed=14)
     dA, dB, _ = device_inputs("e4m3", A, B)
     assert np.array_equal(run_gett(tcmod, spec, ext, "e4m3", dA, dB), oc.contract(spec, ext, A, B))
+
+
+@pytest.mark.parametrize("dtype", ["bf16x3", "tf32x3", "tf32", "bf16", "e4m3"])
+@pytest.mark.parametrize("i_ext", [12, 16])
+def test_pack_both_strided_with_alpha_beta(tcmod, dtype, i_ext):
+    # both inputs pre-converted from operands with gaps between their
+    # elements (the gaps hold 1e6: a pre-pass that read past a mode would
+    # show), K = 12 (chunks cross the innermost K mode's end: the per-element
+    # path) or 16 (whole chunks: one decode per chunk), alpha = 2, beta =
+    # 1/2: the same bits as the per-tile conversion (one K mode: the same K
+    # order) and within the form's bound
+    spec, ext = "abc=ai,ibc", [40, 9, 7, i_ext]
+    a, b, c, i = ext
+    strides = [1, a, a * b, 2, 2 * a + 3, 1, i + 1, (i + 1) * b]  # C dense; A (a, i); B (i, b, c)
+    ext_d, sc, sa, sb = oc.operand_layout(spec, ext, strides)
+    nA = oc.required_length("ai", ext_d, sa)
+    nB = oc.required_length("ibc", ext_d, sb)
+    rng = np.random.default_rng(31 + i)
+    A = np.full(nA, 1e6)
+    B = np.full(nB, 1e6)
+    for x in range(a):
+        for y in range(i):
+            A[x * sa["a"] + y * sa["i"]] = rng.uniform(-1, 1)
+    for y in range(i):
+        for u in range(b):
+            for v in range(c):
+                B[y * sb["i"] + u * sb["b"] + v * sb["c"]] = rng.uniform(-1, 1)
+    C0 = rng.uniform(-1, 1, a * b * c)
+    dA, dB, (Ar, Br) = device_inputs(dtype, A, B)
+    outs = {}
+    for pack in (0, 3):
+        plan = tcmod.Plan(spec, ext, strides=strides, dtype=dtype)
+        plan.set_gett_pack(pack)
+        plan.select(0)
+        dC = torch.from_numpy(C0).float().to("cuda:0")
+        plan.execute(dA, dB, dC, alpha=2.0, beta=0.5)
+        torch.cuda.synchronize()
+        plan.device_status()
+        plan.close()
+        outs[pack] = dC.double().cpu().numpy()
+    assert np.array_equal(outs[3], outs[0])
+    C0f = C0.astype(np.float32).astype(np.float64)
+    want = oc.contract(spec, ext, Ar, Br, C=C0f.copy(), alpha=2.0, beta=0.5, strides=strides)
+    scale = 2.0 * oc.contract(spec, ext, np.abs(Ar), np.abs(Br), strides=strides) + 0.5 * np.abs(C0f)
+    bound = e4m3_bound(i) if dtype == "e4m3" else sum_bound(dtype, i, extra=2)
+    err = float(np.max(np.abs(outs[3] - want) / scale))
+    assert err <= bound, (err, bound)
