@@ -390,6 +390,39 @@ def test_precision_workload_meets_fp32_level(tcmod, dist):
     assert np.isfinite(got).all()
 
 
+@pytest.mark.parametrize("dtype", ["bf16", "f16", "tf32", "tf32x3", "e4m3"])
+def test_precision_workload_other_forms_full_size(tcmod, dtype):
+    # the 4096^2 precision workload in every other tensor form, at full size
+    # and in the default launch the benchmark times (both inputs
+    # pre-converted): the same bits as the per-tile conversion (this
+    # layout's K order does not depend on it) and within the form's bound on
+    # sampled outputs computed one by one
+    spec, ext = "ab=aij,jib", [4096, 4096, 64, 64]
+    A, B, _ = synth.uniform_operands(spec, ext, seed=0)
+    dA, dB, (Ar, Br) = device_inputs(dtype, A, B)
+    outs = {}
+    for pack in (1, 0):
+        plan = tcmod.Plan(spec, ext, dtype=dtype)
+        plan.set_gett_pack(pack)
+        assert (plan.workspace(0) > 0) == (pack == 1)
+        dC = torch.full((4096 * 4096,), float("nan"), dtype=torch.float32, device="cuda:0")
+        plan.execute(dA, dB, dC)
+        torch.cuda.synchronize()
+        plan.device_status()
+        plan.close()
+        outs[pack] = dC
+    assert torch.equal(outs[1], outs[0])
+    got = outs[1].double().cpu().numpy()
+    rng = np.random.default_rng(3)
+    pts = np.stack([rng.integers(0, 4096, 3000) for _ in range(2)], axis=1)
+    want = oc.contract_points(spec, ext, Ar, Br, pts, threads=4)
+    scale = oc.contract_points(spec, ext, np.abs(Ar), np.abs(Br), pts, threads=4)
+    err = float(np.max(np.abs(got[pts[:, 0] + 4096 * pts[:, 1]] - want) / scale))
+    bound = e4m3_bound(4096) if dtype == "e4m3" else sum_bound(dtype, 4096)
+    assert err <= bound, (err, bound)
+    assert np.isfinite(got).all()
+
+
 # Output layouts of the epilogue: C whose free modes of B do not chain
 # (padded strides: the per-tile column check and the column table), and
 # contractions with no free index in B or in A.
