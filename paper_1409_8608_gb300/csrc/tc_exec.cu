@@ -397,6 +397,37 @@ __device__ __forceinline__ void tile_body(const TileDesc &d, int64_t bid) {
             Bs[sb][kk][j] = rb[l];
         }
     };
+    // FP32 with alpha = 1: the stage's elements go straight to shared memory
+    // with 4-byte asynchronous copies (zero-filled past the extents), so no
+    // register holds them and no second pass stores them; the same values
+    // land in the same places as through load_stage + store_stage
+    const bool async_copy = sizeof(T) == 4 && d.alpha_one;
+    auto async_stage = [&](int b) {
+        auto cp4 = [](void *dst, const void *src, bool valid) {
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                             (uint32_t)__cvta_generic_to_shared(dst)),
+                         "l"(src), "r"(valid ? 4 : 0)
+                         : "memory");
+        };
+#pragma unroll
+        for (int l = 0; l < LA; ++l) {
+            int i, kk;
+            place(tid + l * NT, d.a_m_fast, BM, i, kk);
+            const int64_t om = offAm[i], ok = kA[b][kk];
+            const bool v = om >= 0 && ok >= 0;
+            cp4(&As[b][kk][i], v ? A + om + ok : A, v);
+        }
+#pragma unroll
+        for (int l = 0; l < LB; ++l) {
+            int j, kk;
+            place(tid + l * NT, d.b_n_fast, BN, j, kk);
+            const int64_t on = offBn[j], ok = kB[b][kk];
+            const bool v = on >= 0 && ok >= 0;
+            cp4(&Bs[b][kk][j], v ? B + on + ok : B, v);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto async_wait = []() { asm volatile("cp.async.wait_all;" ::: "memory"); };
     // Stage s sits in buffer s & 1 (shared memory and K tables alike).
     // While stage s is multiplied, stage s + 1's global loads are in flight
     // and then stored to the other buffer, whose last reader (stage s - 1)
@@ -407,14 +438,22 @@ __device__ __forceinline__ void tile_body(const TileDesc &d, int64_t bid) {
     // overlaps the multiplications instead of delaying the barrier.
     k_tables(0, 0);
     __syncthreads();
-    load_stage(0);
-    store_stage(0);
+    if (async_copy) {
+        async_stage(0);
+        async_wait();
+    } else {
+        load_stage(0);
+        store_stage(0);
+    }
     if (BK < d.K) k_tables(BK, 1);
     __syncthreads();
     int sb = 0;
     for (int64_t k0 = 0; k0 < d.K; k0 += BK, sb ^= 1) {
         const bool more = k0 + BK < d.K;
-        if (more) load_stage(sb ^ 1);
+        if (more) {
+            if (async_copy) async_stage(sb ^ 1);
+            else load_stage(sb ^ 1);
+        }
         if (k0 + 2 * BK < d.K) k_tables(k0 + 2 * BK, sb);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
@@ -447,7 +486,10 @@ __device__ __forceinline__ void tile_body(const TileDesc &d, int64_t bid) {
 #pragma unroll
                 for (int j = 0; j < TN; ++j) acc[i][j] = fma_t<T>(a[i], b[j], acc[i][j]);
         }
-        if (more) store_stage(sb ^ 1);
+        if (more) {
+            if (async_copy) async_wait();
+            else store_stage(sb ^ 1);
+        }
         __syncthreads();
     }
 
